@@ -1,0 +1,94 @@
+"""Pins of the oracle's FAS/PFASST (Sections 5.1.2, 5.2, 5.3, Algorithm 1)."""
+import numpy as np
+import pytest
+
+from oracle.pfasst import PFASST, restrict_space, interpolate_space
+from oracle.sdc import SDCLevel, lagrange_matrix, lobatto_nodes
+from oracle.sht import unpack
+from oracle.swe import SWEParams
+import synthetic as syn
+
+
+def _params():
+    return SWEParams(a=syn.EARTH_RADIUS, omega=syn.OMEGA, g=syn.GRAVITY, nu=1e5,
+                     phibar=syn.GRAVITY * syn.MEAN_DEPTH)
+
+
+def _state(T, seed=1):
+    return unpack(syn.zonal_jet(T), T) + unpack(
+        syn.random_spectrum(T, (3,), seed=seed, rms=1e-5), T) * np.array([1e3, 1, 1])[:, None, None]
+
+
+def _levels(Tf, Tc, dt):
+    f = SDCLevel(Tf, *syn.gaussian_grid_size(Tf), 5, dt, _params())
+    c = SDCLevel(Tc, *syn.gaussian_grid_size(Tc), 3, dt, _params())
+    return f, c
+
+
+def test_space_restriction_of_interpolation_is_identity():
+    x = unpack(syn.random_spectrum(7, (3,), seed=2, nmin=0), 7)
+    y = interpolate_space(x, 16)
+    assert np.array_equal(restrict_space(y, 8), x)
+    assert np.all(y[..., 8:, :] == 0) and np.all(y[..., :, 8:] == 0)
+
+
+@pytest.mark.parametrize("fine,coarse,inj", [(5, 3, [0, 2, 4]), (3, 2, [0, 2]), (5, 2, [0, 4])])
+def test_nested_lobatto_time_restriction_is_injection(fine, coarse, inj):
+    R = lagrange_matrix(lobatto_nodes(fine), lobatto_nodes(coarse))
+    E = np.zeros_like(R)
+    for i, j in enumerate(inj):
+        E[i, j] = 1.0
+    assert np.max(np.abs(R - E)) < 1e-14
+    # interpolation reproduces the coarse values at the shared nodes
+    P = lagrange_matrix(lobatto_nodes(coarse), lobatto_nodes(fine))
+    assert np.max(np.abs(R @ P - np.eye(coarse))) < 1e-14
+
+
+def test_fas_invariant_restricted_fine_solution_solves_coarse_problem():
+    """Section 5.1.2: with tau_c, R Theta_f is a solution of the coarse problem."""
+    f, c = _levels(15, 7, 600.0)
+    th, FE, FI = f.spread(_state(15))
+    for _ in range(30):
+        th, FE, FI = f.sweep(th, FE, FI)
+    pf = PFASST(f, c, 1)
+    thc = pf.restrict(th)
+    FEc = np.empty_like(thc)
+    FIc = np.empty_like(thc)
+    for i in range(3):
+        FEc[i], FIc[i] = c.eval_f(thc[i])
+    tau = pf.fas(FE, FI, FEc, FIc)
+    thc2, _, _ = c.sweep(thc, FEc, FIc, tau)
+    assert np.max(np.abs(thc2 - thc)) < 1e-14 * np.max(np.abs(thc))
+
+
+def _serial(f, th0, n_ts):
+    out, x = [], th0
+    for _ in range(n_ts):
+        th, FE, FI = f.spread(x)
+        for _ in range(40):
+            th, FE, FI = f.sweep(th, FE, FI)
+        x = th[-1]
+        out.append(x)
+    return np.array(out)
+
+
+@pytest.mark.parametrize("Tc", [15, 7])
+def test_pfasst_converges_to_serial_collocation(Tc):
+    Tf, n_ts = 15, 4
+    f, c = _levels(Tf, Tc, 600.0)
+    th0 = _state(Tf)
+    ref = _serial(f, th0, n_ts)
+    pf = PFASST(f, c, n_ts)
+    errs = [np.max(np.abs(pf.run(th0, k) - ref)) for k in (2, 12)]
+    scale = np.max(np.abs(ref[:, 1]))
+    assert errs[1] < 1e-12 * np.max(np.abs(ref))
+    assert errs[1] < errs[0]
+    assert scale > 0
+
+
+def test_pfasst_single_slice_is_two_level_sdc():
+    f, c = _levels(15, 7, 600.0)
+    th0 = _state(15)
+    ref = _serial(f, th0, 1)
+    out = PFASST(f, c, 1).run(th0, 8)
+    assert np.max(np.abs(out - ref)) < 1e-12 * np.max(np.abs(ref))
