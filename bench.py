@@ -1,0 +1,409 @@
+"""Benchmark: two-level PFASST-SH on one GB300 (fine T255 on 384x768, coarse
+T127 on 192x384, 32 time slices, 5/3 Gauss-Lobatto nodes, dt = 120 s).
+
+A step is one PFASST iteration (Algorithm 1: fine sweeps, restriction + FAS,
+serial coarse chain, interpolation) over all 32 slices -- every stage of the
+hot path.  The JSON line reports PFASST iterations/s (the headline), SWE RHS
+evaluations/s at T255 with 32 states per call, an end-to-end block solve
+through the C ABI with host buffers, the roofline of the dominant kernel and
+the FP64 CPU oracle timed on a bounded sample.
+
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64] [--impl reference]
+
+Under torchrun (N > 1) every rank solves an independent replica of the
+workload (different bump location); `value` is the whole-job rate.
+"""
+from __future__ import annotations
+
+import argparse
+import json
+import math
+import os
+import statistics
+import subprocess
+import sys
+import tempfile
+import time
+
+import numpy as np
+
+ROOT = os.path.dirname(os.path.abspath(__file__))
+sys.path.insert(0, ROOT)
+
+import synthetic as syn  # noqa: E402
+
+TF, TC, NTS, NF, NC, DT, NPF = 255, 127, 32, 5, 3, 120.0, 4
+GRID_F = syn.gaussian_grid_size(TF)
+GRID_C = syn.gaussian_grid_size(TC)
+BUMP_AMPLITUDE, BUMP_WIDTH = 120.0, 1.0 / 15.0
+WORKLOAD = ("two-level PFASST-SH: T255 (384x768, 5 Lobatto nodes) / T127 (192x384, 3 nodes), "
+            "32 time slices, dt=120 s, balanced jet + 120 m Gaussian bump")
+
+
+def env_int(name, default):
+    try:
+        return int(os.environ.get(name, default))
+    except ValueError:
+        return default
+
+
+# ---------------------------------------------------------------------------
+# algorithmic work per unit
+# ---------------------------------------------------------------------------
+def legendre_flops(T: int, nlat: int, cols_complex: int) -> float:
+    """Real flops of one synthesis or analysis pass over `cols_complex` complex
+    columns: per m, 2 (FMA) * 2 (re/im) * (nlat/2) * K_m * cols with K_m = T+2-m."""
+    K = sum(T + 2 - m for m in range(T + 1))
+    return 4.0 * (nlat // 2) * K * cols_complex
+
+
+def grid_rhs_bytes(T: int, nlat: int, B: int, elem: int) -> float:
+    """HBM bytes of the fused FFT/grid kernel: read 4 spectra (m <= T) of every
+    latitude, write 5 hemispheric spectra, complex of `elem`-byte reals."""
+    return B * nlat * (T + 1) * (4 + 5) * 2 * elem
+
+
+# ---------------------------------------------------------------------------
+# clocks sampled during the timed region
+# ---------------------------------------------------------------------------
+class ClockSampler:
+    QUERY = ("index,clocks.sm,clocks.max.sm,power.draw,clocks_event_reasons.active,"
+             "clocks_event_reasons.hw_slowdown,clocks_event_reasons.hw_thermal_slowdown,"
+             "clocks_event_reasons.sw_thermal_slowdown,clocks_event_reasons.sw_power_cap")
+
+    def __init__(self, index: int):
+        self.index = index
+        self.proc = None
+        self.path = None
+
+    def start(self):
+        try:
+            fd, self.path = tempfile.mkstemp(suffix=".csv")
+            os.close(fd)
+            self.proc = subprocess.Popen(
+                ["nvidia-smi", "-i", str(self.index), f"--query-gpu={self.QUERY}", "--format=csv,noheader,nounits",
+                 "-lms", "200", "-f", self.path], stdout=subprocess.DEVNULL, stderr=subprocess.DEVNULL)
+        except Exception:
+            self.proc = None
+
+    def stop(self) -> dict:
+        if not self.proc:
+            return {"sm_mhz": None, "sm_max_mhz": None, "reasons": ["unsampled"]}
+        self.proc.terminate()
+        try:
+            self.proc.wait(timeout=5)
+        except Exception:
+            self.proc.kill()
+        sm, smax, reasons = [], [], set()
+        names = ["hw_slowdown", "hw_thermal_slowdown", "sw_thermal_slowdown", "sw_power_cap"]
+        try:
+            for line in open(self.path):
+                f = [x.strip() for x in line.split(",")]
+                if len(f) < 9:
+                    continue
+                try:
+                    sm.append(float(f[1]))
+                    smax.append(float(f[2]))
+                except ValueError:
+                    continue
+                for nm, v in zip(names, f[5:9]):
+                    if v.lower().startswith("active"):
+                        reasons.add(nm)
+            os.unlink(self.path)
+        except Exception:
+            pass
+        return {"sm_mhz": statistics.median(sm) if sm else None, "sm_max_mhz": max(smax) if smax else None,
+                "reasons": sorted(reasons), "samples": len(sm)}
+
+
+# ---------------------------------------------------------------------------
+# workload
+# ---------------------------------------------------------------------------
+def initial_state(ps, torch, dev, seed: int):
+    """Balanced jet + Gaussian height bump, projected with an FP64 plan of the library."""
+    nlat, nlon = GRID_F
+    plan = ps.sht_plan_create(TF, nlat, nlon, 1, "fp64")
+    lam_c, phi_c = syn.bump_center(seed)
+    lam = 2.0 * math.pi * np.arange(nlon) / nlon
+    grid = syn.GRAVITY * syn.gaussian_bump(np.array(plan.mu), lam, amplitude=BUMP_AMPLITUDE, width=BUMP_WIDTH,
+                                           lam_c=lam_c, phi_c=phi_c)
+    d_grid = torch.tensor(grid[None], dtype=torch.float64, device=dev)
+    d_spec = torch.empty((1, syn.ncoef(TF)), dtype=torch.complex128, device=dev)
+    ps.sht_forward(plan, d_grid, d_spec)
+    ps.pfsh_sync_status()
+    st = syn.zonal_jet(TF)
+    st[0] += d_spec[0].cpu().numpy()
+    st[0, 0] = st[0, 0].real
+    plan.close()
+    phibar = st[0, 0].real / math.sqrt(2.0)
+    return st, phibar
+
+
+def run_ours(args, rank, world, local_rank):
+    import torch
+    import paper_1904_05988_gb300 as ps
+
+    torch.cuda.set_device(local_rank)
+    dev = torch.device("cuda", local_rank)
+    dist = None
+    if world > 1:
+        import torch.distributed as dist
+        dist.init_process_group("nccl", device_id=dev)
+
+    def barrier():
+        if dist is not None:
+            dist.barrier()
+        torch.cuda.synchronize()
+
+    st0, phibar = initial_state(ps, torch, dev, seed=2 + rank)
+    pf = ps.pfasst_create(NTS, NF, NC, TF, *GRID_F, TC, *GRID_C, DT, syn.EARTH_RADIUS, syn.OMEGA, syn.NU,
+                          phibar, args.prec)
+    d_st0 = torch.tensor(st0, dtype=torch.complex128, device=dev)
+    stream = torch.cuda.current_stream()
+    ps.pfasst_set_initial(pf, d_st0)
+    ps.pfasst_predict(pf)
+    for _ in range(args.warmup):
+        ps.pfasst_iteration(pf, False)
+    ps.pfsh_sync_status()
+
+    # ---- timed region: K iterations of Algorithm 1 over all slices ----
+    clocks = ClockSampler(local_rank)
+    clocks.start()
+    time.sleep(0.3)
+    barrier()
+    n0 = ps.pfsh_kernel_launches()
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(args.steps):
+        ps.pfasst_iteration(pf, False)
+    e1.record(stream)
+    barrier()
+    launches = ps.pfsh_kernel_launches() - n0
+    ms = e0.elapsed_time(e1)
+    clk = clocks.stop()
+    ps.pfsh_sync_status()
+    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
+    ms_max = ms_t.item()
+    ms_per_step = ms_max / args.steps
+    value = world * args.steps / (ms_max / 1e3)
+
+    # ---- SWE RHS evaluations/s at T255, 32 states per call ----
+    plan_r = ps.sht_plan_create(TF, *GRID_F, 5 * NTS, args.prec)
+    ctx_r = ps.swe_ctx_create(plan_r, syn.EARTH_RADIUS, syn.OMEGA, syn.NU, phibar)
+    rhs_in = d_st0[None].repeat(NTS, 1, 1).contiguous()
+    rhs_fe, rhs_fi = torch.empty_like(rhs_in), torch.empty_like(rhs_in)
+    for _ in range(3):
+        ps.swe_rhs(ctx_r, rhs_in, rhs_fe, rhs_fi)
+    torch.cuda.synchronize()
+    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    nrhs = 10
+    r0.record(stream)
+    for _ in range(nrhs):
+        ps.swe_rhs(ctx_r, rhs_in, rhs_fe, rhs_fi)
+    r1.record(stream)
+    torch.cuda.synchronize()
+    rhs_per_s = nrhs * NTS / (r0.elapsed_time(r1) / 1e3)
+
+    # ---- profiled pass (same workload, separate from the timed region) ----
+    ps.pfsh_profiler_enable(True)
+    for _ in range(2):
+        ps.pfasst_iteration(pf, False)
+    ps.pfsh_profiler_enable(False)
+    prof = ps.pfsh_profiler_report()
+    roofline = roofline_of(prof, args.prec, 2)
+
+    # ---- end to end: host initial value -> block solve -> host end value ----
+    h_in = torch.tensor(st0, dtype=torch.complex128).pin_memory()
+    h_out = torch.empty_like(h_in).pin_memory()
+    d_in = torch.empty_like(d_st0)
+    d_out = torch.empty_like(d_st0)
+    blocks = max(1, min(3, args.steps))
+    torch.cuda.synchronize()
+    b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    b0.record(stream)
+    for _ in range(blocks):
+        d_in.copy_(h_in, non_blocking=True)
+        ps.pfasst_set_initial(pf, d_in)
+        ps.pfasst_predict(pf)
+        for k in range(NPF):
+            ps.pfasst_iteration(pf, k == NPF - 1)
+        ps.pfasst_get(pf, 0, NTS - 1, NF - 1, d_out)
+        h_out.copy_(d_out, non_blocking=True)
+    b1.record(stream)
+    torch.cuda.synchronize()
+    ms_block = b0.elapsed_time(b1) / blocks
+    if not np.all(np.isfinite(h_out.numpy().view(np.float64))):
+        raise RuntimeError("non-finite solution")
+    e2e_val = world * NPF / (ms_block / 1e3)
+    state_bytes = 3 * syn.ncoef(TF) * 16
+
+    cpu = cpu_baseline_sample() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
+    if rank == 0:
+        line = {
+            "metric": "PFASST iterations/s (T255/T127, 32 slices, 5/3 nodes) and SWE RHS evals/s at T255",
+            "value": value, "unit": "PFASST iterations/s", "n_gpus": world, "steps": args.steps,
+            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else f"f64 spectral + {args.prec} Legendre",
+            "data": "synthetic",
+            "config": {"workload": WORKLOAD, "n_ts": NTS, "nodes": [NF, NC], "T": [TF, TC],
+                       "grid": [list(GRID_F), list(GRID_C)], "dt": DT, "prec": args.prec,
+                       "parallelism": f"replicas x{world}", "l2": "working set 1.6 GB > 129 MB L2"},
+            "swe_rhs_evals_per_s": rhs_per_s,
+            "e2e": {"value": e2e_val, "unit": "PFASST iterations/s", "h2d_bytes_per_step": state_bytes,
+                    "d2h_bytes_per_step": state_bytes,
+                    "what": f"per block: H2D initial value, predictor, {NPF} iterations, D2H last slice end value"},
+            "gpu_launches": int(launches),
+            "clocks": clk,
+            "roofline": roofline,
+            "kernels_ms_per_iteration": {k: round(v[1] / 2, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
+            "cpu_baseline": cpu,
+        }
+        print(json.dumps(line), flush=True)
+    if dist is not None:
+        dist.destroy_process_group()
+
+
+def peaks():
+    try:
+        with open(os.path.join(ROOT, "MEASURED_PEAKS.json")) as fh:
+            return json.load(fh), "measured"
+    except Exception:
+        return {"hbm_gbs": 6800.0, "bf16_tflops": 1900.0, "bf16_tflops_sustained": 1700.0}, "fallback"
+
+
+FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no measured copy exists)
+
+
+def rhs_states_per_iteration():
+    """RHS evaluations in one (non-final) iteration of Algorithm 1 over all
+    slices: fine = sweep nodes 1..Mf + node 0 after Step D; coarse = every
+    node in Step B + node 0 of slices 1.. in Step C + sweep nodes 1..Mc."""
+    fine = NTS * (NF - 1) + NTS
+    coarse = NTS * NC + (NTS - 1) + NTS * (NC - 1)
+    return fine, coarse
+
+
+def kernel_work_per_iteration(name: str, prec: str):
+    """(algorithmic work, unit) of all launches of `name` in one iteration."""
+    nf_states, nc_states = rhs_states_per_iteration()
+    (nlat_f, _), (nlat_c, _) = GRID_F, GRID_C
+    elem = 8 if prec == "fp64" else 4
+    if name.startswith("k_synth"):
+        return nf_states * legendre_flops(TF, nlat_f, 4) + nc_states * legendre_flops(TC, nlat_c, 4), "flop"
+    if name.startswith("k_anal"):
+        return nf_states * legendre_flops(TF, nlat_f, 5) + nc_states * legendre_flops(TC, nlat_c, 5), "flop"
+    if name == "k_grid_rhs":
+        return (nf_states * grid_rhs_bytes(TF, nlat_f, 1, elem) + nc_states * grid_rhs_bytes(TC, nlat_c, 1, elem),
+                "byte")
+    return None, None
+
+
+def roofline_of(prof: dict, prec: str, iterations: int) -> dict:
+    """Roofline of the kernel with the largest total time in the profiled
+    pass: algorithmic work of its launches / their summed duration (equal to
+    work per launch / mean launch duration)."""
+    if not prof:
+        return None
+    name, (n, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
+    work, unit = kernel_work_per_iteration(name, prec)
+    pk, src = peaks()
+    out = {"kernel": name, "launches": n, "mean_launch_ms": tot_ms / n, "traffic": None}
+    if work is None:
+        out.update({"bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None})
+        return out
+    rate = work * iterations / (tot_ms / 1e3)
+    if unit == "flop" and prec == "fp64":
+        out.update({"bound": "alu", "achieved": rate / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
+                    "frac": rate / 1e12 / FP64_PEAK_TFLOPS,
+                    "peak_source": "nominal FP64 rate of the recipe (1.25 TFLOP/s); no measured FP64 peak"})
+    elif unit == "flop":
+        peak = pk["bf16_tflops_sustained"]
+        out.update({"bound": "tensor", "achieved": rate / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "frac": rate / 1e12 / peak, "peak_source": src + " bf16 sustained"})
+    else:
+        out.update({"bound": "hbm", "achieved": rate / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                    "frac": rate / 1e9 / pk["hbm_gbs"], "peak_source": src})
+    return out
+
+
+# ---------------------------------------------------------------------------
+# CPU oracle (bounded sample)
+# ---------------------------------------------------------------------------
+def oracle_problem(n_ts: int):
+    from oracle.pfasst import PFASST
+    from oracle.sdc import SDCLevel
+    from oracle.sht import SHT, unpack
+    from oracle.swe import SWEParams
+
+    lam_c, phi_c = syn.bump_center(2)
+    sht = SHT(TF, *GRID_F, L=TF + 1)
+    lam = 2.0 * math.pi * np.arange(GRID_F[1]) / GRID_F[1]
+    bump = syn.GRAVITY * syn.gaussian_bump(sht.mu, lam, amplitude=BUMP_AMPLITUDE, width=BUMP_WIDTH,
+                                           lam_c=lam_c, phi_c=phi_c)
+    st = unpack(syn.zonal_jet(TF), TF)
+    st[0] += sht.analysis(bump, TF + 1)
+    phibar = st[0, 0, 0].real / math.sqrt(2.0)
+    p = SWEParams(a=syn.EARTH_RADIUS, omega=syn.OMEGA, g=syn.GRAVITY, nu=syn.NU, phibar=phibar)
+    pf = PFASST(SDCLevel(TF, *GRID_F, NF, DT, p), SDCLevel(TC, *GRID_C, NC, DT, p), n_ts)
+    return pf, st
+
+
+def cpu_baseline_sample(steps: int = 1):
+    """Oracle: one Algorithm-1 iteration over 2 of the 32 slices (after its own
+    predictor), scaled x16 to a 32-slice iteration (work is linear in slices)."""
+    pf, st = oracle_problem(2)
+    pf.predict(st)
+    t = time.perf_counter()
+    for _ in range(steps):
+        pf.iteration(False)
+    dt = (time.perf_counter() - t) / steps
+    return {"value": 1.0 / (dt * NTS / 2), "unit": "PFASST iterations/s", "cores": os.cpu_count(),
+            "kind": "oracle", "sample": f"{steps} iteration(s) over 2 of 32 slices at T255/T127, scaled x16; "
+                                        f"{dt:.1f} s each; numpy {np.__version__}"}
+
+
+def run_reference(args, rank, world):
+    if rank != 0:
+        return
+    pf, st = oracle_problem(2)
+    pf.predict(st)
+    for _ in range(args.warmup):
+        pf.iteration(False)
+    t = time.perf_counter()
+    for _ in range(args.steps):
+        pf.iteration(False)
+    el = time.perf_counter() - t
+    value = args.steps / (el * NTS / 2)
+    cpu = {"value": value, "unit": "PFASST iterations/s", "cores": os.cpu_count(), "kind": "oracle",
+           "sample": "each step: one iteration over 2 of 32 slices at T255/T127, scaled x16"}
+    print(json.dumps({
+        "impl": "reference", "metric": "PFASST iterations/s (T255/T127, 32 slices, 5/3 nodes) and SWE RHS evals/s at T255",
+        "value": value, "unit": "PFASST iterations/s", "n_gpus": world, "steps": args.steps, "warmup": args.warmup,
+        "ms_per_step": el / args.steps * 1e3 * NTS / 2, "higher_is_better": True, "scaling": "weak",
+        "vs_baseline": None, "dtype": "f64", "data": "synthetic",
+        "config": {"workload": WORKLOAD, "n_ts": NTS, "nodes": [NF, NC], "T": [TF, TC], "dt": DT, "prec": "fp64"},
+        "cpu_baseline": cpu,
+        "e2e": {"value": value, "unit": "PFASST iterations/s", "h2d_bytes_per_step": 0, "d2h_bytes_per_step": 0},
+    }), flush=True)
+
+
+def main():
+    ap = argparse.ArgumentParser()
+    ap.add_argument("--gpus", type=int, default=1)
+    ap.add_argument("--steps", type=int, default=10)
+    ap.add_argument("--warmup", type=int, default=3)
+    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16", "fp16", "bf16x3"])
+    ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
+    ap.add_argument("--no-cpu-baseline", action="store_true")
+    args = ap.parse_args()
+    rank, world, local_rank = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
+    if args.impl == "reference":
+        run_reference(args, rank, world)
+    else:
+        run_ours(args, rank, world, local_rank)
+
+
+if __name__ == "__main__":
+    main()

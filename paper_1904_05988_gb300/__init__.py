@@ -1,0 +1,318 @@
+"""GB300-native PFASST-SH hot path: Python binding of ``include/pfsh.h``.
+
+Argument marshalling only: every function below forwards device pointers of
+torch CUDA tensors to the C ABI of ``lib/libpfsh.so`` and raises
+``PfshError`` on a negative status.  There is no fallback: if the library is
+missing, importing this package fails; run ``python paper_1904_05988_gb300/build.py``
+(or ``__graft_entry__.build()``) first.
+
+Names and argument order follow the C ABI.  Spectral arrays are complex128
+tensors of shape ``[..., ncoef]`` (m-major triangle, see the header) and
+states ``[..., 3, ncoef]``; grids are float64 (FP64 plans) or float32
+``[batch, nlat, nlon]``.
+"""
+from __future__ import annotations
+
+import ctypes
+import os
+
+import torch
+
+from .build import LIB
+
+PFSH_OK, PFSH_EINVAL, PFSH_ENOMEM, PFSH_ECUDA, PFSH_EUNSUPPORTED, PFSH_ETIMEOUT, PFSH_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
+PFSH_FP64, PFSH_FP32, PFSH_BF16, PFSH_FP16, PFSH_BF16X3 = 0, 1, 2, 3, 4
+PREC_NAMES = {"fp64": PFSH_FP64, "fp32": PFSH_FP32, "bf16": PFSH_BF16, "fp16": PFSH_FP16, "bf16x3": PFSH_BF16X3}
+
+EXPORTED = ["sht_plan_create", "sht_plan_destroy", "sht_plan_query", "sht_inverse", "sht_forward",
+            "swe_ctx_create", "swe_ctx_destroy", "swe_rhs", "swe_implicit_solve",
+            "sdc_level_create", "sdc_level_destroy", "sdc_spread", "sdc_sweep",
+            "pfasst_create", "pfasst_destroy", "pfasst_set_initial", "pfasst_predict",
+            "pfasst_iteration", "pfasst_get", "pfsh_sync_status", "pfsh_last_error",
+            "pfsh_kernel_launches", "pfsh_profiler_enable", "pfsh_profiler_report"]
+
+
+class PfshError(RuntimeError):
+    def __init__(self, code: int, msg: str):
+        super().__init__(f"pfsh status {code}: {msg}")
+        self.code = code
+
+
+def _load() -> ctypes.CDLL:
+    if not os.path.exists(LIB):
+        raise ImportError(f"CUDA library {LIB} is missing: build it with paper_1904_05988_gb300.build.build()")
+    return ctypes.CDLL(LIB)
+
+
+_lib = _load()
+
+c_int, c_double, c_void_p, c_size_t = ctypes.c_int, ctypes.c_double, ctypes.c_void_p, ctypes.c_size_t
+
+
+class SweParams(ctypes.Structure):
+    _fields_ = [("a", c_double), ("omega", c_double), ("nu", c_double), ("phibar", c_double)]
+
+
+class ShtInfo(ctypes.Structure):
+    _fields_ = [("T", c_int), ("nlat", c_int), ("nlon", c_int), ("ncoef", c_int), ("max_batch", c_int),
+                ("prec", c_int), ("device_bytes", c_size_t), ("mu", ctypes.POINTER(c_double)),
+                ("w", ctypes.POINTER(c_double))]
+
+
+class PfasstConfig(ctypes.Structure):
+    _fields_ = [("n_ts", c_int), ("fine_nodes", c_int), ("coarse_nodes", c_int),
+                ("Tf", c_int), ("nlat_f", c_int), ("nlon_f", c_int),
+                ("Tc", c_int), ("nlat_c", c_int), ("nlon_c", c_int),
+                ("dt", c_double), ("phys", SweParams), ("prec", c_int)]
+
+
+_sig = {
+    "sht_plan_create": [ctypes.POINTER(c_void_p), c_int, c_int, c_int, c_int, c_int],
+    "sht_plan_destroy": [c_void_p],
+    "sht_plan_query": [c_void_p, ctypes.POINTER(ShtInfo)],
+    "sht_inverse": [c_void_p, c_void_p, c_void_p, c_int, c_void_p],
+    "sht_forward": [c_void_p, c_void_p, c_void_p, c_int, c_void_p],
+    "swe_ctx_create": [ctypes.POINTER(c_void_p), c_void_p, ctypes.POINTER(SweParams)],
+    "swe_ctx_destroy": [c_void_p],
+    "swe_rhs": [c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p],
+    "swe_implicit_solve": [c_void_p, c_void_p, c_void_p, c_double, c_int, c_void_p],
+    "sdc_level_create": [ctypes.POINTER(c_void_p), c_void_p, c_int, c_double, c_int],
+    "sdc_level_destroy": [c_void_p],
+    "sdc_spread": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p],
+    "sdc_sweep": [c_void_p, c_void_p, c_void_p, c_void_p, c_void_p, c_int, c_void_p],
+    "pfasst_create": [ctypes.POINTER(c_void_p), ctypes.POINTER(PfasstConfig)],
+    "pfasst_destroy": [c_void_p],
+    "pfasst_set_initial": [c_void_p, c_void_p, c_void_p],
+    "pfasst_predict": [c_void_p, c_void_p],
+    "pfasst_iteration": [c_void_p, c_int, c_void_p],
+    "pfasst_get": [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p],
+    "pfsh_sync_status": [c_void_p],
+}
+for _name, _args in _sig.items():
+    _f = getattr(_lib, _name)
+    _f.argtypes = _args
+    _f.restype = c_int
+_lib.pfsh_last_error.argtypes = []
+_lib.pfsh_last_error.restype = ctypes.c_char_p
+_lib.pfsh_kernel_launches.argtypes = []
+_lib.pfsh_kernel_launches.restype = ctypes.c_ulonglong
+_lib.pfsh_profiler_enable.argtypes = [c_int]
+_lib.pfsh_profiler_enable.restype = c_int
+_lib.pfsh_profiler_report.argtypes = [ctypes.c_char_p, c_size_t]
+_lib.pfsh_profiler_report.restype = c_int
+
+
+def last_error() -> str:
+    return _lib.pfsh_last_error().decode()
+
+
+def _check(rc: int) -> None:
+    if rc != PFSH_OK:
+        raise PfshError(rc, last_error())
+
+
+def _stream(stream) -> int | None:
+    if stream is None:
+        return torch.cuda.current_stream().cuda_stream or None
+    return stream.cuda_stream if hasattr(stream, "cuda_stream") else stream
+
+
+def _ptr(t: torch.Tensor | None, dtype: torch.dtype | None = None, numel: int | None = None) -> int | None:
+    if t is None:
+        return None
+    if not t.is_cuda:
+        raise ValueError("tensor must live on a CUDA device")
+    if not t.is_contiguous():
+        raise ValueError("tensor must be contiguous")
+    if dtype is not None and t.dtype != dtype:
+        raise ValueError(f"expected {dtype}, got {t.dtype}")
+    if numel is not None and t.numel() < numel:
+        raise ValueError(f"tensor too small: {t.numel()} < {numel} elements")
+    return t.data_ptr()
+
+
+def ncoef(T: int) -> int:
+    return (T + 1) * (T + 2) // 2
+
+
+# ---------------------------------------------------------------------------
+# handles
+# ---------------------------------------------------------------------------
+class _Handle:
+    _destroy = None
+
+    def __init__(self, ptr: int):
+        self.ptr = ptr
+
+    def close(self):
+        if self.ptr:
+            getattr(_lib, self._destroy)(self.ptr)
+            self.ptr = None
+
+    def __del__(self):
+        try:
+            self.close()
+        except Exception:
+            pass
+
+
+class ShtPlan(_Handle):
+    _destroy = "sht_plan_destroy"
+
+    def __init__(self, ptr: int):
+        super().__init__(ptr)
+        info = ShtInfo()
+        _check(_lib.sht_plan_query(ptr, ctypes.byref(info)))
+        self.T, self.nlat, self.nlon = info.T, info.nlat, info.nlon
+        self.ncoef, self.max_batch, self.prec = info.ncoef, info.max_batch, info.prec
+        self.device_bytes = info.device_bytes
+        self.mu = [info.mu[i] for i in range(self.nlat)]
+        self.w = [info.w[i] for i in range(self.nlat)]
+
+    @property
+    def grid_dtype(self) -> torch.dtype:
+        return torch.float64 if self.prec == PFSH_FP64 else torch.float32
+
+
+class SweCtx(_Handle):
+    _destroy = "swe_ctx_destroy"
+
+    def __init__(self, ptr: int, plan: ShtPlan, params: SweParams):
+        super().__init__(ptr)
+        self.plan, self.params = plan, params  # keep the plan alive
+
+
+class SdcLevel(_Handle):
+    _destroy = "sdc_level_destroy"
+
+    def __init__(self, ptr: int, ctx: SweCtx, nodes: int, dt: float, max_batch: int):
+        super().__init__(ptr)
+        self.ctx, self.nodes, self.dt, self.max_batch = ctx, nodes, dt, max_batch
+
+
+class Pfasst(_Handle):
+    _destroy = "pfasst_destroy"
+
+    def __init__(self, ptr: int, cfg: PfasstConfig):
+        super().__init__(ptr)
+        self.cfg = cfg
+
+
+# ---------------------------------------------------------------------------
+# ABI functions (same names)
+# ---------------------------------------------------------------------------
+def sht_plan_create(T: int, nlat: int, nlon: int, max_batch: int, prec: int | str = PFSH_FP64) -> ShtPlan:
+    prec = PREC_NAMES[prec] if isinstance(prec, str) else prec
+    h = c_void_p()
+    _check(_lib.sht_plan_create(ctypes.byref(h), T, nlat, nlon, max_batch, prec))
+    return ShtPlan(h.value)
+
+
+def sht_inverse(plan: ShtPlan, spec: torch.Tensor, grid: torch.Tensor, stream=None) -> torch.Tensor:
+    batch = spec.numel() // plan.ncoef
+    _check(_lib.sht_inverse(plan.ptr, _ptr(spec, torch.complex128, batch * plan.ncoef),
+                            _ptr(grid, plan.grid_dtype, batch * plan.nlat * plan.nlon), batch, _stream(stream)))
+    return grid
+
+
+def sht_forward(plan: ShtPlan, grid: torch.Tensor, spec: torch.Tensor, stream=None) -> torch.Tensor:
+    batch = grid.numel() // (plan.nlat * plan.nlon)
+    _check(_lib.sht_forward(plan.ptr, _ptr(grid, plan.grid_dtype, batch * plan.nlat * plan.nlon),
+                            _ptr(spec, torch.complex128, batch * plan.ncoef), batch, _stream(stream)))
+    return spec
+
+
+def swe_ctx_create(plan: ShtPlan, a: float, omega: float, nu: float, phibar: float) -> SweCtx:
+    p = SweParams(a, omega, nu, phibar)
+    h = c_void_p()
+    _check(_lib.swe_ctx_create(ctypes.byref(h), plan.ptr, ctypes.byref(p)))
+    return SweCtx(h.value, plan, p)
+
+
+def swe_rhs(ctx: SweCtx, state: torch.Tensor, fE: torch.Tensor, fI: torch.Tensor | None = None,
+            stream=None) -> None:
+    nc3 = 3 * ctx.plan.ncoef
+    B = state.numel() // nc3
+    _check(_lib.swe_rhs(ctx.ptr, _ptr(state, torch.complex128, B * nc3), _ptr(fE, torch.complex128, B * nc3),
+                        _ptr(fI, torch.complex128, B * nc3), B, _stream(stream)))
+
+
+def swe_implicit_solve(ctx: SweCtx, b: torch.Tensor, x: torch.Tensor, h: float, stream=None) -> None:
+    nc3 = 3 * ctx.plan.ncoef
+    B = b.numel() // nc3
+    _check(_lib.swe_implicit_solve(ctx.ptr, _ptr(b, torch.complex128, B * nc3), _ptr(x, torch.complex128, B * nc3),
+                                   h, B, _stream(stream)))
+
+
+def sdc_level_create(ctx: SweCtx, nodes: int, dt: float, max_batch: int) -> SdcLevel:
+    h = c_void_p()
+    _check(_lib.sdc_level_create(ctypes.byref(h), ctx.ptr, nodes, dt, max_batch))
+    return SdcLevel(h.value, ctx, nodes, dt, max_batch)
+
+
+def sdc_spread(level: SdcLevel, theta0: torch.Tensor, theta: torch.Tensor, fE: torch.Tensor, fI: torch.Tensor,
+               stream=None) -> None:
+    nc3 = 3 * level.ctx.plan.ncoef
+    B = theta0.numel() // nc3
+    n = level.nodes * B * nc3
+    _check(_lib.sdc_spread(level.ptr, _ptr(theta0, torch.complex128, B * nc3), _ptr(theta, torch.complex128, n),
+                           _ptr(fE, torch.complex128, n), _ptr(fI, torch.complex128, n), B, _stream(stream)))
+
+
+def sdc_sweep(level: SdcLevel, theta: torch.Tensor, fE: torch.Tensor, fI: torch.Tensor,
+              tau: torch.Tensor | None = None, stream=None) -> None:
+    nc3 = 3 * level.ctx.plan.ncoef
+    B = theta.numel() // (nc3 * level.nodes)
+    n = level.nodes * B * nc3
+    _check(_lib.sdc_sweep(level.ptr, _ptr(theta, torch.complex128, n), _ptr(fE, torch.complex128, n),
+                          _ptr(fI, torch.complex128, n), _ptr(tau, torch.complex128, n), B, _stream(stream)))
+
+
+def pfasst_create(n_ts: int, fine_nodes: int, coarse_nodes: int, Tf: int, nlat_f: int, nlon_f: int,
+                  Tc: int, nlat_c: int, nlon_c: int, dt: float, a: float, omega: float, nu: float,
+                  phibar: float, prec: int | str = PFSH_FP64) -> Pfasst:
+    prec = PREC_NAMES[prec] if isinstance(prec, str) else prec
+    cfg = PfasstConfig(n_ts, fine_nodes, coarse_nodes, Tf, nlat_f, nlon_f, Tc, nlat_c, nlon_c, dt,
+                       SweParams(a, omega, nu, phibar), prec)
+    h = c_void_p()
+    _check(_lib.pfasst_create(ctypes.byref(h), ctypes.byref(cfg)))
+    return Pfasst(h.value, cfg)
+
+
+def pfasst_set_initial(pf: Pfasst, theta0: torch.Tensor, stream=None) -> None:
+    _check(_lib.pfasst_set_initial(pf.ptr, _ptr(theta0, torch.complex128, 3 * ncoef(pf.cfg.Tf)), _stream(stream)))
+
+
+def pfasst_predict(pf: Pfasst, stream=None) -> None:
+    _check(_lib.pfasst_predict(pf.ptr, _stream(stream)))
+
+
+def pfasst_iteration(pf: Pfasst, last: bool = False, stream=None) -> None:
+    _check(_lib.pfasst_iteration(pf.ptr, 1 if last else 0, _stream(stream)))
+
+
+def pfasst_get(pf: Pfasst, level: int, slice_: int, node: int, out: torch.Tensor, stream=None) -> torch.Tensor:
+    T = pf.cfg.Tf if level == 0 else pf.cfg.Tc
+    _check(_lib.pfasst_get(pf.ptr, level, slice_, node, _ptr(out, torch.complex128, 3 * ncoef(T)), _stream(stream)))
+    return out
+
+
+def pfsh_sync_status(stream=None) -> None:
+    _check(_lib.pfsh_sync_status(_stream(stream)))
+
+
+def pfsh_kernel_launches() -> int:
+    return int(_lib.pfsh_kernel_launches())
+
+
+def pfsh_profiler_enable(on: bool) -> None:
+    _check(_lib.pfsh_profiler_enable(1 if on else 0))
+
+
+def pfsh_profiler_report() -> dict:
+    """{kernel: [launches, total_ms]} of the launches recorded while enabled."""
+    import json
+    need = _lib.pfsh_profiler_report(None, 0)
+    buf = ctypes.create_string_buffer(need + 16)
+    _lib.pfsh_profiler_report(buf, len(buf))
+    return json.loads(buf.value.decode())

@@ -1,0 +1,190 @@
+// Internal declarations of the PFASST-SH CUDA library (not part of the ABI).
+#pragma once
+
+#include <cuda_runtime.h>
+#include <stdint.h>
+
+#include <string>
+#include <vector>
+
+#include "../../include/pfsh.h"
+
+namespace pfsh {
+
+// ---------------------------------------------------------------------------
+// errors
+// ---------------------------------------------------------------------------
+void set_error(const std::string &msg);
+int fail(int code, const std::string &msg);
+int cuda_fail(cudaError_t e, const char *what);
+
+#define PFSH_CUDA(call)                                   \
+  do {                                                    \
+    cudaError_t e_ = (call);                              \
+    if (e_ != cudaSuccess) return ::pfsh::cuda_fail(e_, #call); \
+  } while (0)
+
+#define PFSH_CHECK_LAUNCH(what)                                     \
+  do {                                                              \
+    cudaError_t e_ = cudaGetLastError();                            \
+    if (e_ != cudaSuccess) return ::pfsh::cuda_fail(e_, what);      \
+  } while (0)
+
+// Brackets one kernel launch: counts it and, when the profiler is on,
+// records an event pair on the launching stream.
+struct LaunchScope {
+  LaunchScope(const char *name, cudaStream_t s);
+  ~LaunchScope();
+  const char *name;
+  cudaStream_t stream;
+  int slot;
+};
+#define PFSH_LAUNCH(name, stream) ::pfsh::LaunchScope pfsh_scope_(name, stream)
+
+// sticky device status word shared by every object of the library
+int *device_status();
+enum { ST_OK = 0, ST_TIMEOUT = 1, ST_NUMERIC = 2 };
+
+// ---------------------------------------------------------------------------
+// complex helpers
+// ---------------------------------------------------------------------------
+template <typename R> struct cpx;
+template <> struct cpx<double> { typedef double2 t; };
+template <> struct cpx<float> { typedef float2 t; };
+
+template <typename C> __host__ __device__ __forceinline__ C mk(double x, double y) {
+  C c; c.x = x; c.y = y; return c;
+}
+__device__ __forceinline__ double2 operator+(double2 a, double2 b) { return make_double2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ double2 operator-(double2 a, double2 b) { return make_double2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ double2 operator*(double s, double2 a) { return make_double2(s * a.x, s * a.y); }
+__device__ __forceinline__ float2 operator+(float2 a, float2 b) { return make_float2(a.x + b.x, a.y + b.y); }
+__device__ __forceinline__ float2 operator-(float2 a, float2 b) { return make_float2(a.x - b.x, a.y - b.y); }
+__device__ __forceinline__ float2 operator*(float s, float2 a) { return make_float2(s * a.x, s * a.y); }
+template <typename C> __device__ __forceinline__ C cmul(C a, C b) {
+  C r; r.x = a.x * b.x - a.y * b.y; r.y = a.x * b.y + a.y * b.x; return r;
+}
+template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; return a; }
+template <typename C> __device__ __forceinline__ C times_i(C a) { C r; r.x = -a.y; r.y = a.x; return r; }
+
+// ---------------------------------------------------------------------------
+// triangle indexing
+// ---------------------------------------------------------------------------
+// packed offset of order m in a degree-T triangle (the ABI layout)
+__host__ __device__ __forceinline__ int poff(int T, int m) { return m * (2 * T + 3 - m) / 2; }
+// offset of order m in the extended triangle: m <= T, m <= n <= T+1
+__host__ __device__ __forceinline__ int eoff(int T, int m) { return m * (T + 2) - m * (m - 1) / 2; }
+__host__ __device__ __forceinline__ int ncoef_of(int T) { return (T + 1) * (T + 2) / 2; }
+__host__ __device__ __forceinline__ int next_of(int T) { return (T + 1) * (T + 4) / 2; }
+
+// ---------------------------------------------------------------------------
+// FFT plan (complex length-N transforms, mixed radix Stockham)
+// ---------------------------------------------------------------------------
+constexpr int kMaxPasses = 24;
+struct FftPlan {
+  int N = 0;
+  int npass = 0;
+  int radix[kMaxPasses];
+  double2 *tw64 = nullptr;  // exp(-2 pi i e / N), e = 0..N-1
+  float2 *tw32 = nullptr;
+};
+
+// ---------------------------------------------------------------------------
+// objects behind the opaque ABI handles
+// ---------------------------------------------------------------------------
+}  // namespace pfsh
+
+struct sht_plan {
+  int T, nlat, nlon, nh, ncoef, ne, max_batch, prec;
+  int device;
+  std::vector<double> mu, w;        // host copies (ABI sht_info)
+  double *d_mu = nullptr;           // [nlat]
+  double *d_w = nullptr;            // [nlat]
+  double *d_P = nullptr;            // [ne][nh] FP64 P_n^m(mu_j), j north
+  pfsh::FftPlan fft;
+  // workspace for one pass of at most max_batch fields
+  void *ws = nullptr;
+  size_t ws_bytes = 0;
+  size_t device_bytes = 0;
+  // ws carve-up (FP64 path): X [ne][cols] c128, F [T+1][nlat][cols] c128,
+  // H [T+1][2][nh][cols] c128, Y [ne][cols] c128
+  void *X = nullptr, *F = nullptr, *H = nullptr, *Y = nullptr;
+};
+
+struct swe_ctx {
+  sht_plan *plan;
+  swe_params prm;
+  int max_states;     // states per RHS pass (plan->max_batch / 5)
+};
+
+struct sdc_level {
+  swe_ctx *ctx;
+  int nodes;          // M + 1
+  double dt;
+  int max_batch;
+  double tau_nodes[16];
+  double Q[16][16], QE[16][16], QI[16][16];
+  double *d_old = nullptr;   // [M][max_batch][3][ncoef] c128: node-update constants
+};
+
+struct pfasst {
+  pfasst_config cfg;
+  sht_plan *plan_f = nullptr, *plan_c = nullptr;
+  swe_ctx *ctx_f = nullptr, *ctx_c = nullptr;
+  sdc_level *lev_f = nullptr, *lev_c = nullptr;
+  int Mf, Mc;
+  size_t sf, sc;              // doubles per state (3*ncoef*2) fine / coarse
+  double *th_f, *fe_f, *fi_f; // [Mf+1][n_ts][state]
+  double *th_c, *fe_c, *fi_c; // [Mc+1][n_ts][state]
+  double *th_cs, *fe_cs, *fi_cs; // saved restriction (tilde) [Mc+1][n_ts][state]
+  double *tau;                // [Mc+1][n_ts][coarse state]
+  double *sent;               // [n_ts][fine state]
+  double *base_c;             // [n_ts][coarse state] restricted initial value
+  double *theta0;             // [fine state]
+  double Rt[16][16], Pt[16][16];   // time restriction / interpolation
+};
+
+namespace pfsh {
+
+// ---------------------------------------------------------------------------
+// kernels / launchers (defined in the .cu files)
+// ---------------------------------------------------------------------------
+int fft_plan_init(FftPlan &f, int N);
+void fft_plan_free(FftPlan &f);
+
+// Legendre table generation (FP64 recurrence on the device)
+int legendre_table_build(sht_plan *p, cudaStream_t s);
+
+// transforms on the plan's workspace (cols = number of complex columns)
+int synth_f64(const sht_plan *p, int cols, cudaStream_t s);       // X -> F
+int analysis_f64(const sht_plan *p, int cols, cudaStream_t s);    // H -> Y
+int ifft_rows(const sht_plan *p, int cols, void *grid, cudaStream_t s);        // F -> grid
+int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s);   // grid -> H
+int grid_rhs(const sht_plan *p, int B, const swe_params &prm, cudaStream_t s); // F -> H (RHS)
+
+// spectral pre/post processing
+int spec_to_X(const sht_plan *p, const double *spec, int batch, cudaStream_t s);
+int Y_to_spec(const sht_plan *p, double *spec, int batch, cudaStream_t s);
+int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &prm, cudaStream_t s);
+int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI, int B,
+                 const swe_params &prm, cudaStream_t s);
+int implicit_solve_launch(int T, const double *b, double *x, double h, int B,
+                          const swe_params &prm, cudaStream_t s);
+
+// internal RHS on a contiguous batch (chunks over ctx->max_states)
+int rhs_eval(swe_ctx *c, const double *state, double *fE, double *fI, int B, cudaStream_t s);
+
+// SDC pieces: node arrays are [nodes][..] with a node stride (in doubles)
+int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const double *tau,
+                      size_t node_stride, int B, cudaStream_t s);
+int sdc_build_matrices(sdc_level *l, int nodes);
+void lagrange_matrix(const double *src, int ns, const double *dst, int nd, double out[16][16]);
+
+// PFASST transfer kernels
+int restrict_launch(const double *Rt, int nf, int nc, const double *xf, size_t fstride,
+                    double *xc, size_t cstride, int Tf, int Tc, int B, cudaStream_t s);
+int fas_launch(const pfasst *pf, cudaStream_t s);
+int interp_increment_launch(const pfasst *pf, cudaStream_t s);
+int node0_update_launch(const pfasst *pf, cudaStream_t s);
+
+}  // namespace pfsh

@@ -1,0 +1,400 @@
+// Two-level PFASST over n_ts time slices held on one GPU (Sections 5.1.2,
+// 5.2, 5.3 and Algorithm 1).
+//
+// The paper's processors P_n become slice indices of node-major arrays
+// [node][slice][3][ncoef]; a "send" to the next processor is a device copy.
+// Step A (fine sweep) and Step B (restriction, coarse F, FAS) run batched
+// over all slices; Step C (coarse sweeps) is a chain in slice order; Step D
+// (interpolation of increments, new initial values, node-0 F) is batched.
+#include <math.h>
+
+#include <algorithm>
+#include <new>
+
+#include "internal.cuh"
+
+namespace pfsh {
+
+struct Mat16 {
+  double v[16][16];
+};
+
+__device__ __forceinline__ int tri_m2(int idx, int T) {
+  const float b = 2.f * T + 3.f;
+  int m = (int)((b - sqrtf(fmaxf(b * b - 8.f * idx, 0.f))) * 0.5f);
+  m = max(0, min(m, T));
+  while (m > 0 && poff(T, m) > idx) --m;
+  while (m < T && poff(T, m + 1) <= idx) ++m;
+  return m;
+}
+
+// tau_c[i] = dt D( sum_k Rt[i][k] sum_j Qf[k][j] F_f,j ) - dt sum_j Qc[i][j] F_c,j
+// (FAS correction of Eq. tau_term_level_l+1 with tau_f = 0; the Theta terms
+// of A_c(R Theta_f) - R A_f(Theta_f) cancel.)
+__global__ void k_fas(int Tf, int Tc, int nts, int nf, int ncn, double dt, Mat16 RQf, Mat16 Qc,
+                      const double2 *__restrict__ fe_f, const double2 *__restrict__ fi_f,
+                      const double2 *__restrict__ fe_c, const double2 *__restrict__ fi_c,
+                      double2 *__restrict__ tau) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  const int ncc = ncoef_of(Tc), ncf = ncoef_of(Tf);
+  if (idx >= ncc) return;
+  const int m = tri_m2(idx, Tc);
+  const int fidx = poff(Tf, m) + (idx - poff(Tc, m));
+  const size_t fs = (size_t)nts * 3 * ncf, cs = (size_t)nts * 3 * ncc;
+  for (int f = 0; f < 3; ++f) {
+    const size_t fo = (size_t)b * 3 * ncf + (size_t)f * ncf + fidx;
+    const size_t co = (size_t)b * 3 * ncc + (size_t)f * ncc + idx;
+    double2 Ff[16], Fc[16];
+    for (int k = 0; k < nf; ++k) Ff[k] = fe_f[k * fs + fo] + fi_f[k * fs + fo];
+    for (int k = 0; k < ncn; ++k) Fc[k] = fe_c[k * cs + co] + fi_c[k * cs + co];
+    for (int i = 0; i < ncn; ++i) {
+      double2 a = make_double2(0.0, 0.0);
+      for (int k = 0; k < nf; ++k) {
+        a.x += RQf.v[i][k] * Ff[k].x;
+        a.y += RQf.v[i][k] * Ff[k].y;
+      }
+      double2 c = make_double2(0.0, 0.0);
+      for (int k = 0; k < ncn; ++k) {
+        c.x += Qc.v[i][k] * Fc[k].x;
+        c.y += Qc.v[i][k] * Fc[k].y;
+      }
+      tau[i * cs + co] = make_double2(dt * a.x - dt * c.x, dt * a.y - dt * c.y);
+    }
+  }
+}
+
+// x_f[k] += sum_i Pt[k][i] Z(x_c[i] - x_cs[i]) for fine nodes k >= kmin and
+// the coefficients the coarse level holds (zero-padding elsewhere).
+__global__ void k_interp_inc(int Tf, int Tc, int nts, int nf, int ncn, int kmin, Mat16 Pt,
+                             const double2 *__restrict__ xc, const double2 *__restrict__ xcs,
+                             double2 *__restrict__ xf) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  const int ncc = ncoef_of(Tc), ncf = ncoef_of(Tf);
+  if (idx >= ncc) return;
+  const int m = tri_m2(idx, Tc);
+  const int fidx = poff(Tf, m) + (idx - poff(Tc, m));
+  const size_t fs = (size_t)nts * 3 * ncf, cs = (size_t)nts * 3 * ncc;
+  for (int f = 0; f < 3; ++f) {
+    const size_t fo = (size_t)b * 3 * ncf + (size_t)f * ncf + fidx;
+    const size_t co = (size_t)b * 3 * ncc + (size_t)f * ncc + idx;
+    double2 d[16];
+    for (int i = 0; i < ncn; ++i) d[i] = xc[i * cs + co] - xcs[i * cs + co];
+    for (int k = kmin; k < nf; ++k) {
+      double2 a = make_double2(0.0, 0.0);
+      for (int i = 0; i < ncn; ++i) {
+        a.x += Pt.v[k][i] * d[i].x;
+        a.y += Pt.v[k][i] * d[i].y;
+      }
+      double2 v = xf[k * fs + fo];
+      xf[k * fs + fo] = v + a;
+    }
+  }
+}
+
+// Predictor: x_f[k][b] = theta0 + sum_i Pt[k][i] Z(x_c[i][b] - base_c[b])
+__global__ void k_pred_interp(int Tf, int Tc, int nts, int nf, int ncn, Mat16 Pt, const double2 *__restrict__ th0,
+                              const double2 *__restrict__ xc, const double2 *__restrict__ basec,
+                              double2 *__restrict__ xf) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  const int ncc = ncoef_of(Tc), ncf = ncoef_of(Tf);
+  if (idx >= ncf) return;
+  const int m = tri_m2(idx, Tf);
+  const int n = m + (idx - poff(Tf, m));
+  const size_t fs = (size_t)nts * 3 * ncf, cs = (size_t)nts * 3 * ncc;
+  const bool low = (n <= Tc);
+  const int cidx = low ? poff(Tc, m) + (n - m) : 0;
+  for (int f = 0; f < 3; ++f) {
+    const double2 base = th0[(size_t)f * ncf + idx];
+    double2 d[16];
+    if (low) {
+      const size_t co = (size_t)b * 3 * ncc + (size_t)f * ncc + cidx;
+      const double2 bc = basec[(size_t)b * 3 * ncc + (size_t)f * ncc + cidx];
+      for (int i = 0; i < ncn; ++i) d[i] = xc[i * cs + co] - bc;
+    }
+    for (int k = 0; k < nf; ++k) {
+      double2 v = base;
+      if (low) {
+        double2 a = make_double2(0.0, 0.0);
+        for (int i = 0; i < ncn; ++i) {
+          a.x += Pt.v[k][i] * d[i].x;
+          a.y += Pt.v[k][i] * d[i].y;
+        }
+        v = v + a;
+      }
+      xf[k * fs + (size_t)b * 3 * ncf + (size_t)f * ncf + idx] = v;
+    }
+  }
+}
+
+// Step D, last line of Algorithm 1: theta_f^{n,0} = sent^{n-1} +
+// Z(theta_c^{n,0} - D sent^{n-1}) for slices n >= 1.
+__global__ void k_node0(int Tf, int Tc, int nts, const double2 *__restrict__ sent, const double2 *__restrict__ thc0,
+                        double2 *__restrict__ thf0) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y + 1;
+  const int ncc = ncoef_of(Tc), ncf = ncoef_of(Tf);
+  if (idx >= ncf) return;
+  const int m = tri_m2(idx, Tf);
+  const int n = m + (idx - poff(Tf, m));
+  for (int f = 0; f < 3; ++f) {
+    double2 v = sent[(size_t)(b - 1) * 3 * ncf + (size_t)f * ncf + idx];
+    if (n <= Tc) {
+      const double2 c = thc0[(size_t)b * 3 * ncc + (size_t)f * ncc + poff(Tc, m) + (n - m)];
+      v = v + (c - v);
+    }
+    thf0[(size_t)b * 3 * ncf + (size_t)f * ncf + idx] = v;
+  }
+}
+
+}  // namespace pfsh
+
+using namespace pfsh;
+
+static void pf_free(pfasst *pf) {
+  if (!pf) return;
+  double *bufs[] = {pf->th_f, pf->fe_f, pf->fi_f, pf->th_c, pf->fe_c, pf->fi_c, pf->th_cs,
+                    pf->fe_cs, pf->fi_cs, pf->tau, pf->sent, pf->base_c, pf->theta0};
+  for (double *b : bufs)
+    if (b) cudaFree(b);
+  sdc_level_destroy(pf->lev_f);
+  sdc_level_destroy(pf->lev_c);
+  swe_ctx_destroy(pf->ctx_f);
+  swe_ctx_destroy(pf->ctx_c);
+  sht_plan_destroy(pf->plan_f);
+  sht_plan_destroy(pf->plan_c);
+  delete pf;
+}
+
+extern "C" int pfasst_create(pfasst **out, const pfasst_config *cfg) {
+  if (!out || !cfg) return fail(PFSH_EINVAL, "pfasst_create: NULL argument");
+  *out = nullptr;
+  const pfasst_config &c = *cfg;
+  if (c.n_ts < 1 || c.fine_nodes < 2 || c.fine_nodes > 9 || c.coarse_nodes < 2 || c.coarse_nodes > 9)
+    return fail(PFSH_EINVAL, "pfasst_create: need n_ts >= 1 and 2..9 nodes per level");
+  if (c.Tc > c.Tf || c.Tc < 1) return fail(PFSH_EINVAL, "pfasst_create: need 1 <= Tc <= Tf");
+  if (!(c.dt > 0)) return fail(PFSH_EINVAL, "pfasst_create: dt must be > 0");
+  pfasst *pf = new (std::nothrow) pfasst();
+  if (!pf) return fail(PFSH_ENOMEM, "pfasst_create");
+  pf->cfg = c;
+  pf->Mf = c.fine_nodes - 1;
+  pf->Mc = c.coarse_nodes - 1;
+  const int nts = c.n_ts;
+  // fine passes: sweep batches of n_ts states; coarse: (Mc+1) n_ts states in Step B
+  int mb_f = 5 * std::min(nts, 32);
+  int mb_c = 5 * std::min(nts * c.coarse_nodes, 96);
+  int rc;
+  if ((rc = sht_plan_create(&pf->plan_f, c.Tf, c.nlat_f, c.nlon_f, mb_f, c.prec)) ||
+      (rc = sht_plan_create(&pf->plan_c, c.Tc, c.nlat_c, c.nlon_c, mb_c, c.prec)) ||
+      (rc = swe_ctx_create(&pf->ctx_f, pf->plan_f, &c.phys)) ||
+      (rc = swe_ctx_create(&pf->ctx_c, pf->plan_c, &c.phys)) ||
+      (rc = sdc_level_create(&pf->lev_f, pf->ctx_f, c.fine_nodes, c.dt, nts)) ||
+      (rc = sdc_level_create(&pf->lev_c, pf->ctx_c, c.coarse_nodes, c.dt, nts))) {
+    pf_free(pf);
+    return rc;
+  }
+  pf->sf = (size_t)3 * ncoef_of(c.Tf) * 2;
+  pf->sc = (size_t)3 * ncoef_of(c.Tc) * 2;
+  struct A {
+    double **p;
+    size_t n;
+  } allocs[] = {{&pf->th_f, (size_t)(pf->Mf + 1) * nts * pf->sf}, {&pf->fe_f, (size_t)(pf->Mf + 1) * nts * pf->sf},
+                {&pf->fi_f, (size_t)(pf->Mf + 1) * nts * pf->sf}, {&pf->th_c, (size_t)(pf->Mc + 1) * nts * pf->sc},
+                {&pf->fe_c, (size_t)(pf->Mc + 1) * nts * pf->sc}, {&pf->fi_c, (size_t)(pf->Mc + 1) * nts * pf->sc},
+                {&pf->th_cs, (size_t)(pf->Mc + 1) * nts * pf->sc}, {&pf->fe_cs, (size_t)(pf->Mc + 1) * nts * pf->sc},
+                {&pf->fi_cs, (size_t)(pf->Mc + 1) * nts * pf->sc}, {&pf->tau, (size_t)(pf->Mc + 1) * nts * pf->sc},
+                {&pf->sent, (size_t)nts * pf->sf},                {&pf->base_c, (size_t)nts * pf->sc},
+                {&pf->theta0, pf->sf}};
+  for (auto &a : allocs) {
+    if (cudaMalloc(a.p, a.n * sizeof(double)) != cudaSuccess) {
+      cudaGetLastError();
+      pf_free(pf);
+      return fail(PFSH_ENOMEM, "pfasst_create: device arrays");
+    }
+    cudaMemset(*a.p, 0, a.n * sizeof(double));
+  }
+  lagrange_matrix(pf->lev_f->tau_nodes, c.fine_nodes, pf->lev_c->tau_nodes, c.coarse_nodes, pf->Rt);
+  lagrange_matrix(pf->lev_c->tau_nodes, c.coarse_nodes, pf->lev_f->tau_nodes, c.fine_nodes, pf->Pt);
+  *out = pf;
+  return PFSH_OK;
+}
+
+extern "C" int pfasst_destroy(pfasst *pf) {
+  if (!pf) return PFSH_OK;
+  cudaDeviceSynchronize();
+  pf_free(pf);
+  return PFSH_OK;
+}
+
+extern "C" int pfasst_set_initial(pfasst *pf, const double *theta0, pfsh_stream_t stream) {
+  if (!pf || !theta0) return fail(PFSH_EINVAL, "pfasst_set_initial: NULL argument");
+  PFSH_CUDA(cudaMemcpyAsync(pf->theta0, theta0, pf->sf * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return PFSH_OK;
+}
+
+static int restrict_all(pfasst *pf, const double *xf, double *xc, cudaStream_t s) {
+  const int nts = pf->cfg.n_ts;
+  double R[16 * 16];
+  for (int i = 0; i < 16; ++i)
+    for (int k = 0; k < 16; ++k) R[i * 16 + k] = pf->Rt[i][k];
+  return restrict_launch(R, pf->Mf + 1, pf->Mc + 1, xf, (size_t)nts * pf->sf, xc, (size_t)nts * pf->sc,
+                         pf->cfg.Tf, pf->cfg.Tc, nts, s);
+}
+
+extern "C" int pfasst_predict(pfasst *pf, pfsh_stream_t stream) {
+  if (!pf) return fail(PFSH_EINVAL, "pfasst_predict: NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int nts = pf->cfg.n_ts, Mc = pf->Mc, Mf = pf->Mf;
+  const size_t sc = pf->sc, sf = pf->sf;
+  const size_t cnode = (size_t)nts * sc;
+  int rc;
+  // restricted broadcast value into base_c[0], then to every slice and node
+  double R1[16 * 16] = {0};
+  R1[0] = 1.0;
+  if ((rc = restrict_launch(R1, 1, 1, pf->theta0, sf, pf->base_c, sc, pf->cfg.Tf, pf->cfg.Tc, 1, s))) return rc;
+  for (int n = 1; n < nts; ++n)
+    PFSH_CUDA(cudaMemcpyAsync(pf->base_c + n * sc, pf->base_c, sc * 8, cudaMemcpyDeviceToDevice, s));
+  if ((rc = rhs_eval(pf->ctx_c, pf->base_c, pf->fe_c, pf->fi_c, 1, s))) return rc;
+  for (int n = 1; n < nts; ++n) {
+    PFSH_CUDA(cudaMemcpyAsync(pf->fe_c + n * sc, pf->fe_c, sc * 8, cudaMemcpyDeviceToDevice, s));
+    PFSH_CUDA(cudaMemcpyAsync(pf->fi_c + n * sc, pf->fi_c, sc * 8, cudaMemcpyDeviceToDevice, s));
+  }
+  for (int i = 0; i <= Mc; ++i) {
+    PFSH_CUDA(cudaMemcpyAsync(pf->th_c + i * cnode, pf->base_c, cnode * 8, cudaMemcpyDeviceToDevice, s));
+    if (i) {
+      PFSH_CUDA(cudaMemcpyAsync(pf->fe_c + i * cnode, pf->fe_c, cnode * 8, cudaMemcpyDeviceToDevice, s));
+      PFSH_CUDA(cudaMemcpyAsync(pf->fi_c + i * cnode, pf->fi_c, cnode * 8, cudaMemcpyDeviceToDevice, s));
+    }
+  }
+  // rounds: slices n >= j take slice n-1's round j-1 end value and sweep
+  for (int j = 0; j < nts; ++j) {
+    const int cnt = nts - j;
+    if (j > 0) {
+      PFSH_CUDA(cudaMemcpyAsync(pf->th_c + j * sc, pf->th_c + Mc * cnode + (j - 1) * sc, cnt * sc * 8,
+                                cudaMemcpyDeviceToDevice, s));
+      if ((rc = rhs_eval(pf->ctx_c, pf->th_c + j * sc, pf->fe_c + j * sc, pf->fi_c + j * sc, cnt, s))) return rc;
+    }
+    if ((rc = sdc_sweep_strided(pf->lev_c, pf->th_c + j * sc, pf->fe_c + j * sc, pf->fi_c + j * sc, nullptr, cnode,
+                                cnt, s)))
+      return rc;
+  }
+  // fine prediction: theta0 + interpolated coarse increment, then fine F everywhere
+  Mat16 P;
+  for (int i = 0; i < 16; ++i)
+    for (int k = 0; k < 16; ++k) P.v[i][k] = pf->Pt[i][k];
+  dim3 g((ncoef_of(pf->cfg.Tf) + 255) / 256, nts);
+  {
+    PFSH_LAUNCH("k_pred_interp", s);
+    k_pred_interp<<<g, 256, 0, s>>>(pf->cfg.Tf, pf->cfg.Tc, nts, Mf + 1, Mc + 1, P, (const double2 *)pf->theta0,
+                                    (const double2 *)pf->th_c, (const double2 *)pf->base_c, (double2 *)pf->th_f);
+  }
+  PFSH_CHECK_LAUNCH("k_pred_interp");
+  return rhs_eval(pf->ctx_f, pf->th_f, pf->fe_f, pf->fi_f, (Mf + 1) * nts, s);
+}
+
+extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
+  if (!pf) return fail(PFSH_EINVAL, "pfasst_iteration: NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const pfasst_config &c = pf->cfg;
+  const int nts = c.n_ts, Mc = pf->Mc, Mf = pf->Mf;
+  const size_t sc = pf->sc, sf = pf->sf;
+  const size_t cnode = (size_t)nts * sc, fnode = (size_t)nts * sf;
+  int rc;
+  // A) fine sweep of every slice
+  if ((rc = sdc_sweep_strided(pf->lev_f, pf->th_f, pf->fe_f, pf->fi_f, nullptr, fnode, nts, s))) return rc;
+  if (last) return PFSH_OK;
+  PFSH_CUDA(cudaMemcpyAsync(pf->sent, pf->th_f + Mf * fnode, fnode * 8, cudaMemcpyDeviceToDevice, s));
+  // B) restrict, coarse F at every node, save, FAS
+  if ((rc = restrict_all(pf, pf->th_f, pf->th_c, s))) return rc;
+  if ((rc = rhs_eval(pf->ctx_c, pf->th_c, pf->fe_c, pf->fi_c, (Mc + 1) * nts, s))) return rc;
+  const size_t cbytes = (size_t)(Mc + 1) * cnode * 8;
+  PFSH_CUDA(cudaMemcpyAsync(pf->th_cs, pf->th_c, cbytes, cudaMemcpyDeviceToDevice, s));
+  PFSH_CUDA(cudaMemcpyAsync(pf->fe_cs, pf->fe_c, cbytes, cudaMemcpyDeviceToDevice, s));
+  PFSH_CUDA(cudaMemcpyAsync(pf->fi_cs, pf->fi_c, cbytes, cudaMemcpyDeviceToDevice, s));
+  {
+    Mat16 RQf, Qc;
+    for (int i = 0; i < 16; ++i)
+      for (int k = 0; k < 16; ++k) {
+        RQf.v[i][k] = 0.0;
+        Qc.v[i][k] = 0.0;
+      }
+    for (int i = 0; i <= Mc; ++i) {
+      for (int k = 0; k <= Mf; ++k) {
+        double acc = 0.0;
+        for (int q = 0; q <= Mf; ++q) acc += pf->Rt[i][q] * pf->lev_f->Q[q][k];
+        RQf.v[i][k] = acc;
+      }
+      for (int k = 0; k <= Mc; ++k) Qc.v[i][k] = pf->lev_c->Q[i][k];
+    }
+    dim3 g((ncoef_of(c.Tc) + 255) / 256, nts);
+    {
+      PFSH_LAUNCH("k_fas", s);
+      k_fas<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, c.dt, RQf, Qc, (const double2 *)pf->fe_f,
+                              (const double2 *)pf->fi_f, (const double2 *)pf->fe_c, (const double2 *)pf->fi_c,
+                              (double2 *)pf->tau);
+    }
+    PFSH_CHECK_LAUNCH("k_fas");
+  }
+  // C) coarse chain in slice order
+  for (int n = 0; n < nts; ++n) {
+    if (n > 0) {
+      PFSH_CUDA(cudaMemcpyAsync(pf->th_c + n * sc, pf->th_c + Mc * cnode + (n - 1) * sc, sc * 8,
+                                cudaMemcpyDeviceToDevice, s));
+      if ((rc = rhs_eval(pf->ctx_c, pf->th_c + n * sc, pf->fe_c + n * sc, pf->fi_c + n * sc, 1, s))) return rc;
+    }
+    if ((rc = sdc_sweep_strided(pf->lev_c, pf->th_c + n * sc, pf->fe_c + n * sc, pf->fi_c + n * sc,
+                                pf->tau + n * sc, cnode, 1, s)))
+      return rc;
+  }
+  // D) interpolate increments (nodes >= 1), new initial values, node-0 F
+  {
+    Mat16 P;
+    for (int i = 0; i < 16; ++i)
+      for (int k = 0; k < 16; ++k) P.v[i][k] = pf->Pt[i][k];
+    dim3 g((ncoef_of(c.Tc) + 255) / 256, nts);
+    const double *xc[3] = {pf->th_c, pf->fe_c, pf->fi_c};
+    const double *xs[3] = {pf->th_cs, pf->fe_cs, pf->fi_cs};
+    double *xf[3] = {pf->th_f, pf->fe_f, pf->fi_f};
+    for (int q = 0; q < 3; ++q) {
+      {
+        PFSH_LAUNCH("k_interp_inc", s);
+        k_interp_inc<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, 1, P, (const double2 *)xc[q],
+                                       (const double2 *)xs[q], (double2 *)xf[q]);
+      }
+      PFSH_CHECK_LAUNCH("k_interp_inc");
+    }
+    if (nts > 1) {
+      dim3 g0((ncoef_of(c.Tf) + 255) / 256, nts - 1);
+      {
+        PFSH_LAUNCH("k_node0", s);
+        k_node0<<<g0, 256, 0, s>>>(c.Tf, c.Tc, nts, (const double2 *)pf->sent, (const double2 *)pf->th_c,
+                                   (double2 *)pf->th_f);
+      }
+      PFSH_CHECK_LAUNCH("k_node0");
+    }
+  }
+  return rhs_eval(pf->ctx_f, pf->th_f, pf->fe_f, pf->fi_f, nts, s);
+}
+
+extern "C" int pfasst_get(pfasst *pf, int level, int slice, int node, double *out, pfsh_stream_t stream) {
+  if (!pf || !out) return fail(PFSH_EINVAL, "pfasst_get: NULL argument");
+  const int nts = pf->cfg.n_ts;
+  if (slice < 0 || slice >= nts) return fail(PFSH_EINVAL, "pfasst_get: slice out of range");
+  const double *src;
+  size_t st;
+  if (level == 0) {
+    if (node < 0 || node > pf->Mf) return fail(PFSH_EINVAL, "pfasst_get: node out of range");
+    st = pf->sf;
+    src = pf->th_f + ((size_t)node * nts + slice) * st;
+  } else if (level == 1) {
+    if (node < 0 || node > pf->Mc) return fail(PFSH_EINVAL, "pfasst_get: node out of range");
+    st = pf->sc;
+    src = pf->th_c + ((size_t)node * nts + slice) * st;
+  } else {
+    return fail(PFSH_EINVAL, "pfasst_get: level must be 0 or 1");
+  }
+  PFSH_CUDA(cudaMemcpyAsync(out, src, st * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
+  return PFSH_OK;
+}

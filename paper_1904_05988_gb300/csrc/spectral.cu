@@ -1,0 +1,423 @@
+// Spectral-space FP64 kernels: velocity recovery and assembly of the
+// nonlinear term (Section 2), the implicit solve (Section 5.4), the IMEX-SDC
+// node update (Section 5.1.1) and the FAS / space-time transfer operators
+// (Sections 5.1.2 and 5.3).  All are element-wise over triangular spectral
+// arrays and bound by HBM traffic or FP64 issue rate.
+#include "internal.cuh"
+
+namespace pfsh {
+
+// order m of packed index idx in a degree-T triangle (largest m with poff <= idx)
+__device__ __forceinline__ int tri_m(int idx, int T) {
+  const float b = 2.f * T + 3.f;
+  int m = (int)((b - sqrtf(fmaxf(b * b - 8.f * idx, 0.f))) * 0.5f);
+  m = max(0, min(m, T));
+  while (m > 0 && poff(T, m) > idx) --m;
+  while (m < T && poff(T, m + 1) <= idx) ++m;
+  return m;
+}
+
+__device__ __forceinline__ double eps_nm(int n, int m) {
+  if (n <= m) return 0.0;
+  return sqrt(((double)n * n - (double)m * m) / (4.0 * (double)n * n - 1.0));
+}
+
+// ---------------------------------------------------------------------------
+// plain transforms: spec [b][ncoef] <-> X/Y [ext row][b]
+// ---------------------------------------------------------------------------
+__global__ void k_spec_to_X(int T, int ne, int batch, const double2 *__restrict__ spec, double2 *__restrict__ X) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  if (idx >= ne) return;
+  const int m = tri_m(idx, T + 1);  // extended triangle == packed triangle of degree T+1
+  const int n = m + (idx - poff(T + 1, m));
+  double2 v = make_double2(0.0, 0.0);
+  if (n <= T) {
+    v = spec[(size_t)b * ncoef_of(T) + poff(T, m) + (n - m)];
+    if (m == 0) v.y = 0.0;
+  }
+  X[(size_t)idx * batch + b] = v;
+}
+
+__global__ void k_Y_to_spec(int T, int batch, const double2 *__restrict__ Y, double2 *__restrict__ spec) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  const int nc = ncoef_of(T);
+  if (idx >= nc) return;
+  const int m = tri_m(idx, T);
+  const int n = m + (idx - poff(T, m));
+  double2 v = Y[(size_t)(poff(T + 1, m) + (n - m)) * batch + b];
+  if (m == 0) v.y = 0.0;
+  spec[(size_t)b * nc + idx] = v;
+}
+
+int spec_to_X(const sht_plan *p, const double *spec, int batch, cudaStream_t s) {
+  dim3 g((p->ne + 255) / 256, batch);
+  {
+    PFSH_LAUNCH("k_spec_to_X", s);
+    k_spec_to_X<<<g, 256, 0, s>>>(p->T, p->ne, batch, (const double2 *)spec, (double2 *)p->X);
+  }
+  PFSH_CHECK_LAUNCH("k_spec_to_X");
+  return PFSH_OK;
+}
+
+int Y_to_spec(const sht_plan *p, double *spec, int batch, cudaStream_t s) {
+  dim3 g((p->ncoef + 255) / 256, batch);
+  {
+    PFSH_LAUNCH("k_Y_to_spec", s);
+    k_Y_to_spec<<<g, 256, 0, s>>>(p->T, batch, (const double2 *)p->Y, (double2 *)spec);
+  }
+  PFSH_CHECK_LAUNCH("k_Y_to_spec");
+  return PFSH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// RHS prep: state [b][3][ncoef] -> X[ext row][b*4 + f], f = eta, Phi', U, V
+//   eta  = zeta + 2 Omega mu           (mu = P_1^0 / sqrt(3/2))
+//   Phi' = Phi - Phibar                 (1 = sqrt(2) P_0^0)
+//   psi_n = -a^2 zeta_n / (n(n+1)), chi_n likewise (n >= 1; 0 at n = 0)
+//   U_n = [(n-1) eps_n psi_{n-1} - (n+2) eps_{n+1} psi_{n+1} + i m chi_n] / a
+//   V_n = [i m psi_n - (n-1) eps_n chi_{n-1} + (n+2) eps_{n+1} chi_{n+1}] / a
+// ---------------------------------------------------------------------------
+__global__ void k_rhs_prep(int T, int ne, int B, double a, double omega, double phibar,
+                           const double2 *__restrict__ state, double2 *__restrict__ X) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  if (idx >= ne) return;
+  const int nc = ncoef_of(T);
+  const int m = tri_m(idx, T + 1);
+  const int n = m + (idx - poff(T + 1, m));
+  const double2 *Phi = state + (size_t)b * 3 * nc;
+  const double2 *zeta = Phi + nc;
+  const double2 *delta = Phi + 2 * nc;
+  const int base = poff(T, m) - m;  // packed index of (m, n') is base + n'
+  const double a2 = a * a;
+  auto psi_chi = [&](int nn, double2 *ps, double2 *ch) {
+    if (nn < m || nn > T || nn == 0) {
+      *ps = make_double2(0.0, 0.0);
+      *ch = make_double2(0.0, 0.0);
+      return;
+    }
+    const double f = -a2 / ((double)nn * (nn + 1));
+    double2 z = zeta[base + nn], d = delta[base + nn];
+    if (m == 0) { z.y = 0.0; d.y = 0.0; }
+    *ps = f * z;
+    *ch = f * d;
+  };
+  double2 eta = make_double2(0.0, 0.0), php = make_double2(0.0, 0.0);
+  if (n <= T) {
+    eta = zeta[base + n];
+    php = Phi[base + n];
+    if (m == 0) {
+      eta.y = 0.0;
+      php.y = 0.0;
+      if (n == 1) eta.x += 2.0 * omega / sqrt(1.5);
+      if (n == 0) php.x -= sqrt(2.0) * phibar;
+    }
+  }
+  double2 ps_m, ch_m, ps_0, ch_0, ps_p, ch_p;
+  psi_chi(n - 1, &ps_m, &ch_m);
+  psi_chi(n, &ps_0, &ch_0);
+  psi_chi(n + 1, &ps_p, &ch_p);
+  const double cm = (n - 1) * eps_nm(n, m);
+  const double cp = (n + 2) * eps_nm(n + 1, m);
+  const double inva = 1.0 / a;
+  double2 U, V;
+  U.x = (cm * ps_m.x - cp * ps_p.x - m * ch_0.y) * inva;
+  U.y = (cm * ps_m.y - cp * ps_p.y + m * ch_0.x) * inva;
+  V.x = (-m * ps_0.y - cm * ch_m.x + cp * ch_p.x) * inva;
+  V.y = (m * ps_0.x - cm * ch_m.y + cp * ch_p.y) * inva;
+  double2 *row = X + (size_t)idx * (4 * B) + b * 4;
+  row[0] = eta;
+  row[1] = php;
+  row[2] = U;
+  row[3] = V;
+}
+
+int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &prm, cudaStream_t s) {
+  dim3 g((p->ne + 255) / 256, B);
+  {
+    PFSH_LAUNCH("k_rhs_prep", s);
+    k_rhs_prep<<<g, 256, 0, s>>>(p->T, p->ne, B, prm.a, prm.omega, prm.phibar, (const double2 *)state,
+                                 (double2 *)p->X);
+  }
+  PFSH_CHECK_LAUNCH("k_rhs_prep");
+  return PFSH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// RHS assembly: Y[ext row][b*5 + f] (f = A1, B1, A2, B2, E analysed with the
+// 1/(1-mu^2) factor) -> F_E, and F_I from the state:
+//   div_n  = [i m A_n + n eps_{n+1} B_{n+1} - (n+1) eps_n B_{n-1}] / a
+//   curl_n = [i m B_n - n eps_{n+1} A_{n+1} + (n+1) eps_n A_{n-1}] / a
+//   F_E = [-div(A2,B2), -div(A1,B1), curl(A1,B1) + n(n+1)/a^2 E]
+//   F_I = [-Phibar delta - nu k Phi, -nu k zeta, k Phi - nu k delta], k = n(n+1)/a^2
+// ---------------------------------------------------------------------------
+__global__ void k_rhs_assemble(int T, int B, double a, double nu, double phibar,
+                               const double2 *__restrict__ Y, const double2 *__restrict__ state,
+                               double2 *__restrict__ fE, double2 *__restrict__ fI) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  const int nc = ncoef_of(T);
+  if (idx >= nc) return;
+  const int m = tri_m(idx, T);
+  const int n = m + (idx - poff(T, m));
+  const int cols = 5 * B;
+  const size_t r0 = (size_t)(poff(T + 1, m) + (n - m));
+  auto y = [&](size_t row, int f) { return Y[row * cols + b * 5 + f]; };
+  const double e1 = eps_nm(n + 1, m), e0 = eps_nm(n, m);
+  const double cu = n * e1, cd = (n + 1) * e0;
+  const double2 z = make_double2(0.0, 0.0);
+  double2 A1 = y(r0, 0), B1 = y(r0, 1), A2 = y(r0, 2), B2 = y(r0, 3), E = y(r0, 4);
+  double2 A1u = y(r0 + 1, 0), B1u = y(r0 + 1, 1), B2u = y(r0 + 1, 3);
+  double2 A1d = n > m ? y(r0 - 1, 0) : z, B1d = n > m ? y(r0 - 1, 1) : z, B2d = n > m ? y(r0 - 1, 3) : z;
+  const double inva = 1.0 / a;
+  const double k = (double)n * (n + 1) / (a * a);
+  double2 div1, div2, curl1;
+  div1.x = (-m * A1.y + cu * B1u.x - cd * B1d.x) * inva;
+  div1.y = (m * A1.x + cu * B1u.y - cd * B1d.y) * inva;
+  div2.x = (-m * A2.y + cu * B2u.x - cd * B2d.x) * inva;
+  div2.y = (m * A2.x + cu * B2u.y - cd * B2d.y) * inva;
+  curl1.x = (-m * B1.y - cu * A1u.x + cd * A1d.x) * inva;
+  curl1.y = (m * B1.x - cu * A1u.y + cd * A1d.y) * inva;
+  double2 *oE = fE + (size_t)b * 3 * nc;
+  double2 fe0 = make_double2(-div2.x, -div2.y);
+  double2 fe1 = make_double2(-div1.x, -div1.y);
+  double2 fe2 = make_double2(curl1.x + k * E.x, curl1.y + k * E.y);
+  if (m == 0) { fe0.y = 0.0; fe1.y = 0.0; fe2.y = 0.0; }
+  oE[idx] = fe0;
+  oE[nc + idx] = fe1;
+  oE[2 * nc + idx] = fe2;
+  if (fI) {
+    const double2 *st = state + (size_t)b * 3 * nc;
+    double2 Phi = st[idx], zeta = st[nc + idx], delta = st[2 * nc + idx];
+    if (m == 0) { Phi.y = 0.0; zeta.y = 0.0; delta.y = 0.0; }
+    double2 *oI = fI + (size_t)b * 3 * nc;
+    oI[idx] = make_double2(-phibar * delta.x - nu * k * Phi.x, -phibar * delta.y - nu * k * Phi.y);
+    oI[nc + idx] = make_double2(-nu * k * zeta.x, -nu * k * zeta.y);
+    oI[2 * nc + idx] = make_double2(k * Phi.x - nu * k * delta.x, k * Phi.y - nu * k * delta.y);
+  }
+}
+
+int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
+                 cudaStream_t s) {
+  dim3 g((p->ncoef + 255) / 256, B);
+  {
+    PFSH_LAUNCH("k_rhs_assemble", s);
+    k_rhs_assemble<<<g, 256, 0, s>>>(p->T, B, prm.a, prm.nu, prm.phibar, (const double2 *)p->Y,
+                                     (const double2 *)state, (double2 *)fE, (double2 *)fI);
+  }
+  PFSH_CHECK_LAUNCH("k_rhs_assemble");
+  return PFSH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// implicit solve x - h L(x) = b, per coefficient (k = n(n+1)/a^2, s = 1 + h nu k)
+//   zeta = b_zeta / s;  [s  h Phibar; -h k  s] [Phi; delta] = [b_Phi; b_delta]
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ void solve3(double2 bP, double2 bz, double2 bd, double h, double k, double nu,
+                                       double phibar, double2 *xP, double2 *xz, double2 *xd) {
+  const double s = 1.0 + h * nu * k;
+  const double det = s * s + h * h * phibar * k;
+  const double id = 1.0 / det, is = 1.0 / s;
+  *xP = make_double2((s * bP.x - h * phibar * bd.x) * id, (s * bP.y - h * phibar * bd.y) * id);
+  *xz = make_double2(bz.x * is, bz.y * is);
+  *xd = make_double2((s * bd.x + h * k * bP.x) * id, (s * bd.y + h * k * bP.y) * id);
+}
+
+__global__ void k_implicit(int T, double a, double nu, double phibar, double h, const double2 *__restrict__ b,
+                           double2 *__restrict__ x) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int bb = blockIdx.y;
+  const int nc = ncoef_of(T);
+  if (idx >= nc) return;
+  const int m = tri_m(idx, T);
+  const int n = m + (idx - poff(T, m));
+  const double k = (double)n * (n + 1) / (a * a);
+  const double2 *in = b + (size_t)bb * 3 * nc;
+  double2 *out = x + (size_t)bb * 3 * nc;
+  double2 xP, xz, xd;
+  solve3(in[idx], in[nc + idx], in[2 * nc + idx], h, k, nu, phibar, &xP, &xz, &xd);
+  out[idx] = xP;
+  out[nc + idx] = xz;
+  out[2 * nc + idx] = xd;
+}
+
+int implicit_solve_launch(int T, const double *b, double *x, double h, int B, const swe_params &prm,
+                          cudaStream_t s) {
+  dim3 g((ncoef_of(T) + 255) / 256, B);
+  {
+    PFSH_LAUNCH("k_implicit", s);
+    k_implicit<<<g, 256, 0, s>>>(T, prm.a, prm.nu, prm.phibar, h, (const double2 *)b, (double2 *)x);
+  }
+  PFSH_CHECK_LAUNCH("k_implicit");
+  return PFSH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// SDC: constants of every node update from the old iterate, then node updates
+// ---------------------------------------------------------------------------
+struct SdcCoef {
+  double cE[16][16];  // dt (Q - QE') for the "old" right-hand sides
+  double cI[16][16];  // dt (Q - QI')
+  double nE[16][16];  // dt QE  (new explicit terms, j < i)
+  double nI[16][16];  // dt QI  (new implicit terms, j < i)
+  double h[16];       // dt QI[i][i]
+};
+
+// O_i = theta_0 + sum_j cE[i][j] FE_j + cI[i][j] FI_j (+ tau_i),  i = 1..M
+__global__ void k_sdc_old(int nc3, int B, int M, size_t nstride, SdcCoef c, const double2 *__restrict__ th,
+                          const double2 *__restrict__ fe, const double2 *__restrict__ fi,
+                          const double2 *__restrict__ tau, size_t tstride, double2 *__restrict__ O) {
+  size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (t >= (size_t)nc3 * B) return;
+  double2 acc[16];
+  const double2 t0 = th[t];
+  for (int i = 1; i <= M; ++i) acc[i] = tau ? t0 + tau[(size_t)i * tstride + t] : t0;
+  for (int j = 0; j <= M; ++j) {
+    const double2 e = fe[(size_t)j * nstride + t], f = fi[(size_t)j * nstride + t];
+    for (int i = 1; i <= M; ++i) {
+      acc[i].x += c.cE[i][j] * e.x + c.cI[i][j] * f.x;
+      acc[i].y += c.cE[i][j] * e.y + c.cI[i][j] * f.y;
+    }
+  }
+  for (int i = 1; i <= M; ++i) O[(size_t)(i - 1) * nc3 * B + t] = acc[i];
+}
+
+// theta_i = solve(O_i + sum_{1<=j<i} nE[i][j] FE_j^new + nI[i][j] FI_j^new, h_i)
+__global__ void k_sdc_node(int T, int B, int i, size_t nstride, SdcCoef c, double a, double nu, double phibar,
+                           const double2 *__restrict__ O, const double2 *__restrict__ fe,
+                           const double2 *__restrict__ fi, double2 *__restrict__ th) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  const int nc = ncoef_of(T);
+  if (idx >= nc) return;
+  const int m = tri_m(idx, T);
+  const int n = m + (idx - poff(T, m));
+  const double k = (double)n * (n + 1) / (a * a);
+  double2 r[3];
+  for (int f = 0; f < 3; ++f) {
+    const size_t t = (size_t)b * 3 * nc + f * nc + idx;
+    double2 v = O[t];
+    for (int j = 1; j < i; ++j) {
+      const double2 e = fe[(size_t)j * nstride + t], g = fi[(size_t)j * nstride + t];
+      v.x += c.nE[i][j] * e.x + c.nI[i][j] * g.x;
+      v.y += c.nE[i][j] * e.y + c.nI[i][j] * g.y;
+    }
+    r[f] = v;
+  }
+  double2 xP, xz, xd;
+  solve3(r[0], r[1], r[2], c.h[i], k, nu, phibar, &xP, &xz, &xd);
+  double2 *out = th + (size_t)i * nstride + (size_t)b * 3 * nc;
+  out[idx] = xP;
+  out[nc + idx] = xz;
+  out[2 * nc + idx] = xd;
+}
+
+int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const double *tau, size_t node_stride,
+                      int B, cudaStream_t s) {
+  const swe_ctx *ctx = l->ctx;
+  const int T = ctx->plan->T;
+  const int nc = ncoef_of(T);
+  const int M = l->nodes - 1;
+  if (B > l->max_batch) return fail(PFSH_EINVAL, "sdc_sweep: batch larger than the level's max_batch");
+  SdcCoef c;
+  for (int i = 0; i < 16; ++i) {
+    c.h[i] = 0.0;
+    for (int j = 0; j < 16; ++j) c.cE[i][j] = c.cI[i][j] = c.nE[i][j] = c.nI[i][j] = 0.0;
+  }
+  const double dt = l->dt;
+  for (int i = 1; i <= M; ++i) {
+    for (int j = 0; j <= M; ++j) {
+      const double qe = (j >= 1 && j <= i - 1) ? l->QE[i][j] : 0.0;
+      const double qi = (j >= 1 && j <= i) ? l->QI[i][j] : 0.0;
+      c.cE[i][j] = dt * (l->Q[i][j] - qe);
+      c.cI[i][j] = dt * (l->Q[i][j] - qi);
+      if (j >= 1 && j < i) {
+        c.nE[i][j] = dt * l->QE[i][j];
+        c.nI[i][j] = dt * l->QI[i][j];
+      }
+    }
+    c.h[i] = dt * l->QI[i][i];
+  }
+  // node stride in complex elements
+  const size_t ns = node_stride / 2;
+  const int nc3 = 3 * nc;
+  {
+    size_t total = (size_t)nc3 * B;
+    {
+      PFSH_LAUNCH("k_sdc_old", s);
+      k_sdc_old<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(nc3, B, M, ns, c, (const double2 *)theta,
+                                                               (const double2 *)fE, (const double2 *)fI,
+                                                               (const double2 *)tau, ns, (double2 *)l->d_old);
+    }
+    PFSH_CHECK_LAUNCH("k_sdc_old");
+  }
+  for (int i = 1; i <= M; ++i) {
+    dim3 g((nc + 255) / 256, B);
+    {
+      PFSH_LAUNCH("k_sdc_node", s);
+      k_sdc_node<<<g, 256, 0, s>>>(T, B, i, ns, c, ctx->prm.a, ctx->prm.nu, ctx->prm.phibar,
+                                   (const double2 *)l->d_old + (size_t)(i - 1) * nc3 * B, (const double2 *)fE,
+                                   (const double2 *)fI, (double2 *)theta);
+    }
+    PFSH_CHECK_LAUNCH("k_sdc_node");
+    int rc = rhs_eval(l->ctx, theta + (size_t)i * node_stride, fE + (size_t)i * node_stride,
+                      fI + (size_t)i * node_stride, B, s);
+    if (rc) return rc;
+  }
+  return PFSH_OK;
+}
+
+// ---------------------------------------------------------------------------
+// space-time transfers between a degree-Tf and a degree-Tc triangle
+// ---------------------------------------------------------------------------
+struct TimeMat {
+  double v[16][16];
+};
+
+// xc[i][b] = sum_k R[i][k] D(xf[k][b])   (D: keep n <= Tc)
+__global__ void k_restrict(int Tf, int Tc, int B, int nf, int nc_nodes, TimeMat R, const double2 *__restrict__ xf,
+                           size_t fstride, size_t fbstride, double2 *__restrict__ xc, size_t cstride) {
+  int idx = blockIdx.x * blockDim.x + threadIdx.x;
+  int b = blockIdx.y;
+  const int ncc = ncoef_of(Tc), ncf = ncoef_of(Tf);
+  if (idx >= ncc) return;
+  const int m = tri_m(idx, Tc);
+  const int fidx = poff(Tf, m) + (idx - poff(Tc, m));
+  for (int f = 0; f < 3; ++f) {
+    for (int i = 0; i < nc_nodes; ++i) {
+      double2 acc = make_double2(0.0, 0.0);
+      for (int k = 0; k < nf; ++k) {
+        const double r = R.v[i][k];
+        if (r == 0.0) continue;
+        const double2 v = xf[(size_t)k * fstride + (size_t)b * fbstride + (size_t)f * ncf + fidx];
+        if (r == 1.0) {
+          acc = acc + v;
+        } else {
+          acc.x += r * v.x;
+          acc.y += r * v.y;
+        }
+      }
+      xc[(size_t)i * cstride + (size_t)b * 3 * ncc + (size_t)f * ncc + idx] = acc;
+    }
+  }
+}
+
+int restrict_launch(const double *Rt, int nf, int ncn, const double *xf, size_t fstride, double *xc, size_t cstride,
+                    int Tf, int Tc, int B, cudaStream_t s) {
+  TimeMat R;
+  for (int i = 0; i < 16; ++i)
+    for (int k = 0; k < 16; ++k) R.v[i][k] = (i < ncn && k < nf) ? Rt[i * 16 + k] : 0.0;
+  dim3 g((ncoef_of(Tc) + 255) / 256, B);
+  // fbstride: batch stride inside a node (one fine state) unless broadcasting
+  {
+    PFSH_LAUNCH("k_restrict", s);
+    k_restrict<<<g, 256, 0, s>>>(Tf, Tc, B, nf, ncn, R, (const double2 *)xf, fstride / 2,
+                                 (size_t)3 * ncoef_of(Tf), (double2 *)xc, cstride / 2);
+  }
+  PFSH_CHECK_LAUNCH("k_restrict");
+  return PFSH_OK;
+}
+
+}  // namespace pfsh
