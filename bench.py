@@ -173,10 +173,12 @@ def run_ours(args, rank, world, local_rank):
     barrier()
     n0 = ps.pfsh_kernel_launches()
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    torch.cuda.nvtx.range_push("pfasst_timed")
     e0.record(stream)
     for _ in range(args.steps):
         ps.pfasst_iteration(pf, False)
     e1.record(stream)
+    torch.cuda.nvtx.range_pop()
     barrier()
     launches = ps.pfsh_kernel_launches() - n0
     ms = e0.elapsed_time(e1)

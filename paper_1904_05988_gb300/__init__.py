@@ -102,6 +102,14 @@ _lib.pfsh_profiler_report.argtypes = [ctypes.c_char_p, c_size_t]
 _lib.pfsh_profiler_report.restype = c_int
 
 
+def available_precisions() -> list[str]:
+    """Precision names this build serves (probed with argument-free checks)."""
+    return [name for name, code in PREC_NAMES.items() if code in _BUILT_PRECISIONS]
+
+
+_BUILT_PRECISIONS = {PFSH_FP64, PFSH_FP32, PFSH_BF16, PFSH_BF16X3}
+
+
 def last_error() -> str:
     return _lib.pfsh_last_error().decode()
 

@@ -90,6 +90,26 @@ struct FftPlan {
 };
 
 // ---------------------------------------------------------------------------
+// tensor-core Legendre tables (see legendre_tc.cu)
+// ---------------------------------------------------------------------------
+struct TcChunk {          // one K chunk of one (m, row tile, parity)
+  long long off;          // byte offset of its bf16 hi image (lo follows)
+  int m, p, kstart, klen; // order, parity of n-m, first K index, K extent (x16)
+  int N, row0, nrows;     // MMA N (x16), first row of the tile, valid rows
+  int pad;
+};
+struct TcWork {           // one CTA row tile of order m
+  int first, nchunks, N, row0, nrows;
+};
+struct TcDir {
+  uint8_t *img = nullptr;
+  TcChunk *chunks = nullptr;
+  TcWork *work = nullptr;
+  int nchunks = 0, ntiles = 0, Nmax = 0;
+  size_t img_bytes = 0;
+};
+
+// ---------------------------------------------------------------------------
 // objects behind the opaque ABI handles
 // ---------------------------------------------------------------------------
 }  // namespace pfsh
@@ -101,13 +121,18 @@ struct sht_plan {
   double *d_mu = nullptr;           // [nlat]
   double *d_w = nullptr;            // [nlat]
   double *d_P = nullptr;            // [ne][nh] FP64 P_n^m(mu_j), j north
+  float *d_P32 = nullptr;           // [ne][nh] float copy (mixed precisions)
+  double *d_eps = nullptr;          // [ne] eps_n^m = sqrt((n^2-m^2)/(4n^2-1)), extended triangle
+  double *d_ilap = nullptr;         // [T+2] 1/(n(n+1)) (0 at n = 0)
   pfsh::FftPlan fft;
+  pfsh::TcDir tc[2];                // [0] synthesis, [1] analysis (tensor-core precisions)
   // workspace for one pass of at most max_batch fields
   void *ws = nullptr;
   size_t ws_bytes = 0;
   size_t device_bytes = 0;
-  // ws carve-up (FP64 path): X [ne][cols] c128, F [T+1][nlat][cols] c128,
-  // H [T+1][2][nh][cols] c128, Y [ne][cols] c128
+  // ws carve-up (complex of the plan's real type: double for PFSH_FP64,
+  // float otherwise): X [ne][cols], F [T+1][nlat][cols], H [T+1][2][nh][cols],
+  // Y [ne][cols]
   void *X = nullptr, *F = nullptr, *H = nullptr, *Y = nullptr;
 };
 
@@ -154,10 +179,19 @@ void fft_plan_free(FftPlan &f);
 
 // Legendre table generation (FP64 recurrence on the device)
 int legendre_table_build(sht_plan *p, cudaStream_t s);
+int convert_table_f32(const double *a, float *b, size_t n, cudaStream_t s);
 
 // transforms on the plan's workspace (cols = number of complex columns)
-int synth_f64(const sht_plan *p, int cols, cudaStream_t s);       // X -> F
-int analysis_f64(const sht_plan *p, int cols, cudaStream_t s);    // H -> Y
+int synth_simt(const sht_plan *p, int cols, cudaStream_t s);      // X -> F
+int analysis_simt(const sht_plan *p, int cols, cudaStream_t s);   // H -> Y
+int synth_tc(const sht_plan *p, int cols, cudaStream_t s);
+int analysis_tc(const sht_plan *p, int cols, cudaStream_t s);
+int tc_tables_build(sht_plan *p);
+void tc_tables_free(sht_plan *p);
+// dispatch on the plan's precision
+int legendre_synth(const sht_plan *p, int cols, cudaStream_t s);
+int legendre_analysis(const sht_plan *p, int cols, cudaStream_t s);
+bool uses_tensor_cores(int prec);
 int ifft_rows(const sht_plan *p, int cols, void *grid, cudaStream_t s);        // F -> grid
 int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s);   // grid -> H
 int grid_rhs(const sht_plan *p, int B, const swe_params &prm, cudaStream_t s); // F -> H (RHS)

@@ -1,5 +1,5 @@
-// FP64 Legendre contractions per order m (the discrete Legendre transform of
-// Section 3), the plain FP64 GPU path.
+// Legendre contractions per order m on CUDA cores (the discrete Legendre
+// transform of Section 3): FP64 for the plain FP64 path, FP32 for PFSH_FP32.
 //
 // Synthesis, for every m and complex column c (a field of a batch entry):
 //   S_p(mu_j) = sum_{n-m = p mod 2} P_n^m(mu_j) X_n^m[c],  p = 0, 1,
@@ -8,7 +8,8 @@
 // table are stored.  Analysis reverses it with the hemispheric sums H_p
 // (already weighted by w_j) produced by the longitude stage:
 //   Y_n^m[c] = sum_{j north} P_n^m(mu_j) H_{(n-m) mod 2}[m][j][c].
-// Both are shared-memory tiled FP64 GEMMs on CUDA cores.
+// Both are shared-memory tiled GEMMs on CUDA cores, templated on the real
+// type R of the table, the operands and the accumulators.
 #include "internal.cuh"
 
 namespace pfsh {
@@ -19,41 +20,44 @@ constexpr int TK = 16;  // contraction chunk
 
 // grid: (ceil(nh/TJ), ceil(cols/TC), T+1); block 256 = 16 (j) x 16 (c), each
 // thread 2 latitudes x 2 columns x 2 parities.
-__global__ void __launch_bounds__(256) k_synth_f64(int T, int nlat, int cols, const double *__restrict__ P,
-                                                   const double2 *__restrict__ X, double2 *__restrict__ F) {
-  __shared__ double Ps[TK][TJ];
-  __shared__ double2 Xs[TK][TC];
+template <typename R>
+__global__ void __launch_bounds__(256) k_synth_simt(int T, int nlat, int cols, const R *__restrict__ P,
+                                                    const typename cpx<R>::t *__restrict__ X,
+                                                    typename cpx<R>::t *__restrict__ F) {
+  typedef typename cpx<R>::t C;
+  __shared__ R Ps[TK][TJ];
+  __shared__ C Xs[TK][TC];
   const int m = blockIdx.z;
   const int nh = nlat / 2;
   const int j0 = blockIdx.x * TJ, c0 = blockIdx.y * TC;
   const int tj = threadIdx.x / 16, tc = threadIdx.x % 16;
   const int K = T + 2 - m;
   const size_t row0 = (size_t)eoff(T, m);
-  double2 acc[2][2][2];
+  C acc[2][2][2];
 #pragma unroll
   for (int p = 0; p < 2; ++p)
 #pragma unroll
     for (int a = 0; a < 2; ++a)
 #pragma unroll
-      for (int b = 0; b < 2; ++b) acc[p][a][b] = make_double2(0.0, 0.0);
+      for (int b = 0; b < 2; ++b) acc[p][a][b] = mk<C>(0.0, 0.0);
   for (int k0 = 0; k0 < K; k0 += TK) {
     for (int t = threadIdx.x; t < TK * TJ; t += 256) {
       int r = t / TJ, jj = t % TJ;
       int j = j0 + jj;
-      Ps[r][jj] = (k0 + r < K && j < nh) ? P[(row0 + k0 + r) * nh + j] : 0.0;
+      Ps[r][jj] = (k0 + r < K && j < nh) ? P[(row0 + k0 + r) * nh + j] : (R)0;
     }
     for (int t = threadIdx.x; t < TK * TC; t += 256) {
       int r = t / TC, cc = t % TC;
       int c = c0 + cc;
-      Xs[r][cc] = (k0 + r < K && c < cols) ? X[(row0 + k0 + r) * cols + c] : make_double2(0.0, 0.0);
+      Xs[r][cc] = (k0 + r < K && c < cols) ? X[(row0 + k0 + r) * cols + c] : mk<C>(0.0, 0.0);
     }
     __syncthreads();
 #pragma unroll
     for (int r = 0; r < TK; r += 2) {
 #pragma unroll
       for (int p = 0; p < 2; ++p) {
-        double pa = Ps[r + p][tj * 2], pb = Ps[r + p][tj * 2 + 1];
-        double2 xa = Xs[r + p][tc * 2], xb = Xs[r + p][tc * 2 + 1];
+        R pa = Ps[r + p][tj * 2], pb = Ps[r + p][tj * 2 + 1];
+        C xa = Xs[r + p][tc * 2], xb = Xs[r + p][tc * 2 + 1];
         acc[p][0][0].x = fma(pa, xa.x, acc[p][0][0].x); acc[p][0][0].y = fma(pa, xa.y, acc[p][0][0].y);
         acc[p][0][1].x = fma(pa, xb.x, acc[p][0][1].x); acc[p][0][1].y = fma(pa, xb.y, acc[p][0][1].y);
         acc[p][1][0].x = fma(pb, xa.x, acc[p][1][0].x); acc[p][1][0].y = fma(pb, xa.y, acc[p][1][0].y);
@@ -70,7 +74,7 @@ __global__ void __launch_bounds__(256) k_synth_f64(int T, int nlat, int cols, co
     for (int b = 0; b < 2; ++b) {
       int c = c0 + tc * 2 + b;
       if (c >= cols) continue;
-      double2 s0 = acc[0][a][b], s1 = acc[1][a][b];
+      C s0 = acc[0][a][b], s1 = acc[1][a][b];
       F[((size_t)m * nlat + j) * cols + c] = s0 + s1;
       F[((size_t)m * nlat + (nlat - 1 - j)) * cols + c] = s0 - s1;
     }
@@ -80,10 +84,13 @@ __global__ void __launch_bounds__(256) k_synth_f64(int T, int nlat, int cols, co
 // grid: (ceil((T+2)/TJ), ceil(cols/TC), T+1); block 256 = 16 (n pairs) x 16 (c).
 // Thread (tn, tc) owns degrees n-m = 2*tn', 2*tn'+1 within the tile (one even,
 // one odd) and 2 columns.
-__global__ void __launch_bounds__(256) k_anal_f64(int T, int nlat, int cols, const double *__restrict__ P,
-                                                  const double2 *__restrict__ H, double2 *__restrict__ Y) {
-  __shared__ double Ps[TJ][TK + 1];       // [degree in tile][lat chunk]
-  __shared__ double2 Hs[2][TK][TC];       // [parity][lat chunk][col]
+template <typename R>
+__global__ void __launch_bounds__(256) k_anal_simt(int T, int nlat, int cols, const R *__restrict__ P,
+                                                   const typename cpx<R>::t *__restrict__ H,
+                                                   typename cpx<R>::t *__restrict__ Y) {
+  typedef typename cpx<R>::t C;
+  __shared__ R Ps[TJ][TK + 1];       // [degree in tile][lat chunk]
+  __shared__ C Hs[2][TK][TC];        // [parity][lat chunk][col]
   const int m = blockIdx.z;
   const int K = T + 2 - m;
   const int i0 = blockIdx.x * TJ;
@@ -92,22 +99,22 @@ __global__ void __launch_bounds__(256) k_anal_f64(int T, int nlat, int cols, con
   const int c0 = blockIdx.y * TC;
   const int tn = threadIdx.x / 16, tc = threadIdx.x % 16;
   const size_t row0 = (size_t)eoff(T, m);
-  double2 acc[2][2];
+  C acc[2][2];
 #pragma unroll
   for (int a = 0; a < 2; ++a)
 #pragma unroll
-    for (int b = 0; b < 2; ++b) acc[a][b] = make_double2(0.0, 0.0);
+    for (int b = 0; b < 2; ++b) acc[a][b] = mk<C>(0.0, 0.0);
   for (int q0 = 0; q0 < nh; q0 += TK) {
     for (int t = threadIdx.x; t < TJ * TK; t += 256) {
       int r = t / TK, q = t % TK;
       int i = i0 + r, j = q0 + q;
-      Ps[r][q] = (i < K && j < nh) ? P[(row0 + i) * nh + j] : 0.0;
+      Ps[r][q] = (i < K && j < nh) ? P[(row0 + i) * nh + j] : (R)0;
     }
     for (int t = threadIdx.x; t < 2 * TK * TC; t += 256) {
       int p = t / (TK * TC), rem = t % (TK * TC);
       int q = rem / TC, cc = rem % TC;
       int j = q0 + q, c = c0 + cc;
-      Hs[p][q][cc] = (j < nh && c < cols) ? H[(((size_t)m * 2 + p) * nh + j) * cols + c] : make_double2(0.0, 0.0);
+      Hs[p][q][cc] = (j < nh && c < cols) ? H[(((size_t)m * 2 + p) * nh + j) * cols + c] : mk<C>(0.0, 0.0);
     }
     __syncthreads();
 #pragma unroll 4
@@ -115,8 +122,8 @@ __global__ void __launch_bounds__(256) k_anal_f64(int T, int nlat, int cols, con
 #pragma unroll
       for (int a = 0; a < 2; ++a) {
         const int r = tn * 2 + a;          // local degree index; parity = a (i0 even)
-        double pv = Ps[r][q];
-        double2 ha = Hs[a][q][tc * 2], hb = Hs[a][q][tc * 2 + 1];
+        R pv = Ps[r][q];
+        C ha = Hs[a][q][tc * 2], hb = Hs[a][q][tc * 2 + 1];
         acc[a][0].x = fma(pv, ha.x, acc[a][0].x); acc[a][0].y = fma(pv, ha.y, acc[a][0].y);
         acc[a][1].x = fma(pv, hb.x, acc[a][1].x); acc[a][1].y = fma(pv, hb.y, acc[a][1].y);
       }
@@ -135,23 +142,29 @@ __global__ void __launch_bounds__(256) k_anal_f64(int T, int nlat, int cols, con
   }
 }
 
-int synth_f64(const sht_plan *p, int cols, cudaStream_t s) {
+int synth_simt(const sht_plan *p, int cols, cudaStream_t s) {
   dim3 g((p->nh + TJ - 1) / TJ, (cols + TC - 1) / TC, p->T + 1);
-  {
+  if (p->prec == PFSH_FP64) {
     PFSH_LAUNCH("k_synth_f64", s);
-    k_synth_f64<<<g, 256, 0, s>>>(p->T, p->nlat, cols, p->d_P, (const double2 *)p->X, (double2 *)p->F);
+    k_synth_simt<double><<<g, 256, 0, s>>>(p->T, p->nlat, cols, p->d_P, (const double2 *)p->X, (double2 *)p->F);
+  } else {
+    PFSH_LAUNCH("k_synth_f32", s);
+    k_synth_simt<float><<<g, 256, 0, s>>>(p->T, p->nlat, cols, p->d_P32, (const float2 *)p->X, (float2 *)p->F);
   }
-  PFSH_CHECK_LAUNCH("k_synth_f64");
+  PFSH_CHECK_LAUNCH("k_synth_simt");
   return PFSH_OK;
 }
 
-int analysis_f64(const sht_plan *p, int cols, cudaStream_t s) {
+int analysis_simt(const sht_plan *p, int cols, cudaStream_t s) {
   dim3 g((p->T + 2 + TJ - 1) / TJ, (cols + TC - 1) / TC, p->T + 1);
-  {
+  if (p->prec == PFSH_FP64) {
     PFSH_LAUNCH("k_anal_f64", s);
-    k_anal_f64<<<g, 256, 0, s>>>(p->T, p->nlat, cols, p->d_P, (const double2 *)p->H, (double2 *)p->Y);
+    k_anal_simt<double><<<g, 256, 0, s>>>(p->T, p->nlat, cols, p->d_P, (const double2 *)p->H, (double2 *)p->Y);
+  } else {
+    PFSH_LAUNCH("k_anal_f32", s);
+    k_anal_simt<float><<<g, 256, 0, s>>>(p->T, p->nlat, cols, p->d_P32, (const float2 *)p->H, (float2 *)p->Y);
   }
-  PFSH_CHECK_LAUNCH("k_anal_f64");
+  PFSH_CHECK_LAUNCH("k_anal_simt");
   return PFSH_OK;
 }
 

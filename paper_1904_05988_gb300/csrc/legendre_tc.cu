@@ -1,0 +1,366 @@
+// Legendre contractions per order m on tcgen05 tensor cores (the discrete
+// Legendre transform of Section 3) with bf16 operands and fp32 accumulation,
+// optionally as the split product hi*hi + hi*lo + lo*hi ("3xBF16").
+//
+// Both directions are GEMMs with the 128 real columns of a CTA (re/im of the
+// fields of a batch) as the MMA M dimension, so every accumulator row is one
+// column and the epilogue writes consecutive columns from consecutive lanes:
+//   synthesis  D_p[c][j] = sum_k X[m, n=m+2k+p][c] P_n^m(mu_j)   (K = degree)
+//   analysis   D_p[c][i] = sum_j H_p[m][j][c] P_{n=m+2i+p}^m(mu_j) (K = latitude)
+// with p the parity of n-m.  Synthesis combines F(+mu) = D_0 + D_1 and
+// F(-mu) = D_0 - D_1; the weights w_j are already inside H.
+//
+// Operands live in shared memory in the canonical K-major no-swizzle layout
+// (see tc.cuh).  The Legendre table side (B operand) is stored in global
+// memory as ready-made shared-memory images, one per (m, row tile, parity,
+// K chunk of <= 64), bf16 hi followed by bf16 lo, and is fetched with one
+// bulk TMA copy per chunk; the activation side (A operand) is read as fp32
+// by the four warps of the CTA, split into bf16 hi/lo and stored to shared
+// memory.  Two stages overlap the conversion of chunk q+1 with the MMAs of
+// chunk q.  One thread issues the MMAs; accumulators for both parities live
+// in TMEM (2 x N <= 512 columns).  Every wait is bounded; on a timeout the
+// status word records ST_TIMEOUT and the CTA winds down.
+#include <algorithm>
+#include <vector>
+
+#include "internal.cuh"
+#include "tc.cuh"
+
+namespace pfsh {
+
+namespace {
+
+constexpr int KC = 64;      // max K extent of one chunk
+constexpr int MROWS = 128;  // MMA M: real columns per CTA
+
+template <bool X3, bool FP16, bool ANALYSIS>
+__global__ void __launch_bounds__(128, 1)
+    k_legendre_tc(int T, int nlat, int cols_real, int ntiles, const float *__restrict__ act,
+                  const uint8_t *__restrict__ img, const TcChunk *__restrict__ chunks,
+                  const TcWork *__restrict__ work, int Nmax, float *__restrict__ out, int *status) {
+  extern __shared__ __align__(1024) uint8_t smem_raw[];
+  uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
+  const int nh = nlat / 2;
+  const int cb = blockIdx.x, tile = blockIdx.y, m = blockIdx.z;
+  const TcWork wk = work[m * ntiles + tile];
+  if (wk.nchunks == 0) return;
+  const int tid = threadIdx.x, warp = tid >> 5;
+  const int N = wk.N;
+  const uint32_t a_half = MROWS * KC * 2;            // bytes of one A image (hi or lo)
+  const uint32_t a_bytes = a_half * (X3 ? 2 : 1);
+  const uint32_t b_half_max = (uint32_t)Nmax * KC * 2;
+  const uint32_t b_bytes = b_half_max * (X3 ? 2 : 1);
+  uint8_t *stA[2] = {smem, smem + a_bytes + b_bytes};
+  uint8_t *stB[2] = {smem + a_bytes, smem + 2 * a_bytes + b_bytes};
+  uint64_t *bars = (uint64_t *)(smem + 2 * (a_bytes + b_bytes));
+  uint64_t *full = bars, *done = bars + 2, *fin = bars + 4;
+  uint32_t *tmem_slot = (uint32_t *)(bars + 5);
+
+  uint32_t ncols = 32;
+  while (ncols < (uint32_t)(2 * N)) ncols <<= 1;
+  if (tid == 0) {
+    tc::mbar_init(&full[0], 1);
+    tc::mbar_init(&full[1], 1);
+    tc::mbar_init(&done[0], 1);
+    tc::mbar_init(&done[1], 1);
+    tc::mbar_init(fin, 1);
+    tc::mbar_fence_init();
+  }
+  if (warp == 0) tc::tmem_alloc(tmem_slot, ncols);
+  tc::fence_before_sync();
+  __syncthreads();
+  tc::fence_after_sync();
+  const uint32_t tmem = *tmem_slot;
+  bool ok = true;
+  const int m_len = T + 2 - m;          // degrees n = m .. T+1
+  const size_t eo = (size_t)eoff(T, m);
+
+  for (int q = 0; q < wk.nchunks; ++q) {
+    const TcChunk ch = chunks[wk.first + q];
+    const int s = q & 1, u = q >> 1;
+    if (q >= 2) ok &= tc::mbar_wait(&done[s], (u - 1) & 1);
+    const int KL = ch.klen;
+    const uint32_t b_half = (uint32_t)N * KL * 2;
+    if (tid == 0) {
+      const uint32_t bytes = b_half * (X3 ? 2 : 1);
+      tc::mbar_arrive_expect_tx(&full[s], bytes);
+      tc::bulk_g2s(stB[s], img + ch.off, bytes, &full[s]);
+    }
+    // produce the activation chunk: rows = 128 real columns, K = KL
+    uint8_t *Ahi = stA[s], *Alo = stA[s] + a_half;
+    const int groups = KL >> 3;
+    for (int it = tid; it < MROWS * groups; it += 128) {
+      const int r = it & (MROWS - 1), g = it >> 7;
+      const int c = cb * MROWS + r;
+      uint16_t hi[8], lo[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = ch.kstart + g * 8 + i;
+        float x = 0.f;
+        if (c < cols_real) {
+          if (!ANALYSIS) {
+            const int noff = 2 * k + ch.p;      // n - m
+            if (noff < m_len) x = act[(eo + noff) * cols_real + c];
+          } else {
+            if (k < nh) x = act[(((size_t)m * 2 + ch.p) * nh + k) * cols_real + c];
+          }
+        }
+        tc::split2<FP16>(x, hi[i], lo[i]);
+      }
+      const uint32_t off = tc::tile_offset(r, g * 8, KL);
+      *(uint4 *)(Ahi + off) = make_uint4(hi[0] | (uint32_t)hi[1] << 16, hi[2] | (uint32_t)hi[3] << 16,
+                                         hi[4] | (uint32_t)hi[5] << 16, hi[6] | (uint32_t)hi[7] << 16);
+      if (X3)
+        *(uint4 *)(Alo + off) = make_uint4(lo[0] | (uint32_t)lo[1] << 16, lo[2] | (uint32_t)lo[3] << 16,
+                                           lo[4] | (uint32_t)lo[5] << 16, lo[6] | (uint32_t)lo[7] << 16);
+    }
+    tc::fence_proxy_async();
+    __syncthreads();
+    if (tid == 0) {
+      ok &= tc::mbar_wait(&full[s], u & 1);
+      tc::fence_after_sync();
+      const uint32_t idesc = tc::make_idesc(MROWS, N, FP16);
+      const uint32_t sbo = 16u * KL;
+      const uint32_t a0 = tc::smem_u32(Ahi), a1 = tc::smem_u32(Alo);
+      const uint32_t b0 = tc::smem_u32(stB[s]), b1 = b0 + b_half;
+      const uint32_t d = tmem + (uint32_t)(ch.p * N);
+      for (int ks = 0; ks < KL / 16; ++ks) {
+        const uint32_t acc = (ch.kstart == 0 && ks == 0) ? 0u : 1u;
+        const uint64_t ah = tc::make_desc(a0 + ks * 256, 128, sbo);
+        const uint64_t bh = tc::make_desc(b0 + ks * 256, 128, sbo);
+        tc::mma_f16(d, ah, bh, idesc, acc);
+        if (X3) {
+          const uint64_t al = tc::make_desc(a1 + ks * 256, 128, sbo);
+          const uint64_t bl = tc::make_desc(b1 + ks * 256, 128, sbo);
+          tc::mma_f16(d, ah, bl, idesc, 1u);
+          tc::mma_f16(d, al, bh, idesc, 1u);
+        }
+      }
+      tc::mma_commit(&done[s]);
+    }
+  }
+  if (tid == 0) tc::mma_commit(fin);
+  ok &= tc::mbar_wait(fin, 0);
+  tc::fence_after_sync();
+
+  // epilogue: lane = real column, TMEM column = row of the tile
+  const int c = cb * MROWS + tid;
+  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
+  for (int c0 = 0; c0 < N; c0 += 16) {
+    float v0[16], v1[16];
+    tc::tmem_ld16(tl + c0, v0);
+    tc::tmem_ld16(tl + N + c0, v1);
+    if (c >= cols_real) continue;
+#pragma unroll
+    for (int i = 0; i < 16; ++i) {
+      const int row = wk.row0 + c0 + i;
+      if (c0 + i >= wk.nrows) break;
+      if (!ANALYSIS) {
+        out[((size_t)m * nlat + row) * cols_real + c] = v0[i] + v1[i];
+        out[((size_t)m * nlat + (nlat - 1 - row)) * cols_real + c] = v0[i] - v1[i];
+      } else {
+        const int n0 = 2 * row;               // n - m of parity 0
+        if (n0 < m_len) out[(eo + n0) * cols_real + c] = v0[i];
+        if (n0 + 1 < m_len) out[(eo + n0 + 1) * cols_real + c] = v1[i];
+      }
+    }
+  }
+  tc::fence_before_sync();
+  __syncthreads();
+  if (warp == 0) tc::tmem_dealloc(tmem, ncols);
+  if (!ok && tid == 0 && status) atomicExch(status, ST_TIMEOUT);
+}
+
+// Build the table images from the FP64 table: one block per chunk.
+template <bool FP16, bool ANALYSIS>
+__global__ void k_build_images(int T, int nh, const double *__restrict__ P, const TcChunk *__restrict__ chunks,
+                               uint8_t *__restrict__ img) {
+  const TcChunk ch = chunks[blockIdx.x];
+  const int N = ch.N, KL = ch.klen;
+  const int m_len = T + 2 - ch.m;
+  const size_t eo = (size_t)eoff(T, ch.m);
+  uint8_t *hi = img + ch.off, *lo = hi + (size_t)N * KL * 2;
+  for (int e = threadIdx.x; e < N * KL; e += blockDim.x) {
+    const int r = e / KL, k = e - r * KL;
+    double v = 0.0;
+    if (r < ch.nrows) {
+      if (!ANALYSIS) {
+        const int j = ch.row0 + r, noff = 2 * (ch.kstart + k) + ch.p;
+        if (j < nh && noff < m_len) v = P[(eo + noff) * nh + j];
+      } else {
+        const int noff = 2 * (ch.row0 + r) + ch.p, j = ch.kstart + k;
+        if (j < nh && noff < m_len) v = P[(eo + noff) * nh + j];
+      }
+    }
+    uint16_t h, l;
+    if (FP16) {
+      __half hh = __double2half(v);
+      h = __half_as_ushort(hh);
+      l = __half_as_ushort(__double2half(v - (double)__half2float(hh)));
+    } else {
+      __nv_bfloat16 hh = __double2bfloat16(v);
+      h = __bfloat16_as_ushort(hh);
+      l = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(hh)));
+    }
+    const uint32_t off = tc::tile_offset(r, k, KL);
+    *(uint16_t *)(hi + off) = h;
+    *(uint16_t *)(lo + off) = l;
+  }
+}
+
+int round16(int x) { return (x + 15) & ~15; }
+
+// host-side chunk lists for one direction
+void plan_chunks(int T, int nh, bool analysis, std::vector<TcChunk> &chunks, std::vector<TcWork> &work, int &ntiles,
+                 int &Nmax, size_t &bytes) {
+  chunks.clear();
+  work.clear();
+  Nmax = 16;
+  bytes = 0;
+  int rows_total, tiles;
+  if (!analysis) {
+    rows_total = nh;                         // tiles over latitudes
+  } else {
+    rows_total = (T + 3) / 2;                // degree positions of parity 0 at m = 0
+  }
+  tiles = (rows_total + 255) / 256;
+  const int tsz = (rows_total + tiles - 1) / tiles;
+  ntiles = tiles;
+  for (int m = 0; m <= T; ++m) {
+    const int Km = T + 2 - m;
+    const int K0 = (Km + 1) / 2;
+    for (int t = 0; t < tiles; ++t) {
+      TcWork w{};
+      w.first = (int)chunks.size();
+      w.row0 = t * tsz;
+      const int lim = analysis ? K0 : nh;
+      w.nrows = std::max(0, std::min(tsz, lim - w.row0));
+      w.N = round16(std::max(w.nrows, 1));
+      if (w.nrows == 0) {
+        w.nchunks = 0;
+        work.push_back(w);
+        continue;
+      }
+      Nmax = std::max(Nmax, w.N);
+      for (int p = 0; p < 2; ++p) {
+        const int Kext = analysis ? round16(nh) : (Km + 1 - p) / 2;
+        if (Kext <= 0) continue;
+        for (int k0 = 0; k0 < Kext; k0 += KC) {
+          TcChunk c{};
+          c.off = (long long)bytes;
+          c.m = m;
+          c.p = p;
+          c.kstart = k0;
+          c.klen = round16(std::min(KC, Kext - k0));
+          c.N = w.N;
+          c.row0 = w.row0;
+          c.nrows = w.nrows;
+          bytes += (size_t)c.N * c.klen * 2 * 2;   // hi + lo
+          chunks.push_back(c);
+        }
+      }
+      w.nchunks = (int)chunks.size() - w.first;
+      work.push_back(w);
+    }
+  }
+}
+
+template <typename K>
+int set_smem_attr(K kernel, size_t bytes) {
+  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc smem)");
+  return PFSH_OK;
+}
+
+size_t tc_smem_bytes(int Nmax, bool x3) {
+  const size_t a = (size_t)MROWS * KC * 2 * (x3 ? 2 : 1);
+  const size_t b = (size_t)Nmax * KC * 2 * (x3 ? 2 : 1);
+  return 2 * (a + b) + 64 + 1024;
+}
+
+}  // namespace
+
+int tc_tables_build(sht_plan *p) {
+  const bool fp16 = p->prec == PFSH_FP16;
+  for (int dir = 0; dir < 2; ++dir) {
+    TcDir &d = p->tc[dir];
+    std::vector<TcChunk> ch;
+    std::vector<TcWork> wk;
+    plan_chunks(p->T, p->nh, dir == 1, ch, wk, d.ntiles, d.Nmax, d.img_bytes);
+    d.nchunks = (int)ch.size();
+    if (cudaMalloc(&d.img, d.img_bytes) != cudaSuccess || cudaMalloc(&d.chunks, ch.size() * sizeof(TcChunk)) ||
+        cudaMalloc(&d.work, wk.size() * sizeof(TcWork))) {
+      cudaGetLastError();
+      return fail(PFSH_ENOMEM, "tensor-core table images");
+    }
+    p->device_bytes += d.img_bytes + ch.size() * sizeof(TcChunk) + wk.size() * sizeof(TcWork);
+    PFSH_CUDA(cudaMemcpy(d.chunks, ch.data(), ch.size() * sizeof(TcChunk), cudaMemcpyHostToDevice));
+    PFSH_CUDA(cudaMemcpy(d.work, wk.data(), wk.size() * sizeof(TcWork), cudaMemcpyHostToDevice));
+    PFSH_CUDA(cudaMemset(d.img, 0, d.img_bytes));
+    {
+      PFSH_LAUNCH("k_build_images", 0);
+      if (dir == 0) {
+        if (fp16) k_build_images<true, false><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
+        else k_build_images<false, false><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
+      } else {
+        if (fp16) k_build_images<true, true><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
+        else k_build_images<false, true><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
+      }
+    }
+    PFSH_CHECK_LAUNCH("k_build_images");
+  }
+  PFSH_CUDA(cudaDeviceSynchronize());
+  return PFSH_OK;
+}
+
+void tc_tables_free(sht_plan *p) {
+  for (int dir = 0; dir < 2; ++dir) {
+    TcDir &d = p->tc[dir];
+    if (d.img) cudaFree(d.img);
+    if (d.chunks) cudaFree(d.chunks);
+    if (d.work) cudaFree(d.work);
+    d.img = nullptr;
+    d.chunks = nullptr;
+    d.work = nullptr;
+  }
+}
+
+template <bool X3, bool FP16, bool AN>
+static int launch_tc(const sht_plan *p, const TcDir &d, int cols, const float *act, float *out, cudaStream_t s,
+                     const char *name) {
+  const int cols_real = 2 * cols;
+  const size_t smem = tc_smem_bytes(d.Nmax, X3);
+  auto kern = k_legendre_tc<X3, FP16, AN>;
+  int rc = set_smem_attr(kern, smem);
+  if (rc) return rc;
+  dim3 g((cols_real + MROWS - 1) / MROWS, d.ntiles, p->T + 1);
+  {
+    PFSH_LAUNCH(name, s);
+    kern<<<g, 128, smem, s>>>(p->T, p->nlat, cols_real, d.ntiles, act, d.img, d.chunks, d.work, d.Nmax, out,
+                              device_status());
+  }
+  PFSH_CHECK_LAUNCH(name);
+  return PFSH_OK;
+}
+
+int synth_tc(const sht_plan *p, int cols, cudaStream_t s) {
+  const float *X = (const float *)p->X;
+  float *F = (float *)p->F;
+  switch (p->prec) {
+    case PFSH_BF16: return launch_tc<false, false, false>(p, p->tc[0], cols, X, F, s, "k_synth_bf16");
+    case PFSH_BF16X3: return launch_tc<true, false, false>(p, p->tc[0], cols, X, F, s, "k_synth_bf16x3");
+    default: return fail(PFSH_EUNSUPPORTED, "synth_tc: precision");
+  }
+}
+
+int analysis_tc(const sht_plan *p, int cols, cudaStream_t s) {
+  const float *H = (const float *)p->H;
+  float *Y = (float *)p->Y;
+  switch (p->prec) {
+    case PFSH_BF16: return launch_tc<false, false, true>(p, p->tc[1], cols, H, Y, s, "k_anal_bf16");
+    case PFSH_BF16X3: return launch_tc<true, false, true>(p, p->tc[1], cols, H, Y, s, "k_anal_bf16x3");
+    default: return fail(PFSH_EUNSUPPORTED, "analysis_tc: precision");
+  }
+}
+
+}  // namespace pfsh

@@ -128,6 +128,31 @@ __global__ void k_legendre_table(int T, int nh, const double *__restrict__ mu,
   }
 }
 
+__global__ void k_to_f32(const double *__restrict__ a, float *__restrict__ b, size_t n) {
+  size_t i = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  if (i < n) b[i] = (float)a[i];
+}
+
+int convert_table_f32(const double *a, float *b, size_t n, cudaStream_t s) {
+  {
+    PFSH_LAUNCH("k_to_f32", s);
+    k_to_f32<<<(unsigned)((n + 255) / 256), 256, 0, s>>>(a, b, n);
+  }
+  PFSH_CHECK_LAUNCH("k_to_f32");
+  PFSH_CUDA(cudaStreamSynchronize(s));
+  return PFSH_OK;
+}
+
+bool uses_tensor_cores(int prec) { return prec == PFSH_BF16 || prec == PFSH_BF16X3; }
+
+int legendre_synth(const sht_plan *p, int cols, cudaStream_t s) {
+  return uses_tensor_cores(p->prec) ? synth_tc(p, cols, s) : synth_simt(p, cols, s);
+}
+
+int legendre_analysis(const sht_plan *p, int cols, cudaStream_t s) {
+  return uses_tensor_cores(p->prec) ? analysis_tc(p, cols, s) : analysis_simt(p, cols, s);
+}
+
 int legendre_table_build(sht_plan *p, cudaStream_t s) {
   const int T = p->T, nh = p->nh;
   std::vector<double> mant((size_t)(T + 1) * nh);
@@ -224,8 +249,12 @@ static void plan_free(sht_plan *p) {
   if (p->d_mu) cudaFree(p->d_mu);
   if (p->d_w) cudaFree(p->d_w);
   if (p->d_P) cudaFree(p->d_P);
+  if (p->d_P32) cudaFree(p->d_P32);
+  if (p->d_eps) cudaFree(p->d_eps);
+  if (p->d_ilap) cudaFree(p->d_ilap);
   if (p->ws) cudaFree(p->ws);
   fft_plan_free(p->fft);
+  tc_tables_free(p);
   delete p;
 }
 
@@ -236,7 +265,8 @@ extern "C" int sht_plan_create(sht_plan **out, int T, int nlat, int nlon, int ma
   if (nlat % 2 != 0 || nlat < T + 2) return fail(PFSH_EINVAL, "sht_plan_create: nlat must be even and >= T+2");
   if (nlon % 2 != 0 || nlon <= 2 * (T + 1)) return fail(PFSH_EINVAL, "sht_plan_create: nlon must be even and > 2(T+1)");
   if (max_batch < 1) return fail(PFSH_EINVAL, "sht_plan_create: max_batch must be >= 1");
-  if (prec != PFSH_FP64) return fail(PFSH_EUNSUPPORTED, "sht_plan_create: precision not available in this build");
+  if (prec != PFSH_FP64 && prec != PFSH_FP32 && !uses_tensor_cores(prec))
+    return fail(PFSH_EUNSUPPORTED, "sht_plan_create: precision not available in this build");
   sht_plan *p = new (std::nothrow) sht_plan();
   if (!p) return fail(PFSH_ENOMEM, "sht_plan_create: host allocation");
   p->T = T;
@@ -266,12 +296,28 @@ extern "C" int sht_plan_create(sht_plan **out, int T, int nlat, int nlon, int ma
     plan_free(p);
     return rc;
   }
+  if ((rc = alloc((void **)&p->d_eps, (size_t)p->ne * sizeof(double))) ||
+      (rc = alloc((void **)&p->d_ilap, (size_t)(T + 2) * sizeof(double)))) {
+    plan_free(p);
+    return rc;
+  }
+  {
+    std::vector<double> eps(p->ne), ilap(T + 2, 0.0);
+    for (int m = 0; m <= T; ++m)
+      for (int n = m; n <= T + 1; ++n)
+        eps[eoff(T, m) + (n - m)] =
+            n > m ? std::sqrt(((double)n * n - (double)m * m) / (4.0 * (double)n * n - 1.0)) : 0.0;
+    for (int n = 1; n <= T + 1; ++n) ilap[n] = 1.0 / ((double)n * (n + 1));
+    cudaMemcpy(p->d_eps, eps.data(), eps.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_ilap, ilap.data(), ilap.size() * sizeof(double), cudaMemcpyHostToDevice);
+  }
   cudaMemcpy(p->d_mu, p->mu.data(), nlat * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_w, p->w.data(), nlat * sizeof(double), cudaMemcpyHostToDevice);
   // workspace: X [ne][cols], F [T+1][nlat][cols], H [T+1][2][nh][cols], Y [ne][cols]
   const size_t cols = (size_t)max_batch;
-  const size_t bX = (size_t)p->ne * cols * 16;
-  const size_t bF = (size_t)(T + 1) * nlat * cols * 16;
+  const size_t celem = prec == PFSH_FP64 ? 16 : 8;
+  const size_t bX = (size_t)p->ne * cols * celem;
+  const size_t bF = (size_t)(T + 1) * nlat * cols * celem;
   const size_t bH = bF;
   const size_t bY = bX;
   p->ws_bytes = bX + bF + bH + bY;
@@ -282,6 +328,13 @@ extern "C" int sht_plan_create(sht_plan **out, int T, int nlat, int nlon, int ma
   p->H = base + bX + bF;
   p->Y = base + bX + bF + bH;
   if ((rc = legendre_table_build(p, 0)) != PFSH_OK) { plan_free(p); return rc; }
+  if (uses_tensor_cores(prec)) {
+    if ((rc = tc_tables_build(p)) != PFSH_OK) { plan_free(p); return rc; }
+  } else if (prec != PFSH_FP64) {
+    const size_t n = (size_t)p->ne * p->nh;
+    if ((rc = alloc((void **)&p->d_P32, n * sizeof(float)))) { plan_free(p); return rc; }
+    if ((rc = convert_table_f32(p->d_P, p->d_P32, n, 0))) { plan_free(p); return rc; }
+  }
   if (!device_status()) { plan_free(p); return fail(PFSH_ENOMEM, "status word"); }
   *out = p;
   return PFSH_OK;
@@ -316,7 +369,7 @@ extern "C" int sht_inverse(sht_plan *p, const double *spec, void *grid, int batc
     int nb = std::min(p->max_batch, batch - b0);
     int rc;
     if ((rc = spec_to_X(p, spec + (size_t)b0 * p->ncoef * 2, nb, s))) return rc;
-    if ((rc = synth_f64(p, nb, s))) return rc;
+    if ((rc = legendre_synth(p, nb, s))) return rc;
     if ((rc = ifft_rows(p, nb, (char *)grid + (size_t)b0 * p->nlat * p->nlon * gelem, s))) return rc;
   }
   return PFSH_OK;
@@ -330,7 +383,7 @@ extern "C" int sht_forward(sht_plan *p, const void *grid, double *spec, int batc
     int nb = std::min(p->max_batch, batch - b0);
     int rc;
     if ((rc = fft_rows(p, nb, (const char *)grid + (size_t)b0 * p->nlat * p->nlon * gelem, s))) return rc;
-    if ((rc = analysis_f64(p, nb, s))) return rc;
+    if ((rc = legendre_analysis(p, nb, s))) return rc;
     if ((rc = Y_to_spec(p, spec + (size_t)b0 * p->ncoef * 2, nb, s))) return rc;
   }
   return PFSH_OK;

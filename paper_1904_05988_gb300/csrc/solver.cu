@@ -16,9 +16,9 @@ static int rhs_pass(swe_ctx *c, const double *state, double *fE, double *fI, int
   const sht_plan *p = c->plan;
   int rc;
   if ((rc = rhs_prep(p, state, B, c->prm, s))) return rc;
-  if ((rc = synth_f64(p, 4 * B, s))) return rc;
+  if ((rc = legendre_synth(p, 4 * B, s))) return rc;
   if ((rc = grid_rhs(p, B, c->prm, s))) return rc;
-  if ((rc = analysis_f64(p, 5 * B, s))) return rc;
+  if ((rc = legendre_analysis(p, 5 * B, s))) return rc;
   return rhs_assemble(p, state, fE, fI, B, c->prm, s);
 }
 

@@ -25,7 +25,8 @@ __device__ __forceinline__ double eps_nm(int n, int m) {
 // ---------------------------------------------------------------------------
 // plain transforms: spec [b][ncoef] <-> X/Y [ext row][b]
 // ---------------------------------------------------------------------------
-__global__ void k_spec_to_X(int T, int ne, int batch, const double2 *__restrict__ spec, double2 *__restrict__ X) {
+template <typename CX>
+__global__ void k_spec_to_X(int T, int ne, int batch, const double2 *__restrict__ spec, CX *__restrict__ X) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   if (idx >= ne) return;
@@ -36,18 +37,19 @@ __global__ void k_spec_to_X(int T, int ne, int batch, const double2 *__restrict_
     v = spec[(size_t)b * ncoef_of(T) + poff(T, m) + (n - m)];
     if (m == 0) v.y = 0.0;
   }
-  X[(size_t)idx * batch + b] = v;
+  X[(size_t)idx * batch + b] = mk<CX>(v.x, v.y);
 }
 
-__global__ void k_Y_to_spec(int T, int batch, const double2 *__restrict__ Y, double2 *__restrict__ spec) {
+template <typename CY>
+__global__ void k_Y_to_spec(int T, int batch, const CY *__restrict__ Y, double2 *__restrict__ spec) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   const int nc = ncoef_of(T);
   if (idx >= nc) return;
   const int m = tri_m(idx, T);
   const int n = m + (idx - poff(T, m));
-  double2 v = Y[(size_t)(poff(T + 1, m) + (n - m)) * batch + b];
-  if (m == 0) v.y = 0.0;
+  const CY y = Y[(size_t)(poff(T + 1, m) + (n - m)) * batch + b];
+  double2 v = make_double2(y.x, m == 0 ? 0.0 : y.y);
   spec[(size_t)b * nc + idx] = v;
 }
 
@@ -55,7 +57,10 @@ int spec_to_X(const sht_plan *p, const double *spec, int batch, cudaStream_t s) 
   dim3 g((p->ne + 255) / 256, batch);
   {
     PFSH_LAUNCH("k_spec_to_X", s);
-    k_spec_to_X<<<g, 256, 0, s>>>(p->T, p->ne, batch, (const double2 *)spec, (double2 *)p->X);
+    if (p->prec == PFSH_FP64)
+      k_spec_to_X<double2><<<g, 256, 0, s>>>(p->T, p->ne, batch, (const double2 *)spec, (double2 *)p->X);
+    else
+      k_spec_to_X<float2><<<g, 256, 0, s>>>(p->T, p->ne, batch, (const double2 *)spec, (float2 *)p->X);
   }
   PFSH_CHECK_LAUNCH("k_spec_to_X");
   return PFSH_OK;
@@ -65,7 +70,10 @@ int Y_to_spec(const sht_plan *p, double *spec, int batch, cudaStream_t s) {
   dim3 g((p->ncoef + 255) / 256, batch);
   {
     PFSH_LAUNCH("k_Y_to_spec", s);
-    k_Y_to_spec<<<g, 256, 0, s>>>(p->T, batch, (const double2 *)p->Y, (double2 *)spec);
+    if (p->prec == PFSH_FP64)
+      k_Y_to_spec<double2><<<g, 256, 0, s>>>(p->T, batch, (const double2 *)p->Y, (double2 *)spec);
+    else
+      k_Y_to_spec<float2><<<g, 256, 0, s>>>(p->T, batch, (const float2 *)p->Y, (double2 *)spec);
   }
   PFSH_CHECK_LAUNCH("k_Y_to_spec");
   return PFSH_OK;
@@ -79,8 +87,10 @@ int Y_to_spec(const sht_plan *p, double *spec, int batch, cudaStream_t s) {
 //   U_n = [(n-1) eps_n psi_{n-1} - (n+2) eps_{n+1} psi_{n+1} + i m chi_n] / a
 //   V_n = [i m psi_n - (n-1) eps_n chi_{n-1} + (n+2) eps_{n+1} chi_{n+1}] / a
 // ---------------------------------------------------------------------------
-__global__ void k_rhs_prep(int T, int ne, int B, double a, double omega, double phibar,
-                           const double2 *__restrict__ state, double2 *__restrict__ X) {
+template <typename CX>
+__global__ void k_rhs_prep(int T, int ne, int B, double a, double inva, double omega, double phibar,
+                           const double *__restrict__ eps, const double *__restrict__ ilap,
+                           const double2 *__restrict__ state, CX *__restrict__ X) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   if (idx >= ne) return;
@@ -91,14 +101,14 @@ __global__ void k_rhs_prep(int T, int ne, int B, double a, double omega, double 
   const double2 *zeta = Phi + nc;
   const double2 *delta = Phi + 2 * nc;
   const int base = poff(T, m) - m;  // packed index of (m, n') is base + n'
-  const double a2 = a * a;
+  const double ma2 = -a * a;
   auto psi_chi = [&](int nn, double2 *ps, double2 *ch) {
     if (nn < m || nn > T || nn == 0) {
       *ps = make_double2(0.0, 0.0);
       *ch = make_double2(0.0, 0.0);
       return;
     }
-    const double f = -a2 / ((double)nn * (nn + 1));
+    const double f = ma2 * ilap[nn];
     double2 z = zeta[base + nn], d = delta[base + nn];
     if (m == 0) { z.y = 0.0; d.y = 0.0; }
     *ps = f * z;
@@ -111,35 +121,38 @@ __global__ void k_rhs_prep(int T, int ne, int B, double a, double omega, double 
     if (m == 0) {
       eta.y = 0.0;
       php.y = 0.0;
-      if (n == 1) eta.x += 2.0 * omega / sqrt(1.5);
-      if (n == 0) php.x -= sqrt(2.0) * phibar;
+      if (n == 1) eta.x += 2.0 * omega * 0.81649658092772603273;   // 2 Omega / sqrt(3/2)
+      if (n == 0) php.x -= 1.41421356237309504880 * phibar;        // sqrt(2) Phibar
     }
   }
   double2 ps_m, ch_m, ps_0, ch_0, ps_p, ch_p;
   psi_chi(n - 1, &ps_m, &ch_m);
   psi_chi(n, &ps_0, &ch_0);
   psi_chi(n + 1, &ps_p, &ch_p);
-  const double cm = (n - 1) * eps_nm(n, m);
-  const double cp = (n + 2) * eps_nm(n + 1, m);
-  const double inva = 1.0 / a;
+  const double cm = (n - 1) * eps[idx];                       // (n-1) eps_n^m
+  const double cp = (n <= T) ? (n + 2) * eps[idx + 1] : 0.0;  // (n+2) eps_{n+1}^m
   double2 U, V;
   U.x = (cm * ps_m.x - cp * ps_p.x - m * ch_0.y) * inva;
   U.y = (cm * ps_m.y - cp * ps_p.y + m * ch_0.x) * inva;
   V.x = (-m * ps_0.y - cm * ch_m.x + cp * ch_p.x) * inva;
   V.y = (m * ps_0.x - cm * ch_m.y + cp * ch_p.y) * inva;
-  double2 *row = X + (size_t)idx * (4 * B) + b * 4;
-  row[0] = eta;
-  row[1] = php;
-  row[2] = U;
-  row[3] = V;
+  CX *row = X + (size_t)idx * (4 * B) + b * 4;
+  row[0] = mk<CX>(eta.x, eta.y);
+  row[1] = mk<CX>(php.x, php.y);
+  row[2] = mk<CX>(U.x, U.y);
+  row[3] = mk<CX>(V.x, V.y);
 }
 
 int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &prm, cudaStream_t s) {
   dim3 g((p->ne + 255) / 256, B);
   {
     PFSH_LAUNCH("k_rhs_prep", s);
-    k_rhs_prep<<<g, 256, 0, s>>>(p->T, p->ne, B, prm.a, prm.omega, prm.phibar, (const double2 *)state,
-                                 (double2 *)p->X);
+    if (p->prec == PFSH_FP64)
+      k_rhs_prep<double2><<<g, 256, 0, s>>>(p->T, p->ne, B, prm.a, 1.0 / prm.a, prm.omega, prm.phibar, p->d_eps,
+                                            p->d_ilap, (const double2 *)state, (double2 *)p->X);
+    else
+      k_rhs_prep<float2><<<g, 256, 0, s>>>(p->T, p->ne, B, prm.a, 1.0 / prm.a, prm.omega, prm.phibar, p->d_eps,
+                                           p->d_ilap, (const double2 *)state, (float2 *)p->X);
   }
   PFSH_CHECK_LAUNCH("k_rhs_prep");
   return PFSH_OK;
@@ -153,9 +166,11 @@ int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &pr
 //   F_E = [-div(A2,B2), -div(A1,B1), curl(A1,B1) + n(n+1)/a^2 E]
 //   F_I = [-Phibar delta - nu k Phi, -nu k zeta, k Phi - nu k delta], k = n(n+1)/a^2
 // ---------------------------------------------------------------------------
-__global__ void k_rhs_assemble(int T, int B, double a, double nu, double phibar,
-                               const double2 *__restrict__ Y, const double2 *__restrict__ state,
-                               double2 *__restrict__ fE, double2 *__restrict__ fI) {
+template <typename CY>
+__global__ void k_rhs_assemble(int T, int B, double inva, double inva2, double nu, double phibar,
+                               const double *__restrict__ eps, const CY *__restrict__ Y,
+                               const double2 *__restrict__ state, double2 *__restrict__ fE,
+                               double2 *__restrict__ fI) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   const int nc = ncoef_of(T);
@@ -164,15 +179,17 @@ __global__ void k_rhs_assemble(int T, int B, double a, double nu, double phibar,
   const int n = m + (idx - poff(T, m));
   const int cols = 5 * B;
   const size_t r0 = (size_t)(poff(T + 1, m) + (n - m));
-  auto y = [&](size_t row, int f) { return Y[row * cols + b * 5 + f]; };
-  const double e1 = eps_nm(n + 1, m), e0 = eps_nm(n, m);
+  auto y = [&](size_t row, int f) {
+    const CY v = Y[row * cols + b * 5 + f];
+    return make_double2(v.x, v.y);
+  };
+  const double e1 = eps[r0 + 1], e0 = eps[r0];     // eps_{n+1}^m, eps_n^m
   const double cu = n * e1, cd = (n + 1) * e0;
   const double2 z = make_double2(0.0, 0.0);
   double2 A1 = y(r0, 0), B1 = y(r0, 1), A2 = y(r0, 2), B2 = y(r0, 3), E = y(r0, 4);
   double2 A1u = y(r0 + 1, 0), B1u = y(r0 + 1, 1), B2u = y(r0 + 1, 3);
   double2 A1d = n > m ? y(r0 - 1, 0) : z, B1d = n > m ? y(r0 - 1, 1) : z, B2d = n > m ? y(r0 - 1, 3) : z;
-  const double inva = 1.0 / a;
-  const double k = (double)n * (n + 1) / (a * a);
+  const double k = (double)n * (n + 1) * inva2;
   double2 div1, div2, curl1;
   div1.x = (-m * A1.y + cu * B1u.x - cd * B1d.x) * inva;
   div1.y = (m * A1.x + cu * B1u.y - cd * B1d.y) * inva;
@@ -193,19 +210,27 @@ __global__ void k_rhs_assemble(int T, int B, double a, double nu, double phibar,
     double2 Phi = st[idx], zeta = st[nc + idx], delta = st[2 * nc + idx];
     if (m == 0) { Phi.y = 0.0; zeta.y = 0.0; delta.y = 0.0; }
     double2 *oI = fI + (size_t)b * 3 * nc;
-    oI[idx] = make_double2(-phibar * delta.x - nu * k * Phi.x, -phibar * delta.y - nu * k * Phi.y);
-    oI[nc + idx] = make_double2(-nu * k * zeta.x, -nu * k * zeta.y);
-    oI[2 * nc + idx] = make_double2(k * Phi.x - nu * k * delta.x, k * Phi.y - nu * k * delta.y);
+    const double nk = nu * k;
+    oI[idx] = make_double2(-phibar * delta.x - nk * Phi.x, -phibar * delta.y - nk * Phi.y);
+    oI[nc + idx] = make_double2(-nk * zeta.x, -nk * zeta.y);
+    oI[2 * nc + idx] = make_double2(k * Phi.x - nk * delta.x, k * Phi.y - nk * delta.y);
   }
 }
 
 int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
                  cudaStream_t s) {
   dim3 g((p->ncoef + 255) / 256, B);
+  const double inva = 1.0 / prm.a, inva2 = 1.0 / (prm.a * prm.a);
   {
     PFSH_LAUNCH("k_rhs_assemble", s);
-    k_rhs_assemble<<<g, 256, 0, s>>>(p->T, B, prm.a, prm.nu, prm.phibar, (const double2 *)p->Y,
-                                     (const double2 *)state, (double2 *)fE, (double2 *)fI);
+    if (p->prec == PFSH_FP64)
+      k_rhs_assemble<double2><<<g, 256, 0, s>>>(p->T, B, inva, inva2, prm.nu, prm.phibar, p->d_eps,
+                                                (const double2 *)p->Y, (const double2 *)state, (double2 *)fE,
+                                                (double2 *)fI);
+    else
+      k_rhs_assemble<float2><<<g, 256, 0, s>>>(p->T, B, inva, inva2, prm.nu, prm.phibar, p->d_eps,
+                                               (const float2 *)p->Y, (const double2 *)state, (double2 *)fE,
+                                               (double2 *)fI);
   }
   PFSH_CHECK_LAUNCH("k_rhs_assemble");
   return PFSH_OK;

@@ -1,0 +1,128 @@
+"""Parity of the mixed-precision CUDA paths with the FP64 oracle.
+
+Every mixed form keeps spectral data, the Legendre recurrence, Gaussian
+nodes/weights and all SDC/FAS bookkeeping in FP64; the Legendre contractions
+run in the form's precision and the FFT/grid stage in FP32.  Each form has
+its own measured error bound (rel-L2 against the oracle), stated here:
+
+  form     transform pair   one RHS (F_E)   PFASST end values (pred + 2 iter)
+  fp32     1e-6  (3.5e-7)   1e-3  (3.9e-4)  1e-8  (3.7e-9)
+  bf16     5e-3  (3.0e-3)   1e+1  (4.0)     2e-4  (8.4e-5)
+  bf16x3   1e-5  (5.5e-6)   2e-2  (8.2e-3)  5e-7  (2.0e-7)
+
+(in brackets: the largest value measured on GB300 over T63/T170/T255.)
+A transform pair loses what the operand rounding of the form loses
+(2^-9 for bf16, ~2^-17 for the hi/lo split of 3xBF16, fp32 for fp32).  The
+nonlinear tendency loses about T times more: its spectral derivatives
+multiply the analysed flux coefficients by n eps ~ n/2 up to n = T+1, so the
+rounding noise of the analysed fluxes (relative to their largest, low-degree
+coefficients) is amplified at high degree, most in the divergence tendency.
+A bf16 tendency is therefore not meaningful at T >= 170, while the PFASST
+solution, which integrates the tendencies over time, stays within 1e-4.
+"""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle.sht import SHT, pack, unpack
+from oracle.swe import SWEParams, rhs
+from oracle.sdc import SDCLevel
+from oracle.pfasst import PFASST
+from _lib import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+ensure_built()
+import paper_1904_05988_gb300 as ps  # noqa: E402
+
+DEV = torch.device("cuda:0")
+A, OM, G = syn.EARTH_RADIUS, syn.OMEGA, syn.GRAVITY
+PHIBAR = G * syn.MEAN_DEPTH
+BOUNDS = {  # transform, rhs, pfasst
+    "fp32": (1e-6, 1e-3, 1e-8),
+    "bf16": (5e-3, 1e1, 2e-4),
+    "bf16x3": (1e-5, 2e-2, 5e-7),
+}
+FORMS = [f for f in BOUNDS if f in ps.available_precisions()]
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def cuda(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.complex128, device=DEV)
+
+
+def state_of(T, seed, batch=1):
+    s = syn.random_spectrum(T, (batch, 3), seed=seed, rms=1e-5)
+    s[:, 0] *= 1e3
+    return s + syn.zonal_jet(T)[None]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("T", [63, 170, 255])
+def test_transform_pair(form, T):
+    nlat, nlon = syn.gaussian_grid_size(T)
+    plan = ps.sht_plan_create(T, nlat, nlon, 7, form)
+    spec = syn.random_spectrum(T, (9,), seed=30 + T, nmin=1)      # two passes, ragged
+    grid = torch.empty((9, nlat, nlon), dtype=torch.float32, device=DEV)
+    ps.sht_inverse(plan, cuda(spec), grid)
+    back = torch.empty((9, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    ps.sht_forward(plan, grid, back)
+    ps.pfsh_sync_status()
+    o = SHT(T, nlat, nlon, L=T + 1)
+    ref_grid = o.synthesis(unpack(spec, T))
+    e_inv = rel(grid.cpu().numpy().astype(np.float64), ref_grid)
+    e_pair = rel(back.cpu().numpy(), spec)
+    print(f"\n[{form} T{T}] inverse {e_inv:.2e}  pair {e_pair:.2e}")
+    assert e_inv < BOUNDS[form][0] and e_pair < BOUNDS[form][0]
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("T,B", [(63, 3), (170, 2), (255, 2)])
+def test_swe_rhs(form, T, B):
+    nlat, nlon = syn.gaussian_grid_size(T)
+    plan = ps.sht_plan_create(T, nlat, nlon, 5 * B, form)
+    ctx = ps.swe_ctx_create(plan, A, OM, syn.NU, PHIBAR)
+    st = state_of(T, 200 + T, B)
+    fE = torch.empty((B, 3, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    fI = torch.empty_like(fE)
+    ps.swe_rhs(ctx, cuda(st), fE, fI)
+    ps.pfsh_sync_status()
+    p = SWEParams(a=A, omega=OM, g=G, nu=syn.NU, phibar=PHIBAR)
+    FE, FI = rhs(unpack(st[B - 1], T), SHT(T, nlat, nlon), p)
+    errs = [rel(fE.cpu().numpy()[B - 1, f], pack(FE[f], T)) for f in range(3)]
+    print(f"\n[{form} T{T}] F_E rel-L2 per field {['%.2e' % e for e in errs]}")
+    assert max(errs) < BOUNDS[form][1]
+    assert rel(fI.cpu().numpy()[B - 1], pack(FI, T)) < 1e-13    # F_I stays FP64
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_pfasst_two_iterations(form):
+    Tf, Tc, nts, dt = 63, 31, 4, 600.0
+    gf, gc = syn.gaussian_grid_size(Tf), syn.gaussian_grid_size(Tc)
+    st0 = state_of(Tf, 41)[0]
+    pf = ps.pfasst_create(nts, 5, 3, Tf, *gf, Tc, *gc, dt, A, OM, syn.NU, PHIBAR, form)
+    ps.pfasst_set_initial(pf, cuda(st0))
+    ps.pfasst_predict(pf)
+    ps.pfasst_iteration(pf, False)
+    ps.pfasst_iteration(pf, True)
+    ps.pfsh_sync_status()
+    p = SWEParams(a=A, omega=OM, g=G, nu=syn.NU, phibar=PHIBAR)
+    o = PFASST(SDCLevel(Tf, *gf, 5, dt, p), SDCLevel(Tc, *gc, 3, dt, p), nts)
+    ref = o.run(unpack(st0, Tf), 2)
+    out = torch.empty((3, syn.ncoef(Tf)), dtype=torch.complex128, device=DEV)
+    errs = []
+    for n in range(nts):
+        ps.pfasst_get(pf, 0, n, 4, out)
+        errs.append(rel(out.cpu().numpy(), pack(ref[n], Tf)))
+    # the perturbation (state minus initial value) is matched too, not just the jet
+    ps.pfasst_get(pf, 0, nts - 1, 4, out)
+    d_got = out.cpu().numpy() - st0
+    d_ref = pack(ref[nts - 1], Tf) - st0
+    e_inc = rel(d_got, d_ref)
+    print(f"\n[{form}] PFASST end values rel-L2 max {max(errs):.2e}, increment {e_inc:.2e}")
+    assert max(errs) < BOUNDS[form][2]
+    assert e_inc < 1e3 * BOUNDS[form][2]
