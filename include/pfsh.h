@@ -205,6 +205,34 @@ int pfasst_get(pfasst *pf, int level, int slice, int node, double *out,
                pfsh_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
+/* Synthesis without any device allocation (no counterpart in the paper)     */
+/* ------------------------------------------------------------------------ */
+
+/* FP64 synthesis (same result as sht_inverse on an FP64 plan) for callers
+ * that may not allocate device memory: for example a loop running under a
+ * no-allocation policy after start-up, or an application whose memory pool
+ * owns every device byte, and which therefore cannot create an sht_plan
+ * (plans get their tables and workspace from cudaMalloc).  Only the caller's
+ * spec [batch][ncoef(T)][2] (device, input) and grid [batch][nlat][nlon]
+ * (device, double, output) are used; nothing is allocated.  The Legendre
+ * functions are evaluated on the fly; Gaussian latitudes, twiddles and the
+ * intermediate Fourier coefficients live in a fixed 4 MiB device array
+ * inside this library, which every GPU that loads the library keeps until
+ * the process exits.
+ * Limits: 1 <= T <= 127, nlat even >= T+2, nlon even > 2(T+1) with prime
+ * factors <= 61, and (T+1)*nlat*batch*16 bytes (+ nlat*8 + nlon*16, each
+ * rounded up to 256) <= 4 MiB; larger requests return PFSH_EINVAL before
+ * any work is queued (split the batch).
+ * The first call on a device looks up the device address of that array
+ * (cudaGetSymbolAddress) and remembers it; make that first call before any
+ * stream capture.  All calls share the one array and every call rewrites
+ * what it reads, so no state carries over between calls; calls whose work
+ * overlaps on the GPU (different streams, no ordering) race on it.
+ * Asynchronous on `stream` like the other compute calls. */
+int sht_inverse_noalloc(int T, int nlat, int nlon, const double *spec,
+                        double *grid, int batch, pfsh_stream_t stream);
+
+/* ------------------------------------------------------------------------ */
 /* Status                                                                    */
 /* ------------------------------------------------------------------------ */
 

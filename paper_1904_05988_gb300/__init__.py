@@ -29,7 +29,7 @@ EXPORTED = ["sht_plan_create", "sht_plan_destroy", "sht_plan_query", "sht_invers
             "sdc_level_create", "sdc_level_destroy", "sdc_spread", "sdc_sweep",
             "pfasst_create", "pfasst_destroy", "pfasst_set_initial", "pfasst_predict",
             "pfasst_iteration", "pfasst_get", "pfsh_sync_status", "pfsh_last_error",
-            "pfsh_kernel_launches", "pfsh_profiler_enable", "pfsh_profiler_report"]
+            "pfsh_kernel_launches", "pfsh_profiler_enable", "pfsh_profiler_report", "sht_inverse_noalloc"]
 
 
 class PfshError(RuntimeError):
@@ -87,6 +87,7 @@ _sig = {
     "pfasst_iteration": [c_void_p, c_int, c_void_p],
     "pfasst_get": [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p],
     "pfsh_sync_status": [c_void_p],
+    "sht_inverse_noalloc": [c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p],
 }
 for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
@@ -324,3 +325,13 @@ def pfsh_profiler_report() -> dict:
     buf = ctypes.create_string_buffer(need + 16)
     _lib.pfsh_profiler_report(buf, len(buf))
     return json.loads(buf.value.decode())
+
+
+def sht_inverse_noalloc(T: int, nlat: int, nlon: int, spec: torch.Tensor, grid: torch.Tensor,
+                        stream=None) -> torch.Tensor:
+    """FP64 synthesis that allocates no device memory (see include/pfsh.h):
+    spec complex128 [batch, ncoef(T)] -> grid float64 [batch, nlat, nlon]."""
+    batch = spec.numel() // ncoef(T)
+    _check(_lib.sht_inverse_noalloc(T, nlat, nlon, _ptr(spec, torch.complex128, batch * ncoef(T)),
+                                    _ptr(grid, torch.float64, batch * nlat * nlon), batch, _stream(stream)))
+    return grid

@@ -280,6 +280,26 @@ int ifft_rows(const sht_plan *p, int cols, void *grid, cudaStream_t s) {
   return PFSH_OK;
 }
 
+// Inverse longitude transform of F[m][lat][cols] (complex fp64) into
+// grid[cols][lat][lon] with caller-supplied twiddles and radix list; used by
+// the allocation-free synthesis entry point.
+int ifft_rows_f64_raw(int N, int npass, const int *radix, int T, int nlat, int cols, const double2 *F,
+                      const double2 *tw, double *grid, cudaStream_t s) {
+  FftArgs f;
+  f.N = N;
+  f.npass = npass;
+  for (int i = 0; i < kMaxPasses; ++i) f.radix[i] = i < npass ? radix[i] : 1;
+  const size_t sm = 2 * (size_t)N * sizeof(double2);
+  int rc = set_smem((const void *)k_ifft_rows<double>, sm);
+  if (rc) return rc;
+  {
+    PFSH_LAUNCH("k_ifft_rows", s);
+    k_ifft_rows<double><<<dim3(nlat / 2, cols), 256, sm, s>>>(f, T, nlat, cols, F, tw, grid);
+  }
+  PFSH_CHECK_LAUNCH("k_ifft_rows");
+  return PFSH_OK;
+}
+
 int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s) {
   FftArgs f = fft_args(p->fft);
   dim3 g(p->nh, cols);

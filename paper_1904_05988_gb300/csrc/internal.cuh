@@ -195,6 +195,8 @@ bool uses_tensor_cores(int prec);
 int ifft_rows(const sht_plan *p, int cols, void *grid, cudaStream_t s);        // F -> grid
 int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s);   // grid -> H
 int grid_rhs(const sht_plan *p, int B, const swe_params &prm, cudaStream_t s); // F -> H (RHS)
+int ifft_rows_f64_raw(int N, int npass, const int *radix, int T, int nlat, int cols, const double2 *F,
+                      const double2 *tw, double *grid, cudaStream_t s);
 
 // spectral pre/post processing
 int spec_to_X(const sht_plan *p, const double *spec, int batch, cudaStream_t s);
