@@ -9,14 +9,10 @@
 // direct DFT), with twiddles exp(-2 pi i e/N) generated on the host in FP64.
 #include <algorithm>
 
+#include "fft_core.cuh"
 #include "internal.cuh"
 
 namespace pfsh {
-
-struct FftArgs {
-  int N, npass;
-  int radix[kMaxPasses];
-};
 
 static FftArgs fft_args(const FftPlan &f) {
   FftArgs a;
@@ -26,101 +22,19 @@ static FftArgs fft_args(const FftPlan &f) {
   return a;
 }
 
-template <typename C> __device__ __forceinline__ C twiddle(const C *tw, int e, bool inv) {
-  C w = tw[e];
-  if (inv) w.y = -w.y;
-  return w;
-}
-
-// nfft transforms of length N stored back to back in `a`; `b` is scratch of
-// the same size.  Returns the buffer that holds the result.  Must be called
-// by every thread of the block.
-template <typename C>
-__device__ C *fft_smem(C *a, C *b, int nfft, const FftArgs &f, const C *__restrict__ tw, bool inv) {
-  const int N = f.N;
-  int Ns = 1;
-  for (int p = 0; p < f.npass; ++p) {
-    const int R = f.radix[p];
-    const int NR = N / R;
-    const int stride = N / (Ns * R);
-    const int total = nfft * NR;
-    for (int t = threadIdx.x; t < total; t += blockDim.x) {
-      const int fi = t / NR;
-      const int j = t - fi * NR;
-      const C *x = a + fi * N;
-      C *y = b + fi * N;
-      const int k = j % Ns;
-      const int idx = (j / Ns) * Ns * R + k;
-      if (R == 4) {
-        C v0 = x[j];
-        C v1 = cmul(x[j + NR], twiddle(tw, k * stride, inv));
-        C v2 = cmul(x[j + 2 * NR], twiddle(tw, 2 * k * stride, inv));
-        C v3 = cmul(x[j + 3 * NR], twiddle(tw, 3 * k * stride, inv));
-        C s02 = v0 + v2, d02 = v0 - v2, s13 = v1 + v3, d13 = v1 - v3;
-        C rot = times_i(d13);  // i (v1 - v3)
-        y[idx] = s02 + s13;
-        y[idx + 2 * Ns] = s02 - s13;
-        if (!inv) {
-          y[idx + Ns] = d02 - rot;
-          y[idx + 3 * Ns] = d02 + rot;
-        } else {
-          y[idx + Ns] = d02 + rot;
-          y[idx + 3 * Ns] = d02 - rot;
-        }
-      } else if (R == 2) {
-        C v0 = x[j];
-        C v1 = cmul(x[j + NR], twiddle(tw, k * stride, inv));
-        y[idx] = v0 + v1;
-        y[idx + Ns] = v0 - v1;
-      } else if (R == 3) {
-        C v0 = x[j];
-        C v1 = cmul(x[j + NR], twiddle(tw, k * stride, inv));
-        C v2 = cmul(x[j + 2 * NR], twiddle(tw, 2 * k * stride, inv));
-        typedef decltype(v0.x) Rt;
-        const Rt c = (Rt)-0.5;
-        const Rt s = inv ? (Rt)0.86602540378443864676 : (Rt)-0.86602540378443864676;
-        C t = v1 + v2, u = v1 - v2;
-        C base = v0 + c * t;
-        C su = times_i(s * u);
-        y[idx] = v0 + t;
-        y[idx + Ns] = base + su;
-        y[idx + 2 * Ns] = base - su;
-      } else {
-        // direct DFT of length R (5 and odd primes up to 61)
-        for (int q = 0; q < R; ++q) {
-          C acc = mk<C>(0.0, 0.0);
-          for (int r = 0; r < R; ++r) {
-            C v = x[j + r * NR];
-            if (r) v = cmul(v, twiddle(tw, k * r * stride, inv));
-            const int e = (r * q) % R;
-            acc = acc + (e ? cmul(v, twiddle(tw, e * NR, inv)) : v);
-          }
-          y[idx + q * Ns] = acc;
-        }
-      }
-    }
-    __syncthreads();
-    C *tmp = a;
-    a = b;
-    b = tmp;
-    Ns *= R;
-  }
-  return a;
-}
-
 // ---------------------------------------------------------------------------
 // inverse: F[m][lat][col] -> grid[col][lat][lon]
 // ---------------------------------------------------------------------------
-template <typename Rl>
+template <typename Rl, typename Shape>
 __global__ void k_ifft_rows(FftArgs f, int T, int nlat, int cols, const typename cpx<Rl>::t *__restrict__ F,
                             const typename cpx<Rl>::t *__restrict__ tw, Rl *__restrict__ grid) {
   typedef typename cpx<Rl>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = Shape::n(f), NP = padded(N);
   C *a = reinterpret_cast<C *>(smem_raw);
-  C *b = a + f.N;
+  C *b = a + NP;
   const int j = blockIdx.x, col = blockIdx.y, js = nlat - 1 - j;
-  const int N = f.N;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) a[k] = mk<C>(0.0, 0.0);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) a[sidx(k)] = mk<C>(0.0, 0.0);
   __syncthreads();
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
     C fn = F[((size_t)m * nlat + j) * cols + col];
@@ -128,16 +42,16 @@ __global__ void k_ifft_rows(FftArgs f, int T, int nlat, int cols, const typename
     if (m == 0) {
       a[0] = mk<C>(fn.x, fs.x);
     } else {
-      a[m] = mk<C>(fn.x - fs.y, fn.y + fs.x);
-      a[N - m] = mk<C>(fn.x + fs.y, -fn.y + fs.x);
+      a[sidx(m)] = mk<C>(fn.x - fs.y, fn.y + fs.x);
+      a[sidx(N - m)] = mk<C>(fn.x + fs.y, -fn.y + fs.x);
     }
   }
   __syncthreads();
-  C *r = fft_smem<C>(a, b, 1, f, tw, true);
+  C *r = Shape::run(f, a, b, 1, tw, true);
   Rl *gn = grid + ((size_t)col * nlat + j) * N;
   Rl *gs = grid + ((size_t)col * nlat + js) * N;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    C z = r[k];
+    C z = r[sidx(k)];
     gn[k] = z.x;
     gs[k] = z.y;
   }
@@ -151,8 +65,8 @@ __device__ __forceinline__ void unpack_write(const C *Z, int N, int T, int j, in
                                              Rl wj, C *__restrict__ H) {
   const Rl half = (Rl)0.5 / (Rl)N;
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
-    C zm = Z[m];
-    C zc = cconj(Z[m == 0 ? 0 : N - m]);
+    C zm = Z[sidx(m)];
+    C zc = cconj(Z[sidx(m == 0 ? 0 : N - m)]);
     C gn = half * (zm + zc);              // north spectrum
     C gs = half * times_i(zc - zm);       // south spectrum: (zm - zc) / (2i)
     C he = wj * (gn + gs), ho = wj * (gn - gs);
@@ -161,20 +75,21 @@ __device__ __forceinline__ void unpack_write(const C *Z, int N, int T, int j, in
   }
 }
 
-template <typename Rl>
+template <typename Rl, typename Shape>
 __global__ void k_fft_rows(FftArgs f, int T, int nlat, int cols, const Rl *__restrict__ grid,
                            const double *__restrict__ w, const typename cpx<Rl>::t *__restrict__ tw,
                            typename cpx<Rl>::t *__restrict__ H) {
   typedef typename cpx<Rl>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int N = Shape::n(f), NP = padded(N);
   C *a = reinterpret_cast<C *>(smem_raw);
-  C *b = a + f.N;
-  const int j = blockIdx.x, col = blockIdx.y, js = nlat - 1 - j, N = f.N;
+  C *b = a + NP;
+  const int j = blockIdx.x, col = blockIdx.y, js = nlat - 1 - j;
   const Rl *gn = grid + ((size_t)col * nlat + j) * N;
   const Rl *gs = grid + ((size_t)col * nlat + js) * N;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) a[k] = mk<C>(gn[k], gs[k]);
+  for (int k = threadIdx.x; k < N; k += blockDim.x) a[sidx(k)] = mk<C>(gn[k], gs[k]);
   __syncthreads();
-  C *r = fft_smem<C>(a, b, 1, f, tw, false);
+  C *r = Shape::run(f, a, b, 1, tw, false);
   unpack_write<C, Rl>(r, N, T, j, nlat / 2, cols, col, (Rl)w[j], H);
 }
 
@@ -184,57 +99,59 @@ __global__ void k_fft_rows(FftArgs f, int T, int nlat, int cols, const Rl *__res
 //   B2 = Phi' V/(1-mu^2), E = (U^2+V^2)/(2(1-mu^2))
 // F columns: b*4 + f ; H columns: b*5 + f
 // ---------------------------------------------------------------------------
-template <typename Rl>
-__global__ void k_grid_rhs(FftArgs f, int T, int nlat, int B, const typename cpx<Rl>::t *__restrict__ F,
-                           const double *__restrict__ mu, const double *__restrict__ w,
-                           const typename cpx<Rl>::t *__restrict__ tw, typename cpx<Rl>::t *__restrict__ H) {
+template <typename Rl, typename Shape>
+__global__ void __launch_bounds__(256) k_grid_rhs(FftArgs f, int T, int nlat, int B,
+                                                  const typename cpx<Rl>::t *__restrict__ F,
+                                                  const double *__restrict__ mu, const double *__restrict__ w,
+                                                  const typename cpx<Rl>::t *__restrict__ tw,
+                                                  typename cpx<Rl>::t *__restrict__ H) {
   typedef typename cpx<Rl>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = f.N;
-  C *A = reinterpret_cast<C *>(smem_raw);  // 5N
-  C *Bf = A + 5 * N;                        // 5N
+  const int N = Shape::n(f), NP = padded(N);
+  C *A = reinterpret_cast<C *>(smem_raw);  // 5 padded transforms
+  C *Bf = A + 5 * NP;                       // 5 padded transforms
   const int j = blockIdx.x, b = blockIdx.y, js = nlat - 1 - j;
   const int colsF = 4 * B, colsH = 5 * B;
-  for (int k = threadIdx.x; k < 4 * N; k += blockDim.x) A[k] = mk<C>(0.0, 0.0);
+  for (int t = threadIdx.x; t < 4 * NP; t += blockDim.x) A[t] = mk<C>(0.0, 0.0);
   __syncthreads();
   for (int t = threadIdx.x; t < 4 * (T + 1); t += blockDim.x) {
-    const int fld = t / (T + 1), m = t - fld * (T + 1);
+    const int m = t >> 2, fld = t & 3;     // consecutive threads: the 4 fields of one m
     C fn = F[((size_t)m * nlat + j) * colsF + b * 4 + fld];
     C fs = F[((size_t)m * nlat + js) * colsF + b * 4 + fld];
-    C *z = A + fld * N;
+    C *z = A + fld * NP;
     if (m == 0) {
       z[0] = mk<C>(fn.x, fs.x);
     } else {
-      z[m] = mk<C>(fn.x - fs.y, fn.y + fs.x);
-      z[N - m] = mk<C>(fn.x + fs.y, -fn.y + fs.x);
+      z[sidx(m)] = mk<C>(fn.x - fs.y, fn.y + fs.x);
+      z[sidx(N - m)] = mk<C>(fn.x + fs.y, -fn.y + fs.x);
     }
   }
   __syncthreads();
-  C *g = fft_smem<C>(A, Bf, 4, f, tw, true);
+  C *g = Shape::run(f, A, Bf, 4, tw, true);
   C *o = (g == A) ? Bf : A;
   const double x = mu[j];
   const Rl inv = (Rl)(1.0 / ((1.0 - x) * (1.0 + x)));
+  const Rl h = (Rl)0.5 * inv;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    C eta = g[k], php = g[N + k], U = g[2 * N + k], V = g[3 * N + k];
-    Rl etaU_n = eta.x * U.x * inv, etaU_s = eta.y * U.y * inv;
-    Rl etaV_n = eta.x * V.x * inv, etaV_s = eta.y * V.y * inv;
-    o[k] = mk<C>(etaU_n, etaU_s);
-    o[N + k] = mk<C>(etaV_n, etaV_s);
-    o[2 * N + k] = mk<C>(php.x * U.x * inv, php.y * U.y * inv);
-    o[3 * N + k] = mk<C>(php.x * V.x * inv, php.y * V.y * inv);
-    const Rl h = (Rl)0.5 * inv;
-    o[4 * N + k] = mk<C>((U.x * U.x + V.x * V.x) * h, (U.y * U.y + V.y * V.y) * h);
+    const int e = sidx(k);
+    const C eta = g[e], php = g[NP + e], U = g[2 * NP + e], V = g[3 * NP + e];
+    const Rl Ui = U.x * inv, Us = U.y * inv, Vi = V.x * inv, Vs = V.y * inv;
+    o[e] = mk<C>(eta.x * Ui, eta.y * Us);
+    o[NP + e] = mk<C>(eta.x * Vi, eta.y * Vs);
+    o[2 * NP + e] = mk<C>(php.x * Ui, php.y * Us);
+    o[3 * NP + e] = mk<C>(php.x * Vi, php.y * Vs);
+    o[4 * NP + e] = mk<C>((U.x * U.x + V.x * V.x) * h, (U.y * U.y + V.y * V.y) * h);
   }
   __syncthreads();
-  C *Z = fft_smem<C>(o, g, 5, f, tw, false);
+  C *Z = Shape::run(f, o, g, 5, tw, false);
   const Rl half = (Rl)0.5 / (Rl)N;
   const Rl wj = (Rl)w[j];
   const int nh = nlat / 2;
   for (int t = threadIdx.x; t < 5 * (T + 1); t += blockDim.x) {
-    const int fld = t / (T + 1), m = t - fld * (T + 1);
-    const C *z = Z + fld * N;
-    C zm = z[m];
-    C zc = cconj(z[m == 0 ? 0 : N - m]);
+    const int m = t / 5, fld = t - 5 * m;   // consecutive threads: the 5 fields of one m
+    const C *z = Z + fld * NP;
+    C zm = z[sidx(m)];
+    C zc = cconj(z[sidx(m == 0 ? 0 : N - m)]);
     C gn = half * (zm + zc);
     C gs = half * times_i(zc - zm);
     C he = wj * (gn + gs), ho = wj * (gn - gs);
@@ -246,38 +163,29 @@ __global__ void k_grid_rhs(FftArgs f, int T, int nlat, int B, const typename cpx
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
-static int set_smem(const void *fn, size_t bytes) {
-  if (bytes > 48 * 1024) {
-    cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-    if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
-  }
-  return PFSH_OK;
+static int set_smem(const void *fn, size_t bytes) { return ensure_smem(fn, bytes); }
+
+template <typename Rl>
+static int ifft_launch(const FftArgs &f, int T, int nlat, int cols, const typename cpx<Rl>::t *F,
+                       const typename cpx<Rl>::t *tw, Rl *grid, cudaStream_t s) {
+  const size_t sm = 2 * (size_t)padded(f.N) * sizeof(typename cpx<Rl>::t);
+  return with_shape(f.N, [&]<typename Shape>() -> int {
+    int rc = set_smem((const void *)k_ifft_rows<Rl, Shape>, sm);
+    if (rc) return rc;
+    {
+      PFSH_LAUNCH("k_ifft_rows", s);
+      k_ifft_rows<Rl, Shape><<<dim3(nlat / 2, cols), 256, sm, s>>>(f, T, nlat, cols, F, tw, grid);
+    }
+    PFSH_CHECK_LAUNCH("k_ifft_rows");
+    return PFSH_OK;
+  });
 }
 
 int ifft_rows(const sht_plan *p, int cols, void *grid, cudaStream_t s) {
   FftArgs f = fft_args(p->fft);
-  dim3 g(p->nh, cols);
-  if (p->prec == PFSH_FP64) {
-    size_t sm = 2 * (size_t)f.N * sizeof(double2);
-    int rc = set_smem((const void *)k_ifft_rows<double>, sm);
-    if (rc) return rc;
-    {
-      PFSH_LAUNCH("k_ifft_rows", s);
-      k_ifft_rows<double><<<g, 256, sm, s>>>(f, p->T, p->nlat, cols, (const double2 *)p->F, p->fft.tw64,
-                                             (double *)grid);
-    }
-  } else {
-    size_t sm = 2 * (size_t)f.N * sizeof(float2);
-    int rc = set_smem((const void *)k_ifft_rows<float>, sm);
-    if (rc) return rc;
-    {
-      PFSH_LAUNCH("k_ifft_rows", s);
-      k_ifft_rows<float><<<g, 256, sm, s>>>(f, p->T, p->nlat, cols, (const float2 *)p->F, p->fft.tw32,
-                                            (float *)grid);
-    }
-  }
-  PFSH_CHECK_LAUNCH("k_ifft_rows");
-  return PFSH_OK;
+  if (p->prec == PFSH_FP64)
+    return ifft_launch<double>(f, p->T, p->nlat, cols, (const double2 *)p->F, p->fft.tw64, (double *)grid, s);
+  return ifft_launch<float>(f, p->T, p->nlat, cols, (const float2 *)p->F, p->fft.tw32, (float *)grid, s);
 }
 
 // Inverse longitude transform of F[m][lat][cols] (complex fp64) into
@@ -289,67 +197,54 @@ int ifft_rows_f64_raw(int N, int npass, const int *radix, int T, int nlat, int c
   f.N = N;
   f.npass = npass;
   for (int i = 0; i < kMaxPasses; ++i) f.radix[i] = i < npass ? radix[i] : 1;
-  const size_t sm = 2 * (size_t)N * sizeof(double2);
-  int rc = set_smem((const void *)k_ifft_rows<double>, sm);
-  if (rc) return rc;
-  {
-    PFSH_LAUNCH("k_ifft_rows", s);
-    k_ifft_rows<double><<<dim3(nlat / 2, cols), 256, sm, s>>>(f, T, nlat, cols, F, tw, grid);
-  }
-  PFSH_CHECK_LAUNCH("k_ifft_rows");
-  return PFSH_OK;
+  return ifft_launch<double>(f, T, nlat, cols, F, tw, grid, s);
+}
+
+template <typename Rl>
+static int fft_launch(const FftArgs &f, int T, int nlat, int cols, const Rl *grid, const double *w,
+                      const typename cpx<Rl>::t *tw, typename cpx<Rl>::t *H, cudaStream_t s) {
+  const size_t sm = 2 * (size_t)padded(f.N) * sizeof(typename cpx<Rl>::t);
+  return with_shape(f.N, [&]<typename Shape>() -> int {
+    int rc = set_smem((const void *)k_fft_rows<Rl, Shape>, sm);
+    if (rc) return rc;
+    {
+      PFSH_LAUNCH("k_fft_rows", s);
+      k_fft_rows<Rl, Shape><<<dim3(nlat / 2, cols), 256, sm, s>>>(f, T, nlat, cols, grid, w, tw, H);
+    }
+    PFSH_CHECK_LAUNCH("k_fft_rows");
+    return PFSH_OK;
+  });
 }
 
 int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s) {
   FftArgs f = fft_args(p->fft);
-  dim3 g(p->nh, cols);
-  if (p->prec == PFSH_FP64) {
-    size_t sm = 2 * (size_t)f.N * sizeof(double2);
-    int rc = set_smem((const void *)k_fft_rows<double>, sm);
+  if (p->prec == PFSH_FP64)
+    return fft_launch<double>(f, p->T, p->nlat, cols, (const double *)grid, p->d_w, p->fft.tw64,
+                              (double2 *)p->H, s);
+  return fft_launch<float>(f, p->T, p->nlat, cols, (const float *)grid, p->d_w, p->fft.tw32, (float2 *)p->H, s);
+}
+
+template <typename Rl>
+static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typename cpx<Rl>::t *tw, cudaStream_t s) {
+  typedef typename cpx<Rl>::t C;
+  const size_t sm = 10 * (size_t)padded(f.N) * sizeof(C);
+  return with_shape(f.N, [&]<typename Shape>() -> int {
+    int rc = set_smem((const void *)k_grid_rhs<Rl, Shape>, sm);
     if (rc) return rc;
     {
-      PFSH_LAUNCH("k_fft_rows", s);
-      k_fft_rows<double><<<g, 256, sm, s>>>(f, p->T, p->nlat, cols, (const double *)grid, p->d_w, p->fft.tw64,
-                                            (double2 *)p->H);
+      PFSH_LAUNCH("k_grid_rhs", s);
+      k_grid_rhs<Rl, Shape><<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, p->d_mu,
+                                                            p->d_w, tw, (C *)p->H);
     }
-  } else {
-    size_t sm = 2 * (size_t)f.N * sizeof(float2);
-    int rc = set_smem((const void *)k_fft_rows<float>, sm);
-    if (rc) return rc;
-    {
-      PFSH_LAUNCH("k_fft_rows", s);
-      k_fft_rows<float><<<g, 256, sm, s>>>(f, p->T, p->nlat, cols, (const float *)grid, p->d_w, p->fft.tw32,
-                                           (float2 *)p->H);
-    }
-  }
-  PFSH_CHECK_LAUNCH("k_fft_rows");
-  return PFSH_OK;
+    PFSH_CHECK_LAUNCH("k_grid_rhs");
+    return PFSH_OK;
+  });
 }
 
 int grid_rhs(const sht_plan *p, int B, const swe_params &, cudaStream_t s) {
   FftArgs f = fft_args(p->fft);
-  dim3 g(p->nh, B);
-  if (p->prec == PFSH_FP64) {
-    size_t sm = 10 * (size_t)f.N * sizeof(double2);
-    int rc = set_smem((const void *)k_grid_rhs<double>, sm);
-    if (rc) return rc;
-    {
-      PFSH_LAUNCH("k_grid_rhs", s);
-      k_grid_rhs<double><<<g, 256, sm, s>>>(f, p->T, p->nlat, B, (const double2 *)p->F, p->d_mu, p->d_w,
-                                            p->fft.tw64, (double2 *)p->H);
-    }
-  } else {
-    size_t sm = 10 * (size_t)f.N * sizeof(float2);
-    int rc = set_smem((const void *)k_grid_rhs<float>, sm);
-    if (rc) return rc;
-    {
-      PFSH_LAUNCH("k_grid_rhs", s);
-      k_grid_rhs<float><<<g, 256, sm, s>>>(f, p->T, p->nlat, B, (const float2 *)p->F, p->d_mu, p->d_w,
-                                           p->fft.tw32, (float2 *)p->H);
-    }
-  }
-  PFSH_CHECK_LAUNCH("k_grid_rhs");
-  return PFSH_OK;
+  if (p->prec == PFSH_FP64) return grid_launch<double>(p, f, B, p->fft.tw64, s);
+  return grid_launch<float>(p, f, B, p->fft.tw32, s);
 }
 
 }  // namespace pfsh

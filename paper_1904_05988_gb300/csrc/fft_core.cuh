@@ -1,0 +1,264 @@
+// Shared-memory Stockham FFT used by the longitude transforms.
+//
+// A transform of length N is a sequence of passes; the pass with radix R
+// after sub-transform size Ns reads x[j + r N/R] (r < R), multiplies by the
+// twiddles exp(-+2 pi i k r / (Ns R)), k = j mod Ns, does an R-point DFT in
+// registers and writes y[(j/Ns) Ns R + k + q Ns] (q < R).  Radices 8 and 16
+// are done in registers as 2x4 and 4x4 with their internal twiddles, so the
+// common lengths take 3 or 4 passes (768 = 16*16*3).  For the grid sizes of
+// the workloads the radix list is a template parameter, which turns all
+// index arithmetic into constants; any other length (prime factors <= 61)
+// takes the run-time path.  Shared-memory element e lives at e + e/16 so
+// that the stride-R stores of the first passes do not serialise on banks.
+#pragma once
+
+#include "internal.cuh"
+
+namespace pfsh {
+
+struct FftArgs {
+  int N, npass;
+  int radix[kMaxPasses];
+};
+
+__device__ __forceinline__ int sidx(int e) { return e + (e >> 4); }
+__host__ __device__ __forceinline__ int padded(int N) { return N + (N >> 4) + 1; }
+
+template <typename C> __device__ __forceinline__ C twiddle(const C *tw, int e, bool inv) {
+  C w = tw[e];
+  if (inv) w.y = -w.y;
+  return w;
+}
+
+template <typename C> __device__ __forceinline__ C rot_i(C a, bool inv) {
+  // multiply by -i (forward) or +i (inverse)
+  C r;
+  if (inv) { r.x = -a.y; r.y = a.x; } else { r.x = a.y; r.y = -a.x; }
+  return r;
+}
+
+template <typename C> __device__ __forceinline__ void dft4(C &a0, C &a1, C &a2, C &a3, bool inv) {
+  const C s02 = a0 + a2, d02 = a0 - a2, s13 = a1 + a3, d13 = a1 - a3;
+  const C r = rot_i(d13, inv);          // -i (a1 - a3) forward
+  a0 = s02 + s13;
+  a2 = s02 - s13;
+  a1 = d02 + r;
+  a3 = d02 - r;
+}
+
+// exp(-2 pi i e / 16) for e = 0..15 (cos, -sin); conjugated for the inverse
+__device__ __forceinline__ double c16(int e) {
+  const double t[16] = {1.0, 0.92387953251128675613, 0.70710678118654752440, 0.38268343236508977173,
+                        0.0, -0.38268343236508977173, -0.70710678118654752440, -0.92387953251128675613,
+                        -1.0, -0.92387953251128675613, -0.70710678118654752440, -0.38268343236508977173,
+                        0.0, 0.38268343236508977173, 0.70710678118654752440, 0.92387953251128675613};
+  return t[e & 15];
+}
+__device__ __forceinline__ double s16(int e) { return c16(e + 12); }   // sin(2 pi e / 16)
+
+template <typename C> __device__ __forceinline__ C w16(C a, int e, bool inv) {
+  typedef decltype(a.x) R;
+  const R c = (R)c16(e), s = inv ? (R)s16(e) : -(R)s16(e);
+  C r;
+  r.x = a.x * c - a.y * s;
+  r.y = a.x * s + a.y * c;
+  return r;
+}
+
+template <int R, typename C> __device__ __forceinline__ void butterfly(C *v, bool inv) {
+  typedef decltype(v[0].x) Rt;
+  if constexpr (R == 2) {
+    const C a = v[0], b = v[1];
+    v[0] = a + b;
+    v[1] = a - b;
+  } else if constexpr (R == 3) {
+    const Rt c = (Rt)-0.5;
+    const Rt s = inv ? (Rt)0.86602540378443864676 : (Rt)-0.86602540378443864676;
+    const C t = v[1] + v[2], u = v[1] - v[2];
+    const C base = v[0] + c * t;
+    C su;
+    su.x = -s * u.y;
+    su.y = s * u.x;
+    v[0] = v[0] + t;
+    v[1] = base + su;
+    v[2] = base - su;
+  } else if constexpr (R == 4) {
+    dft4(v[0], v[1], v[2], v[3], inv);
+  } else if constexpr (R == 5) {
+    // X_q = sum_r v_r W5^{rq}; cos/sin of 2 pi/5 and 4 pi/5
+    const Rt c1 = (Rt)0.30901699437494742410, c2 = (Rt)-0.80901699437494742410;
+    const Rt s1 = inv ? (Rt)0.95105651629515357212 : (Rt)-0.95105651629515357212;
+    const Rt s2 = inv ? (Rt)0.58778525229247312917 : (Rt)-0.58778525229247312917;
+    const C a = v[1] + v[4], b = v[1] - v[4], c = v[2] + v[3], d = v[2] - v[3];
+    const C t1 = v[0] + c1 * a + c2 * c, t2 = v[0] + c2 * a + c1 * c;
+    C u1, u2;   // i (s1 b + s2 d), i (s2 b - s1 d)
+    u1.x = -(s1 * b.y + s2 * d.y);
+    u1.y = s1 * b.x + s2 * d.x;
+    u2.x = -(s2 * b.y - s1 * d.y);
+    u2.y = s2 * b.x - s1 * d.x;
+    v[0] = v[0] + a + c;
+    v[1] = t1 + u1;
+    v[4] = t1 - u1;
+    v[2] = t2 + u2;
+    v[3] = t2 - u2;
+  } else if constexpr (R == 8) {
+    // n = q + 2r, k = s + 4t: U[q][s] = DFT4_r(v[q+2r])[s] W8^{qs}; X[s+4t] = DFT2_q
+    C u0[4] = {v[0], v[2], v[4], v[6]}, u1[4] = {v[1], v[3], v[5], v[7]};
+    dft4(u0[0], u0[1], u0[2], u0[3], inv);
+    dft4(u1[0], u1[1], u1[2], u1[3], inv);
+#pragma unroll
+    for (int s = 1; s < 4; ++s) u1[s] = w16(u1[s], 2 * s, inv);
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      v[s] = u0[s] + u1[s];
+      v[s + 4] = u0[s] - u1[s];
+    }
+  } else if constexpr (R == 16) {
+    // n = q + 4r, k = s + 4t: U[q][s] = DFT4_r(v[q+4r])[s] W16^{qs}; X[s+4t] = DFT4_q
+    C u[4][4];
+#pragma unroll
+    for (int q = 0; q < 4; ++q) {
+      u[q][0] = v[q];
+      u[q][1] = v[q + 4];
+      u[q][2] = v[q + 8];
+      u[q][3] = v[q + 12];
+      dft4(u[q][0], u[q][1], u[q][2], u[q][3], inv);
+#pragma unroll
+      for (int s = 1; s < 4; ++s)
+        if (q) u[q][s] = w16(u[q][s], q * s, inv);
+    }
+#pragma unroll
+    for (int s = 0; s < 4; ++s) {
+      C a0 = u[0][s], a1 = u[1][s], a2 = u[2][s], a3 = u[3][s];
+      dft4(a0, a1, a2, a3, inv);
+      v[s] = a0;
+      v[s + 4] = a1;
+      v[s + 8] = a2;
+      v[s + 12] = a3;
+    }
+  }
+}
+
+// one compile-time pass over nfft transforms (padded stride between transforms)
+template <int R, int Ns, int N, typename C>
+__device__ __forceinline__ void pass_ct(const C *__restrict__ x, C *__restrict__ y, int nfft,
+                                        const C *__restrict__ tw, bool inv) {
+  constexpr int NR = N / R, STR = N / (Ns * R);
+  const int NP = padded(N);
+  const int total = nfft * NR;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int fi = t / NR, j = t - fi * NR;
+    const int k = j % Ns, idx = (j / Ns) * (Ns * R) + k;
+    const C *xs = x + fi * NP;
+    C *ys = y + fi * NP;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      C a = xs[sidx(j + r * NR)];
+      if (Ns > 1 && r > 0) a = cmul(a, twiddle(tw, k * r * STR, inv));
+      v[r] = a;
+    }
+    butterfly<R>(v, inv);
+#pragma unroll
+    for (int q = 0; q < R; ++q) ys[sidx(idx + q * Ns)] = v[q];
+  }
+  __syncthreads();
+}
+
+template <int N, int Ns, int... Rs> struct PassList;
+template <int N, int Ns> struct PassList<N, Ns> {
+  template <typename C> static __device__ __forceinline__ C *run(C *a, C *, int, const C *, bool) { return a; }
+};
+template <int N, int Ns, int R, int... Rs> struct PassList<N, Ns, R, Rs...> {
+  template <typename C> static __device__ __forceinline__ C *run(C *a, C *b, int nfft, const C *tw, bool inv) {
+    pass_ct<R, Ns, N>(a, b, nfft, tw, inv);
+    return PassList<N, Ns * R, Rs...>::run(b, a, nfft, tw, inv);
+  }
+};
+
+template <int N_, int... Rs> struct ShapeCT {
+  static __host__ __device__ int n(const FftArgs &) { return N_; }
+  template <typename C>
+  static __device__ __forceinline__ C *run(const FftArgs &, C *a, C *b, int nfft, const C *tw, bool inv) {
+    return PassList<N_, 1, Rs...>::run(a, b, nfft, tw, inv);
+  }
+};
+
+// run-time path: any length with prime factors <= 61
+struct ShapeRT {
+  static __host__ __device__ int n(const FftArgs &f) { return f.N; }
+  template <typename C>
+  static __device__ C *run(const FftArgs &f, C *a, C *b, int nfft, const C *tw, bool inv) {
+    const int N = f.N, NP = padded(N);
+    int Ns = 1;
+    for (int p = 0; p < f.npass; ++p) {
+      const int R = f.radix[p];
+      const int NR = N / R;
+      const int stride = N / (Ns * R);
+      const int total = nfft * NR;
+      for (int t = threadIdx.x; t < total; t += blockDim.x) {
+        const int fi = t / NR, j = t - fi * NR;
+        const C *x = a + fi * NP;
+        C *y = b + fi * NP;
+        const int k = j % Ns;
+        const int idx = (j / Ns) * Ns * R + k;
+        if (R == 4 || R == 2 || R == 3) {
+          C v[4];
+          for (int r = 0; r < R; ++r) {
+            C w = x[sidx(j + r * NR)];
+            if (r) w = cmul(w, twiddle(tw, k * r * stride, inv));
+            v[r] = w;
+          }
+          if (R == 4) butterfly<4>(v, inv);
+          else if (R == 2) butterfly<2>(v, inv);
+          else butterfly<3>(v, inv);
+          for (int q = 0; q < R; ++q) y[sidx(idx + q * Ns)] = v[q];
+        } else {
+          for (int q = 0; q < R; ++q) {
+            C acc = mk<C>(0.0, 0.0);
+            for (int r = 0; r < R; ++r) {
+              C v = x[sidx(j + r * NR)];
+              if (r) v = cmul(v, twiddle(tw, k * r * stride, inv));
+              const int e = (r * q) % R;
+              acc = acc + (e ? cmul(v, twiddle(tw, e * NR, inv)) : v);
+            }
+            y[sidx(idx + q * Ns)] = acc;
+          }
+        }
+      }
+      __syncthreads();
+      C *tmp = a;
+      a = b;
+      b = tmp;
+      Ns *= R;
+    }
+    return a;
+  }
+};
+
+// lengths with a compile-time radix list
+typedef ShapeCT<48, 16, 3> Shape48;
+typedef ShapeCT<96, 16, 2, 3> Shape96;
+typedef ShapeCT<192, 16, 4, 3> Shape192;
+typedef ShapeCT<384, 16, 8, 3> Shape384;
+typedef ShapeCT<768, 16, 16, 3> Shape768;
+typedef ShapeCT<1536, 16, 16, 2, 3> Shape1536;
+typedef ShapeCT<1920, 16, 8, 3, 5> Shape1920;
+typedef ShapeCT<3840, 16, 16, 3, 5> Shape3840;
+
+// Calls f.template operator()<Shape>() with the shape serving length N.
+template <typename Fn> int with_shape(int N, Fn &&fn) {
+  switch (N) {
+    case 48: return fn.template operator()<Shape48>();
+    case 96: return fn.template operator()<Shape96>();
+    case 192: return fn.template operator()<Shape192>();
+    case 384: return fn.template operator()<Shape384>();
+    case 768: return fn.template operator()<Shape768>();
+    case 1536: return fn.template operator()<Shape1536>();
+    case 1920: return fn.template operator()<Shape1920>();
+    case 3840: return fn.template operator()<Shape3840>();
+    default: return fn.template operator()<ShapeRT>();
+  }
+}
+
+}  // namespace pfsh

@@ -4,6 +4,7 @@
 #include <cuda_runtime.h>
 #include <stdint.h>
 
+#include <algorithm>
 #include <string>
 #include <vector>
 
@@ -124,6 +125,7 @@ struct sht_plan {
   float *d_P32 = nullptr;           // [ne][nh] float copy (mixed precisions)
   double *d_eps = nullptr;          // [ne] eps_n^m = sqrt((n^2-m^2)/(4n^2-1)), extended triangle
   double *d_ilap = nullptr;         // [T+2] 1/(n(n+1)) (0 at n = 0)
+  float *d_eps32 = nullptr, *d_ilap32 = nullptr;   // float copies for mixed plans
   pfsh::FftPlan fft;
   pfsh::TcDir tc[2];                // [0] synthesis, [1] analysis (tensor-core precisions)
   // workspace for one pass of at most max_batch fields
@@ -150,6 +152,7 @@ struct sdc_level {
   double tau_nodes[16];
   double Q[16][16], QE[16][16], QI[16][16];
   double *d_old = nullptr;   // [M][max_batch][3][ncoef] c128: node-update constants
+  double *d_fac = nullptr;   // [M+1][T+1][4] implicit-solve factors per node and degree
 };
 
 struct pfasst {
@@ -167,6 +170,12 @@ struct pfasst {
   double *base_c;             // [n_ts][coarse state] restricted initial value
   double *theta0;             // [fine state]
   double Rt[16][16], Pt[16][16];   // time restriction / interpolation
+  // CUDA-graph replay of pfasst_iteration ([0] full iteration, [1] last)
+  cudaStream_t cap_stream = nullptr;
+  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
+  int calls[2] = {0, 0};
+  unsigned long long glaunches[2] = {0, 0};
+  bool graphs = true;
 };
 
 namespace pfsh {
@@ -188,6 +197,20 @@ int synth_tc(const sht_plan *p, int cols, cudaStream_t s);
 int analysis_tc(const sht_plan *p, int cols, cudaStream_t s);
 int tc_tables_build(sht_plan *p);
 void tc_tables_free(sht_plan *p);
+int synth_small(const sht_plan *p, int cols, cudaStream_t s);
+int analysis_small(const sht_plan *p, int cols, cudaStream_t s);
+bool small_synth(int cols);
+bool small_rhs(int B);
+int rhs_small(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
+              cudaStream_t s);
+bool small_analysis(int cols);
+// launch bookkeeping: kernels replayed by a CUDA graph
+void count_launches(unsigned long long n);
+unsigned long long launches_so_far();
+void g_launches_uncount(unsigned long long n);
+bool profiler_on();
+// set the dynamic shared-memory limit of a kernel once per process
+int ensure_smem(const void *fn, size_t bytes);
 // dispatch on the plan's precision
 int legendre_synth(const sht_plan *p, int cols, cudaStream_t s);
 int legendre_analysis(const sht_plan *p, int cols, cudaStream_t s);

@@ -142,6 +142,133 @@ __global__ void __launch_bounds__(256) k_anal_simt(int T, int nlat, int cols, co
   }
 }
 
+// ---------------------------------------------------------------------------
+// small batches (the serial coarse chain runs one time slice per call)
+// ---------------------------------------------------------------------------
+// Synthesis: one thread per northern latitude of one order m, all (<= NC)
+// columns in registers, no shared memory and no barriers: the table row is
+// read coalesced across threads, the coefficient row is a broadcast.
+template <typename R, int NC>
+__global__ void __launch_bounds__(64) k_synth_small(int T, int nlat, int cols, const R *__restrict__ P,
+                                                    const typename cpx<R>::t *__restrict__ X,
+                                                    typename cpx<R>::t *__restrict__ F) {
+  typedef typename cpx<R>::t C;
+  const int m = blockIdx.y;
+  const int nh = nlat / 2;
+  const int j = blockIdx.x * blockDim.x + threadIdx.x;
+  if (j >= nh) return;
+  const int K = T + 2 - m;
+  const size_t row0 = (size_t)eoff(T, m);
+  C e[NC], o[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) e[c] = o[c] = mk<C>(0.0, 0.0);
+#pragma unroll 4
+  for (int i = 0; i < K; i += 2) {
+    const R pe = P[(row0 + i) * nh + j];
+    const R po = (i + 1 < K) ? P[(row0 + i + 1) * nh + j] : (R)0;
+    const C *xe = X + (row0 + i) * cols;
+    const C *xo = X + (row0 + i + 1) * cols;
+#pragma unroll
+    for (int c = 0; c < NC; ++c) {
+      if (c < cols) {
+        const C a = xe[c];
+        e[c].x += pe * a.x;
+        e[c].y += pe * a.y;
+        if (i + 1 < K) {
+          const C b = xo[c];
+          o[c].x += po * b.x;
+          o[c].y += po * b.y;
+        }
+      }
+    }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c)
+    if (c < cols) {
+      F[((size_t)m * nlat + j) * cols + c] = e[c] + o[c];
+      F[((size_t)m * nlat + (nlat - 1 - j)) * cols + c] = e[c] - o[c];
+    }
+}
+
+// Analysis: one warp per degree of one order m; lanes stride over the
+// latitudes and the partial sums of every column are reduced by shuffles.
+template <typename R, int NC>
+__global__ void __launch_bounds__(128) k_anal_small(int T, int nlat, int cols, const R *__restrict__ P,
+                                                    const typename cpx<R>::t *__restrict__ H,
+                                                    typename cpx<R>::t *__restrict__ Y) {
+  typedef typename cpx<R>::t C;
+  const int m = blockIdx.y;
+  const int i = blockIdx.x * 4 + (threadIdx.x >> 5);
+  const int lane = threadIdx.x & 31;
+  const int K = T + 2 - m;
+  if (i >= K) return;
+  const int nh = nlat / 2, p = i & 1;
+  const size_t row = (size_t)eoff(T, m) + i;
+  const C *h = H + ((size_t)m * 2 + p) * nh * cols;
+  C acc[NC];
+#pragma unroll
+  for (int c = 0; c < NC; ++c) acc[c] = mk<C>(0.0, 0.0);
+  for (int j = lane; j < nh; j += 32) {
+    const R pv = P[row * nh + j];
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (c < cols) {
+        const C v = h[(size_t)j * cols + c];
+        acc[c].x += pv * v.x;
+        acc[c].y += pv * v.y;
+      }
+  }
+#pragma unroll
+  for (int c = 0; c < NC; ++c) {
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, d);
+      acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, d);
+    }
+  }
+  if (lane == 0) {
+#pragma unroll
+    for (int c = 0; c < NC; ++c)
+      if (c < cols) Y[row * cols + c] = acc[c];
+  }
+}
+
+constexpr int kSmallSynthCols = 8;    // complex columns (2 states of 4 fields)
+constexpr int kSmallAnalCols = 10;    // 2 states of 5 fields
+
+int synth_small(const sht_plan *p, int cols, cudaStream_t s) {
+  dim3 g((p->nh + 63) / 64, p->T + 1);
+  if (p->prec == PFSH_FP64) {
+    PFSH_LAUNCH("k_synth_small_f64", s);
+    k_synth_small<double, kSmallSynthCols><<<g, 64, 0, s>>>(p->T, p->nlat, cols, p->d_P, (const double2 *)p->X,
+                                                             (double2 *)p->F);
+  } else {
+    PFSH_LAUNCH("k_synth_small_f32", s);
+    k_synth_small<float, kSmallSynthCols><<<g, 64, 0, s>>>(p->T, p->nlat, cols, p->d_P32, (const float2 *)p->X,
+                                                            (float2 *)p->F);
+  }
+  PFSH_CHECK_LAUNCH("k_synth_small");
+  return PFSH_OK;
+}
+
+int analysis_small(const sht_plan *p, int cols, cudaStream_t s) {
+  dim3 g((p->T + 2 + 3) / 4, p->T + 1);
+  if (p->prec == PFSH_FP64) {
+    PFSH_LAUNCH("k_anal_small_f64", s);
+    k_anal_small<double, kSmallAnalCols><<<g, 128, 0, s>>>(p->T, p->nlat, cols, p->d_P, (const double2 *)p->H,
+                                                            (double2 *)p->Y);
+  } else {
+    PFSH_LAUNCH("k_anal_small_f32", s);
+    k_anal_small<float, kSmallAnalCols><<<g, 128, 0, s>>>(p->T, p->nlat, cols, p->d_P32, (const float2 *)p->H,
+                                                           (float2 *)p->Y);
+  }
+  PFSH_CHECK_LAUNCH("k_anal_small");
+  return PFSH_OK;
+}
+
+bool small_synth(int cols) { return cols <= kSmallSynthCols; }
+bool small_analysis(int cols) { return cols <= kSmallAnalCols; }
+
 int synth_simt(const sht_plan *p, int cols, cudaStream_t s) {
   dim3 g((p->nh + TJ - 1) / TJ, (cols + TC - 1) / TC, p->T + 1);
   if (p->prec == PFSH_FP64) {

@@ -267,9 +267,7 @@ void plan_chunks(int T, int nh, bool analysis, std::vector<TcChunk> &chunks, std
 
 template <typename K>
 int set_smem_attr(K kernel, size_t bytes) {
-  cudaError_t e = cudaFuncSetAttribute(kernel, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
-  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(tc smem)");
-  return PFSH_OK;
+  return ensure_smem((const void *)kernel, bytes);
 }
 
 size_t tc_smem_bytes(int Nmax, bool x3) {

@@ -8,6 +8,8 @@
 // (interpolation of increments, new initial values, node-0 F) is batched.
 #include <math.h>
 
+#include <stdlib.h>
+
 #include <algorithm>
 #include <new>
 
@@ -159,6 +161,9 @@ static void pf_free(pfasst *pf) {
                     pf->fe_cs, pf->fi_cs, pf->tau, pf->sent, pf->base_c, pf->theta0};
   for (double *b : bufs)
     if (b) cudaFree(b);
+  for (int i = 0; i < 2; ++i)
+    if (pf->gexec[i]) cudaGraphExecDestroy(pf->gexec[i]);
+  if (pf->cap_stream) cudaStreamDestroy(pf->cap_stream);
   sdc_level_destroy(pf->lev_f);
   sdc_level_destroy(pf->lev_c);
   swe_ctx_destroy(pf->ctx_f);
@@ -214,6 +219,15 @@ extern "C" int pfasst_create(pfasst **out, const pfasst_config *cfg) {
       return fail(PFSH_ENOMEM, "pfasst_create: device arrays");
     }
     cudaMemset(*a.p, 0, a.n * sizeof(double));
+  }
+  if (cudaStreamCreateWithFlags(&pf->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    pf_free(pf);
+    return fail(PFSH_ECUDA, "pfasst_create: capture stream");
+  }
+  {
+    const char *e = getenv("PFSH_NO_GRAPH");
+    pf->graphs = !(e && e[0] && e[0] != '0');
   }
   lagrange_matrix(pf->lev_f->tau_nodes, c.fine_nodes, pf->lev_c->tau_nodes, c.coarse_nodes, pf->Rt);
   lagrange_matrix(pf->lev_c->tau_nodes, c.coarse_nodes, pf->lev_f->tau_nodes, c.fine_nodes, pf->Pt);
@@ -294,9 +308,7 @@ extern "C" int pfasst_predict(pfasst *pf, pfsh_stream_t stream) {
   return rhs_eval(pf->ctx_f, pf->th_f, pf->fe_f, pf->fi_f, (Mf + 1) * nts, s);
 }
 
-extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
-  if (!pf) return fail(PFSH_EINVAL, "pfasst_iteration: NULL argument");
-  cudaStream_t s = (cudaStream_t)stream;
+static int iteration_body(pfasst *pf, int last, cudaStream_t s) {
   const pfasst_config &c = pf->cfg;
   const int nts = c.n_ts, Mc = pf->Mc, Mf = pf->Mf;
   const size_t sc = pf->sc, sf = pf->sf;
@@ -376,6 +388,46 @@ extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
     }
   }
   return rhs_eval(pf->ctx_f, pf->th_f, pf->fe_f, pf->fi_f, nts, s);
+}
+
+// The iteration is a fixed sequence of ~600 launches on fixed buffers, so it
+// is recorded once into a CUDA graph (on a private capture stream) and
+// replayed on the caller's stream; the first call of each kind runs eagerly,
+// which also sets every kernel attribute before capture.  Profiling or
+// PFSH_NO_GRAPH=1 keeps the eager path.
+extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
+  if (!pf) return fail(PFSH_EINVAL, "pfasst_iteration: NULL argument");
+  cudaStream_t s = (cudaStream_t)stream;
+  const int k = last ? 1 : 0;
+  if (!pf->graphs || profiler_on()) return iteration_body(pf, last, s);
+  if (pf->gexec[k]) {
+    PFSH_CUDA(cudaGraphLaunch(pf->gexec[k], s));
+    count_launches(pf->glaunches[k]);
+    return PFSH_OK;
+  }
+  if (pf->calls[k]++ == 0) return iteration_body(pf, last, s);
+  cudaGraph_t g = nullptr;
+  PFSH_CUDA(cudaStreamBeginCapture(pf->cap_stream, cudaStreamCaptureModeThreadLocal));
+  const unsigned long long n0 = launches_so_far();
+  int rc = iteration_body(pf, last, pf->cap_stream);
+  const unsigned long long n1 = launches_so_far();
+  cudaError_t e = cudaStreamEndCapture(pf->cap_stream, &g);
+  if (rc) {
+    if (g) cudaGraphDestroy(g);
+    return rc;
+  }
+  if (e != cudaSuccess) return cuda_fail(e, "pfasst_iteration: cudaStreamEndCapture");
+  e = cudaGraphInstantiate(&pf->gexec[k], g, 0);
+  cudaGraphDestroy(g);
+  if (e != cudaSuccess) {
+    pf->gexec[k] = nullptr;
+    return cuda_fail(e, "pfasst_iteration: cudaGraphInstantiate");
+  }
+  pf->glaunches[k] = n1 - n0;
+  g_launches_uncount(n1 - n0);
+  PFSH_CUDA(cudaGraphLaunch(pf->gexec[k], s));
+  count_launches(pf->glaunches[k]);
+  return PFSH_OK;
 }
 
 extern "C" int pfasst_get(pfasst *pf, int level, int slice, int node, double *out, pfsh_stream_t stream) {

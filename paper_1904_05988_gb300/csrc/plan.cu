@@ -145,11 +145,16 @@ int convert_table_f32(const double *a, float *b, size_t n, cudaStream_t s) {
 
 bool uses_tensor_cores(int prec) { return prec == PFSH_BF16 || prec == PFSH_BF16X3; }
 
+// Batches of one or two states (the serial coarse chain of PFASST) take
+// latency-oriented CUDA-core kernels (fp64 for FP64 plans, fp32 otherwise):
+// a 128-row tensor-core tile would be at least 94% padding there.
 int legendre_synth(const sht_plan *p, int cols, cudaStream_t s) {
+  if (small_synth(cols)) return synth_small(p, cols, s);
   return uses_tensor_cores(p->prec) ? synth_tc(p, cols, s) : synth_simt(p, cols, s);
 }
 
 int legendre_analysis(const sht_plan *p, int cols, cudaStream_t s) {
+  if (small_analysis(cols)) return analysis_small(p, cols, s);
   return uses_tensor_cores(p->prec) ? analysis_tc(p, cols, s) : analysis_simt(p, cols, s);
 }
 
@@ -252,6 +257,8 @@ static void plan_free(sht_plan *p) {
   if (p->d_P32) cudaFree(p->d_P32);
   if (p->d_eps) cudaFree(p->d_eps);
   if (p->d_ilap) cudaFree(p->d_ilap);
+  if (p->d_eps32) cudaFree(p->d_eps32);
+  if (p->d_ilap32) cudaFree(p->d_ilap32);
   if (p->ws) cudaFree(p->ws);
   fft_plan_free(p->fft);
   tc_tables_free(p);
@@ -310,6 +317,14 @@ extern "C" int sht_plan_create(sht_plan **out, int T, int nlat, int nlon, int ma
     for (int n = 1; n <= T + 1; ++n) ilap[n] = 1.0 / ((double)n * (n + 1));
     cudaMemcpy(p->d_eps, eps.data(), eps.size() * sizeof(double), cudaMemcpyHostToDevice);
     cudaMemcpy(p->d_ilap, ilap.data(), ilap.size() * sizeof(double), cudaMemcpyHostToDevice);
+    std::vector<float> eps32(eps.begin(), eps.end()), ilap32(ilap.begin(), ilap.end());
+    if ((rc = alloc((void **)&p->d_eps32, eps32.size() * sizeof(float))) ||
+        (rc = alloc((void **)&p->d_ilap32, ilap32.size() * sizeof(float)))) {
+      plan_free(p);
+      return rc;
+    }
+    cudaMemcpy(p->d_eps32, eps32.data(), eps32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_ilap32, ilap32.data(), ilap32.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
   cudaMemcpy(p->d_mu, p->mu.data(), nlat * sizeof(double), cudaMemcpyHostToDevice);
   cudaMemcpy(p->d_w, p->w.data(), nlat * sizeof(double), cudaMemcpyHostToDevice);
@@ -330,7 +345,8 @@ extern "C" int sht_plan_create(sht_plan **out, int T, int nlat, int nlon, int ma
   if ((rc = legendre_table_build(p, 0)) != PFSH_OK) { plan_free(p); return rc; }
   if (uses_tensor_cores(prec)) {
     if ((rc = tc_tables_build(p)) != PFSH_OK) { plan_free(p); return rc; }
-  } else if (prec != PFSH_FP64) {
+  }
+  if (prec != PFSH_FP64) {
     const size_t n = (size_t)p->ne * p->nh;
     if ((rc = alloc((void **)&p->d_P32, n * sizeof(float)))) { plan_free(p); return rc; }
     if ((rc = convert_table_f32(p->d_P, p->d_P32, n, 0))) { plan_free(p); return rc; }
@@ -425,6 +441,29 @@ struct ProfRec {
 };
 std::vector<ProfRec> g_prof;
 }  // namespace
+
+void count_launches(unsigned long long n) { g_launches.fetch_add(n, std::memory_order_relaxed); }
+unsigned long long launches_so_far() { return g_launches.load(); }
+// launches recorded during a stream capture did not run; the replays count them
+void g_launches_uncount(unsigned long long n) { g_launches.fetch_sub(n, std::memory_order_relaxed); }
+bool profiler_on() { return g_prof_on.load() != 0; }
+
+static std::mutex g_smem_mu;
+static std::map<const void *, size_t> g_smem_set;
+
+int ensure_smem(const void *fn, size_t bytes) {
+  if (bytes <= 48 * 1024) return PFSH_OK;
+  std::lock_guard<std::mutex> lk(g_smem_mu);
+  int dev = 0;
+  cudaGetDevice(&dev);
+  const void *key = (const char *)fn + dev;   // per device
+  auto it = g_smem_set.find(key);
+  if (it != g_smem_set.end() && it->second >= bytes) return PFSH_OK;
+  cudaError_t e = cudaFuncSetAttribute(fn, cudaFuncAttributeMaxDynamicSharedMemorySize, (int)bytes);
+  if (e != cudaSuccess) return cuda_fail(e, "cudaFuncSetAttribute(smem)");
+  g_smem_set[key] = bytes;
+  return PFSH_OK;
+}
 
 LaunchScope::LaunchScope(const char *n, cudaStream_t s) : name(n), stream(s), slot(-1) {
   g_launches.fetch_add(1, std::memory_order_relaxed);

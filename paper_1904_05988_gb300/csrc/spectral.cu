@@ -4,6 +4,7 @@
 // (Sections 5.1.2 and 5.3).  All are element-wise over triangular spectral
 // arrays and bound by HBM traffic or FP64 issue rate.
 #include "internal.cuh"
+#include "spectral_ops.cuh"
 
 namespace pfsh {
 
@@ -87,10 +88,10 @@ int Y_to_spec(const sht_plan *p, double *spec, int batch, cudaStream_t s) {
 //   U_n = [(n-1) eps_n psi_{n-1} - (n+2) eps_{n+1} psi_{n+1} + i m chi_n] / a
 //   V_n = [i m psi_n - (n-1) eps_n chi_{n-1} + (n+2) eps_{n+1} chi_{n+1}] / a
 // ---------------------------------------------------------------------------
-template <typename CX>
-__global__ void k_rhs_prep(int T, int ne, int B, double a, double inva, double omega, double phibar,
-                           const double *__restrict__ eps, const double *__restrict__ ilap,
-                           const double2 *__restrict__ state, CX *__restrict__ X) {
+template <typename M>
+__global__ void k_rhs_prep(int T, int ne, int B, M ma2, M inva, double omega, double phibar, SpecTables<M> tb,
+                           const double2 *__restrict__ state, typename cpx<M>::t *__restrict__ X) {
+  typedef typename cpx<M>::t C;
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   if (idx >= ne) return;
@@ -98,49 +99,13 @@ __global__ void k_rhs_prep(int T, int ne, int B, double a, double inva, double o
   const int m = tri_m(idx, T + 1);
   const int n = m + (idx - poff(T + 1, m));
   const double2 *Phi = state + (size_t)b * 3 * nc;
-  const double2 *zeta = Phi + nc;
-  const double2 *delta = Phi + 2 * nc;
-  const int base = poff(T, m) - m;  // packed index of (m, n') is base + n'
-  const double ma2 = -a * a;
-  auto psi_chi = [&](int nn, double2 *ps, double2 *ch) {
-    if (nn < m || nn > T || nn == 0) {
-      *ps = make_double2(0.0, 0.0);
-      *ch = make_double2(0.0, 0.0);
-      return;
-    }
-    const double f = ma2 * ilap[nn];
-    double2 z = zeta[base + nn], d = delta[base + nn];
-    if (m == 0) { z.y = 0.0; d.y = 0.0; }
-    *ps = f * z;
-    *ch = f * d;
-  };
-  double2 eta = make_double2(0.0, 0.0), php = make_double2(0.0, 0.0);
-  if (n <= T) {
-    eta = zeta[base + n];
-    php = Phi[base + n];
-    if (m == 0) {
-      eta.y = 0.0;
-      php.y = 0.0;
-      if (n == 1) eta.x += 2.0 * omega * 0.81649658092772603273;   // 2 Omega / sqrt(3/2)
-      if (n == 0) php.x -= 1.41421356237309504880 * phibar;        // sqrt(2) Phibar
-    }
-  }
-  double2 ps_m, ch_m, ps_0, ch_0, ps_p, ch_p;
-  psi_chi(n - 1, &ps_m, &ch_m);
-  psi_chi(n, &ps_0, &ch_0);
-  psi_chi(n + 1, &ps_p, &ch_p);
-  const double cm = (n - 1) * eps[idx];                       // (n-1) eps_n^m
-  const double cp = (n <= T) ? (n + 2) * eps[idx + 1] : 0.0;  // (n+2) eps_{n+1}^m
-  double2 U, V;
-  U.x = (cm * ps_m.x - cp * ps_p.x - m * ch_0.y) * inva;
-  U.y = (cm * ps_m.y - cp * ps_p.y + m * ch_0.x) * inva;
-  V.x = (-m * ps_0.y - cm * ch_m.x + cp * ch_p.x) * inva;
-  V.y = (m * ps_0.x - cm * ch_m.y + cp * ch_p.y) * inva;
-  CX *row = X + (size_t)idx * (4 * B) + b * 4;
-  row[0] = mk<CX>(eta.x, eta.y);
-  row[1] = mk<CX>(php.x, php.y);
-  row[2] = mk<CX>(U.x, U.y);
-  row[3] = mk<CX>(V.x, V.y);
+  C out[4];
+  prep_point<M>(T, m, n, Phi, Phi + nc, Phi + 2 * nc, poff(T, m) - m, (size_t)idx, tb, ma2, inva, omega, phibar, out);
+  C *row = X + (size_t)idx * (4 * B) + b * 4;
+  row[0] = out[0];
+  row[1] = out[1];
+  row[2] = out[2];
+  row[3] = out[3];
 }
 
 int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &prm, cudaStream_t s) {
@@ -148,11 +113,13 @@ int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &pr
   {
     PFSH_LAUNCH("k_rhs_prep", s);
     if (p->prec == PFSH_FP64)
-      k_rhs_prep<double2><<<g, 256, 0, s>>>(p->T, p->ne, B, prm.a, 1.0 / prm.a, prm.omega, prm.phibar, p->d_eps,
-                                            p->d_ilap, (const double2 *)state, (double2 *)p->X);
+      k_rhs_prep<double><<<g, 256, 0, s>>>(p->T, p->ne, B, -prm.a * prm.a, 1.0 / prm.a, prm.omega, prm.phibar,
+                                           SpecTables<double>{p->d_eps, p->d_ilap}, (const double2 *)state,
+                                           (double2 *)p->X);
     else
-      k_rhs_prep<float2><<<g, 256, 0, s>>>(p->T, p->ne, B, prm.a, 1.0 / prm.a, prm.omega, prm.phibar, p->d_eps,
-                                           p->d_ilap, (const double2 *)state, (float2 *)p->X);
+      k_rhs_prep<float><<<g, 256, 0, s>>>(p->T, p->ne, B, (float)(-prm.a * prm.a), (float)(1.0 / prm.a), prm.omega,
+                                          prm.phibar, SpecTables<float>{p->d_eps32, p->d_ilap32},
+                                          (const double2 *)state, (float2 *)p->X);
   }
   PFSH_CHECK_LAUNCH("k_rhs_prep");
   return PFSH_OK;
@@ -166,11 +133,12 @@ int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &pr
 //   F_E = [-div(A2,B2), -div(A1,B1), curl(A1,B1) + n(n+1)/a^2 E]
 //   F_I = [-Phibar delta - nu k Phi, -nu k zeta, k Phi - nu k delta], k = n(n+1)/a^2
 // ---------------------------------------------------------------------------
-template <typename CY>
-__global__ void k_rhs_assemble(int T, int B, double inva, double inva2, double nu, double phibar,
-                               const double *__restrict__ eps, const CY *__restrict__ Y,
+template <typename M>
+__global__ void k_rhs_assemble(int T, int B, M inva, M inva2, double dinva2, double nu, double phibar,
+                               const M *__restrict__ eps, const typename cpx<M>::t *__restrict__ Y,
                                const double2 *__restrict__ state, double2 *__restrict__ fE,
                                double2 *__restrict__ fI) {
+  typedef typename cpx<M>::t C;
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   const int nc = ncoef_of(T);
@@ -179,42 +147,20 @@ __global__ void k_rhs_assemble(int T, int B, double inva, double inva2, double n
   const int n = m + (idx - poff(T, m));
   const int cols = 5 * B;
   const size_t r0 = (size_t)(poff(T + 1, m) + (n - m));
-  auto y = [&](size_t row, int f) {
-    const CY v = Y[row * cols + b * 5 + f];
-    return make_double2(v.x, v.y);
-  };
-  const double e1 = eps[r0 + 1], e0 = eps[r0];     // eps_{n+1}^m, eps_n^m
-  const double cu = n * e1, cd = (n + 1) * e0;
-  const double2 z = make_double2(0.0, 0.0);
-  double2 A1 = y(r0, 0), B1 = y(r0, 1), A2 = y(r0, 2), B2 = y(r0, 3), E = y(r0, 4);
-  double2 A1u = y(r0 + 1, 0), B1u = y(r0 + 1, 1), B2u = y(r0 + 1, 3);
-  double2 A1d = n > m ? y(r0 - 1, 0) : z, B1d = n > m ? y(r0 - 1, 1) : z, B2d = n > m ? y(r0 - 1, 3) : z;
-  const double k = (double)n * (n + 1) * inva2;
-  double2 div1, div2, curl1;
-  div1.x = (-m * A1.y + cu * B1u.x - cd * B1d.x) * inva;
-  div1.y = (m * A1.x + cu * B1u.y - cd * B1d.y) * inva;
-  div2.x = (-m * A2.y + cu * B2u.x - cd * B2d.x) * inva;
-  div2.y = (m * A2.x + cu * B2u.y - cd * B2d.y) * inva;
-  curl1.x = (-m * B1.y - cu * A1u.x + cd * A1d.x) * inva;
-  curl1.y = (m * B1.x - cu * A1u.y + cd * A1d.y) * inva;
-  double2 *oE = fE + (size_t)b * 3 * nc;
-  double2 fe0 = make_double2(-div2.x, -div2.y);
-  double2 fe1 = make_double2(-div1.x, -div1.y);
-  double2 fe2 = make_double2(curl1.x + k * E.x, curl1.y + k * E.y);
-  if (m == 0) { fe0.y = 0.0; fe1.y = 0.0; fe2.y = 0.0; }
-  oE[idx] = fe0;
-  oE[nc + idx] = fe1;
-  oE[2 * nc + idx] = fe2;
-  if (fI) {
-    const double2 *st = state + (size_t)b * 3 * nc;
-    double2 Phi = st[idx], zeta = st[nc + idx], delta = st[2 * nc + idx];
-    if (m == 0) { Phi.y = 0.0; zeta.y = 0.0; delta.y = 0.0; }
-    double2 *oI = fI + (size_t)b * 3 * nc;
-    const double nk = nu * k;
-    oI[idx] = make_double2(-phibar * delta.x - nk * Phi.x, -phibar * delta.y - nk * Phi.y);
-    oI[nc + idx] = make_double2(-nk * zeta.x, -nk * zeta.y);
-    oI[2 * nc + idx] = make_double2(k * Phi.x - nk * delta.x, k * Phi.y - nk * delta.y);
+  C cur[5], up[5], dn[5];
+#pragma unroll
+  for (int f = 0; f < 5; ++f) {
+    cur[f] = Y[r0 * cols + b * 5 + f];
+    up[f] = Y[(r0 + 1) * cols + b * 5 + f];
+    dn[f] = n > m ? Y[(r0 - 1) * cols + b * 5 + f] : mk<C>(0.0, 0.0);
   }
+  double2 fe[3];
+  assemble_point<M, C>(m, n, cur, up, dn, n > m, eps[r0 + 1], eps[r0], inva, inva2, fe);
+  double2 *oE = fE + (size_t)b * 3 * nc;
+  oE[idx] = fe[0];
+  oE[nc + idx] = fe[1];
+  oE[2 * nc + idx] = fe[2];
+  if (fI) linear_point(m, n, state + (size_t)b * 3 * nc, nc, idx, dinva2, nu, phibar, fI + (size_t)b * 3 * nc);
 }
 
 int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
@@ -224,13 +170,13 @@ int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI,
   {
     PFSH_LAUNCH("k_rhs_assemble", s);
     if (p->prec == PFSH_FP64)
-      k_rhs_assemble<double2><<<g, 256, 0, s>>>(p->T, B, inva, inva2, prm.nu, prm.phibar, p->d_eps,
-                                                (const double2 *)p->Y, (const double2 *)state, (double2 *)fE,
-                                                (double2 *)fI);
-    else
-      k_rhs_assemble<float2><<<g, 256, 0, s>>>(p->T, B, inva, inva2, prm.nu, prm.phibar, p->d_eps,
-                                               (const float2 *)p->Y, (const double2 *)state, (double2 *)fE,
+      k_rhs_assemble<double><<<g, 256, 0, s>>>(p->T, B, inva, inva2, inva2, prm.nu, prm.phibar, p->d_eps,
+                                               (const double2 *)p->Y, (const double2 *)state, (double2 *)fE,
                                                (double2 *)fI);
+    else
+      k_rhs_assemble<float><<<g, 256, 0, s>>>(p->T, B, (float)inva, (float)inva2, inva2, prm.nu, prm.phibar,
+                                              p->d_eps32, (const float2 *)p->Y, (const double2 *)state,
+                                              (double2 *)fE, (double2 *)fI);
   }
   PFSH_CHECK_LAUNCH("k_rhs_assemble");
   return PFSH_OK;
@@ -291,35 +237,48 @@ struct SdcCoef {
 };
 
 // O_i = theta_0 + sum_j cE[i][j] FE_j + cI[i][j] FI_j (+ tau_i),  i = 1..M
-__global__ void k_sdc_old(int nc3, int B, int M, size_t nstride, SdcCoef c, const double2 *__restrict__ th,
-                          const double2 *__restrict__ fe, const double2 *__restrict__ fi,
-                          const double2 *__restrict__ tau, size_t tstride, double2 *__restrict__ O) {
+// (M <= MAXM; compile-time bound keeps the accumulators in registers)
+template <int MAXM>
+__global__ void __launch_bounds__(128) k_sdc_old(int nc3, int B, int M, size_t nstride, SdcCoef c,
+                                                 const double2 *__restrict__ th, const double2 *__restrict__ fe,
+                                                 const double2 *__restrict__ fi, const double2 *__restrict__ tau,
+                                                 size_t tstride, double2 *__restrict__ O) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)nc3 * B) return;
-  double2 acc[16];
+  double2 acc[MAXM + 1];
   const double2 t0 = th[t];
-  for (int i = 1; i <= M; ++i) acc[i] = tau ? t0 + tau[(size_t)i * tstride + t] : t0;
-  for (int j = 0; j <= M; ++j) {
+#pragma unroll
+  for (int i = 1; i <= MAXM; ++i)
+    if (i <= M) acc[i] = tau ? t0 + tau[(size_t)i * tstride + t] : t0;
+#pragma unroll
+  for (int j = 0; j <= MAXM; ++j) {
+    if (j > M) break;
     const double2 e = fe[(size_t)j * nstride + t], f = fi[(size_t)j * nstride + t];
-    for (int i = 1; i <= M; ++i) {
-      acc[i].x += c.cE[i][j] * e.x + c.cI[i][j] * f.x;
-      acc[i].y += c.cE[i][j] * e.y + c.cI[i][j] * f.y;
-    }
+#pragma unroll
+    for (int i = 1; i <= MAXM; ++i)
+      if (i <= M) {
+        acc[i].x += c.cE[i][j] * e.x + c.cI[i][j] * f.x;
+        acc[i].y += c.cE[i][j] * e.y + c.cI[i][j] * f.y;
+      }
   }
-  for (int i = 1; i <= M; ++i) O[(size_t)(i - 1) * nc3 * B + t] = acc[i];
+#pragma unroll
+  for (int i = 1; i <= MAXM; ++i)
+    if (i <= M) O[(size_t)(i - 1) * nc3 * B + t] = acc[i];
 }
 
 // theta_i = solve(O_i + sum_{1<=j<i} nE[i][j] FE_j^new + nI[i][j] FI_j^new, h_i)
-__global__ void k_sdc_node(int T, int B, int i, size_t nstride, SdcCoef c, double a, double nu, double phibar,
-                           const double2 *__restrict__ O, const double2 *__restrict__ fe,
-                           const double2 *__restrict__ fi, double2 *__restrict__ th) {
+// with the per-degree solve factors of node i precomputed in FP64:
+// fac[n] = {s = 1 + h nu k, 1/s, 1/(s^2 + h^2 Phibar k), h k}
+__global__ void __launch_bounds__(128) k_sdc_node(int T, int B, int i, size_t nstride, SdcCoef c, double hphibar,
+                                                  const double4 *__restrict__ fac, const double2 *__restrict__ O,
+                                                  const double2 *__restrict__ fe, const double2 *__restrict__ fi,
+                                                  double2 *__restrict__ th) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   const int nc = ncoef_of(T);
   if (idx >= nc) return;
   const int m = tri_m(idx, T);
   const int n = m + (idx - poff(T, m));
-  const double k = (double)n * (n + 1) / (a * a);
   double2 r[3];
   for (int f = 0; f < 3; ++f) {
     const size_t t = (size_t)b * 3 * nc + f * nc + idx;
@@ -331,12 +290,11 @@ __global__ void k_sdc_node(int T, int B, int i, size_t nstride, SdcCoef c, doubl
     }
     r[f] = v;
   }
-  double2 xP, xz, xd;
-  solve3(r[0], r[1], r[2], c.h[i], k, nu, phibar, &xP, &xz, &xd);
+  const double4 q = fac[n];   // s, 1/s, 1/det, h k
   double2 *out = th + (size_t)i * nstride + (size_t)b * 3 * nc;
-  out[idx] = xP;
-  out[nc + idx] = xz;
-  out[2 * nc + idx] = xd;
+  out[idx] = make_double2((q.x * r[0].x - hphibar * r[2].x) * q.z, (q.x * r[0].y - hphibar * r[2].y) * q.z);
+  out[nc + idx] = make_double2(r[1].x * q.y, r[1].y * q.y);
+  out[2 * nc + idx] = make_double2((q.x * r[2].x + q.w * r[0].x) * q.z, (q.x * r[2].y + q.w * r[0].y) * q.z);
 }
 
 int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const double *tau, size_t node_stride,
@@ -372,17 +330,18 @@ int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const
     size_t total = (size_t)nc3 * B;
     {
       PFSH_LAUNCH("k_sdc_old", s);
-      k_sdc_old<<<(unsigned)((total + 255) / 256), 256, 0, s>>>(nc3, B, M, ns, c, (const double2 *)theta,
+      k_sdc_old<8><<<(unsigned)((total + 127) / 128), 128, 0, s>>>(nc3, B, M, ns, c, (const double2 *)theta,
                                                                (const double2 *)fE, (const double2 *)fI,
                                                                (const double2 *)tau, ns, (double2 *)l->d_old);
     }
     PFSH_CHECK_LAUNCH("k_sdc_old");
   }
   for (int i = 1; i <= M; ++i) {
-    dim3 g((nc + 255) / 256, B);
+    dim3 g((nc + 127) / 128, B);
     {
       PFSH_LAUNCH("k_sdc_node", s);
-      k_sdc_node<<<g, 256, 0, s>>>(T, B, i, ns, c, ctx->prm.a, ctx->prm.nu, ctx->prm.phibar,
+      k_sdc_node<<<g, 128, 0, s>>>(T, B, i, ns, c, c.h[i] * ctx->prm.phibar,
+                                   (const double4 *)l->d_fac + (size_t)i * (T + 1),
                                    (const double2 *)l->d_old + (size_t)(i - 1) * nc3 * B, (const double2 *)fE,
                                    (const double2 *)fI, (double2 *)theta);
     }

@@ -53,16 +53,17 @@ def state_of(T, seed, batch=1):
 @pytest.mark.parametrize("T", [31, 63, 85, 170])
 def test_sht_inverse_and_forward_match_oracle(T):
     nlat, nlon = syn.gaussian_grid_size(T)
-    plan = ps.sht_plan_create(T, nlat, nlon, 3, "fp64")
+    plan = ps.sht_plan_create(T, nlat, nlon, 12, "fp64")
     assert np.max(np.abs(np.array(plan.mu) - SHT(T, nlat, nlon, L=T + 1).mu)) < 1e-15
-    spec = syn.random_spectrum(T, (5,), seed=T, nmin=0)   # 5 fields: two passes of 3 (ragged)
-    grid = torch.empty((5, nlat, nlon), dtype=torch.float64, device=DEV)
+    nf = 20   # passes of 12 (tiled kernels) and 8 (small-batch kernels)
+    spec = syn.random_spectrum(T, (nf,), seed=T, nmin=0)
+    grid = torch.empty((nf, nlat, nlon), dtype=torch.float64, device=DEV)
     ps.sht_inverse(plan, cuda(spec), grid)
     ps.pfsh_sync_status()
     o = SHT(T, nlat, nlon, L=T + 1)
     ref = o.synthesis(unpack(spec, T))
     assert rel(grid.cpu().numpy(), ref) < 1e-12
-    back = torch.empty((5, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    back = torch.empty((nf, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
     ps.sht_forward(plan, torch.tensor(ref, device=DEV), back)
     ps.pfsh_sync_status()
     ref_spec = pack(o.analysis(ref, T + 1), T)

@@ -64,12 +64,16 @@ def state_of(T, seed, batch=1):
 @pytest.mark.parametrize("form", FORMS)
 @pytest.mark.parametrize("T", [63, 170, 255])
 def test_transform_pair(form, T):
+    """40 fields in passes of 16, 16 and 8: the first two take the form's
+    contraction (tensor cores for bf16/3xbf16), the ragged last one the
+    small-batch CUDA-core kernels; the error is over all 40."""
     nlat, nlon = syn.gaussian_grid_size(T)
-    plan = ps.sht_plan_create(T, nlat, nlon, 7, form)
-    spec = syn.random_spectrum(T, (9,), seed=30 + T, nmin=1)      # two passes, ragged
-    grid = torch.empty((9, nlat, nlon), dtype=torch.float32, device=DEV)
+    plan = ps.sht_plan_create(T, nlat, nlon, 16, form)
+    nf = 40
+    spec = syn.random_spectrum(T, (nf,), seed=30 + T, nmin=1)
+    grid = torch.empty((nf, nlat, nlon), dtype=torch.float32, device=DEV)
     ps.sht_inverse(plan, cuda(spec), grid)
-    back = torch.empty((9, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    back = torch.empty((nf, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
     ps.sht_forward(plan, grid, back)
     ps.pfsh_sync_status()
     o = SHT(T, nlat, nlon, L=T + 1)
@@ -81,8 +85,10 @@ def test_transform_pair(form, T):
 
 
 @pytest.mark.parametrize("form", FORMS)
-@pytest.mark.parametrize("T,B", [(63, 3), (170, 2), (255, 2)])
+@pytest.mark.parametrize("T,B", [(63, 3), (170, 3), (255, 3), (127, 1)])
 def test_swe_rhs(form, T, B):
+    """B = 3 states (12 synthesis / 15 analysis columns) takes the form's
+    contraction; B = 1 the small-batch path of the serial coarse chain."""
     nlat, nlon = syn.gaussian_grid_size(T)
     plan = ps.sht_plan_create(T, nlat, nlon, 5 * B, form)
     ctx = ps.swe_ctx_create(plan, A, OM, syn.NU, PHIBAR)
