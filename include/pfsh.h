@@ -220,9 +220,10 @@ int pfasst_get(pfasst *pf, int level, int slice, int node, double *out,
  * inside this library, which every GPU that loads the library keeps until
  * the process exits.
  * Limits: 1 <= T <= 127, nlat even >= T+2, nlon even > 2(T+1) with prime
- * factors <= 61, and (T+1)*nlat*batch*16 bytes (+ nlat*8 + nlon*16, each
- * rounded up to 256) <= 4 MiB; larger requests return PFSH_EINVAL before
- * any work is queued (split the batch).
+ * factors <= 61, and (T+1)*nlat*batch*16 bytes plus the latitudes
+ * (nlat*8 bytes) and FFT twiddles (at most 3*nlon*16 bytes), each rounded up
+ * to 256, within 4 MiB; larger requests return PFSH_EINVAL before any work
+ * is queued (split the batch).
  * The first call on a device looks up the device address of that array
  * (cudaGetSymbolAddress) and remembers it; make that first call before any
  * stream capture.  All calls share the one array and every call rewrites

@@ -18,6 +18,7 @@ static FftArgs fft_args(const FftPlan &f) {
   FftArgs a;
   a.N = f.N;
   a.npass = f.npass;
+  a.full = f.full;
   for (int i = 0; i < kMaxPasses; ++i) a.radix[i] = i < f.npass ? f.radix[i] : 1;
   return a;
 }
@@ -102,7 +103,7 @@ __global__ void k_fft_rows(FftArgs f, int T, int nlat, int cols, const Rl *__res
 template <typename Rl, typename Shape>
 __global__ void __launch_bounds__(256) k_grid_rhs(FftArgs f, int T, int nlat, int B,
                                                   const typename cpx<Rl>::t *__restrict__ F,
-                                                  const double *__restrict__ mu, const double *__restrict__ w,
+                                                  const Rl *__restrict__ rowf,
                                                   const typename cpx<Rl>::t *__restrict__ tw,
                                                   typename cpx<Rl>::t *__restrict__ H) {
   typedef typename cpx<Rl>::t C;
@@ -129,8 +130,7 @@ __global__ void __launch_bounds__(256) k_grid_rhs(FftArgs f, int T, int nlat, in
   __syncthreads();
   C *g = Shape::run(f, A, Bf, 4, tw, true);
   C *o = (g == A) ? Bf : A;
-  const double x = mu[j];
-  const Rl inv = (Rl)(1.0 / ((1.0 - x) * (1.0 + x)));
+  const Rl inv = rowf[2 * j];                // 1/(1 - mu_j^2)
   const Rl h = (Rl)0.5 * inv;
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const int e = sidx(k);
@@ -145,7 +145,7 @@ __global__ void __launch_bounds__(256) k_grid_rhs(FftArgs f, int T, int nlat, in
   __syncthreads();
   C *Z = Shape::run(f, o, g, 5, tw, false);
   const Rl half = (Rl)0.5 / (Rl)N;
-  const Rl wj = (Rl)w[j];
+  const Rl wj = rowf[2 * j + 1];
   const int nh = nlat / 2;
   for (int t = threadIdx.x; t < 5 * (T + 1); t += blockDim.x) {
     const int m = t / 5, fld = t - 5 * m;   // consecutive threads: the 5 fields of one m
@@ -189,13 +189,15 @@ int ifft_rows(const sht_plan *p, int cols, void *grid, cudaStream_t s) {
 }
 
 // Inverse longitude transform of F[m][lat][cols] (complex fp64) into
-// grid[cols][lat][lon] with caller-supplied twiddles and radix list; used by
-// the allocation-free synthesis entry point.
-int ifft_rows_f64_raw(int N, int npass, const int *radix, int T, int nlat, int cols, const double2 *F,
+// grid[cols][lat][lon] with caller-supplied radix list and twiddle table (the
+// per-pass layout of fft_core.cuh, full circle at offset `full`); used by the
+// allocation-free synthesis entry point.
+int ifft_rows_f64_raw(int N, int npass, const int *radix, int full, int T, int nlat, int cols, const double2 *F,
                       const double2 *tw, double *grid, cudaStream_t s) {
   FftArgs f;
   f.N = N;
   f.npass = npass;
+  f.full = full;
   for (int i = 0; i < kMaxPasses; ++i) f.radix[i] = i < npass ? radix[i] : 1;
   return ifft_launch<double>(f, T, nlat, cols, F, tw, grid, s);
 }
@@ -225,7 +227,8 @@ int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s) {
 }
 
 template <typename Rl>
-static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typename cpx<Rl>::t *tw, cudaStream_t s) {
+static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typename cpx<Rl>::t *tw, const Rl *rowf,
+                       cudaStream_t s) {
   typedef typename cpx<Rl>::t C;
   const size_t sm = 10 * (size_t)padded(f.N) * sizeof(C);
   return with_shape(f.N, [&]<typename Shape>() -> int {
@@ -233,8 +236,8 @@ static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typenam
     if (rc) return rc;
     {
       PFSH_LAUNCH("k_grid_rhs", s);
-      k_grid_rhs<Rl, Shape><<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, p->d_mu,
-                                                            p->d_w, tw, (C *)p->H);
+      k_grid_rhs<Rl, Shape><<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw,
+                                                            (C *)p->H);
     }
     PFSH_CHECK_LAUNCH("k_grid_rhs");
     return PFSH_OK;
@@ -243,8 +246,8 @@ static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typenam
 
 int grid_rhs(const sht_plan *p, int B, const swe_params &, cudaStream_t s) {
   FftArgs f = fft_args(p->fft);
-  if (p->prec == PFSH_FP64) return grid_launch<double>(p, f, B, p->fft.tw64, s);
-  return grid_launch<float>(p, f, B, p->fft.tw32, s);
+  if (p->prec == PFSH_FP64) return grid_launch<double>(p, f, B, p->fft.tw64, p->d_rowf, s);
+  return grid_launch<float>(p, f, B, p->fft.tw32, p->d_rowf32, s);
 }
 
 }  // namespace pfsh

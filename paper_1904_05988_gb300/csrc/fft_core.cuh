@@ -18,6 +18,7 @@ namespace pfsh {
 
 struct FftArgs {
   int N, npass;
+  int full;                // offset of the full-circle table exp(-2 pi i e/N), e < N
   int radix[kMaxPasses];
 };
 
@@ -139,11 +140,15 @@ template <int R, typename C> __device__ __forceinline__ void butterfly(C *v, boo
   }
 }
 
+// Twiddles are stored per pass: the pass with radix R after sub-transform
+// size Ns owns R*Ns entries, entry r*Ns + k = exp(-2 pi i k r / (Ns R)), so
+// the lanes of a warp (consecutive k) read consecutive entries.
+
 // one compile-time pass over nfft transforms (padded stride between transforms)
-template <int R, int Ns, int N, typename C>
+template <int R, int Ns, int N, int OFF, typename C>
 __device__ __forceinline__ void pass_ct(const C *__restrict__ x, C *__restrict__ y, int nfft,
                                         const C *__restrict__ tw, bool inv) {
-  constexpr int NR = N / R, STR = N / (Ns * R);
+  constexpr int NR = N / R;
   const int NP = padded(N);
   const int total = nfft * NR;
   for (int t = threadIdx.x; t < total; t += blockDim.x) {
@@ -155,7 +160,7 @@ __device__ __forceinline__ void pass_ct(const C *__restrict__ x, C *__restrict__
 #pragma unroll
     for (int r = 0; r < R; ++r) {
       C a = xs[sidx(j + r * NR)];
-      if (Ns > 1 && r > 0) a = cmul(a, twiddle(tw, k * r * STR, inv));
+      if (Ns > 1 && r > 0) a = cmul(a, twiddle(tw, OFF + r * Ns + k, inv));
       v[r] = a;
     }
     butterfly<R>(v, inv);
@@ -165,14 +170,14 @@ __device__ __forceinline__ void pass_ct(const C *__restrict__ x, C *__restrict__
   __syncthreads();
 }
 
-template <int N, int Ns, int... Rs> struct PassList;
-template <int N, int Ns> struct PassList<N, Ns> {
+template <int N, int Ns, int OFF, int... Rs> struct PassList;
+template <int N, int Ns, int OFF> struct PassList<N, Ns, OFF> {
   template <typename C> static __device__ __forceinline__ C *run(C *a, C *, int, const C *, bool) { return a; }
 };
-template <int N, int Ns, int R, int... Rs> struct PassList<N, Ns, R, Rs...> {
+template <int N, int Ns, int OFF, int R, int... Rs> struct PassList<N, Ns, OFF, R, Rs...> {
   template <typename C> static __device__ __forceinline__ C *run(C *a, C *b, int nfft, const C *tw, bool inv) {
-    pass_ct<R, Ns, N>(a, b, nfft, tw, inv);
-    return PassList<N, Ns * R, Rs...>::run(b, a, nfft, tw, inv);
+    pass_ct<R, Ns, N, OFF>(a, b, nfft, tw, inv);
+    return PassList<N, Ns * R, OFF + R * Ns, Rs...>::run(b, a, nfft, tw, inv);
   }
 };
 
@@ -180,7 +185,7 @@ template <int N_, int... Rs> struct ShapeCT {
   static __host__ __device__ int n(const FftArgs &) { return N_; }
   template <typename C>
   static __device__ __forceinline__ C *run(const FftArgs &, C *a, C *b, int nfft, const C *tw, bool inv) {
-    return PassList<N_, 1, Rs...>::run(a, b, nfft, tw, inv);
+    return PassList<N_, 1, 0, Rs...>::run(a, b, nfft, tw, inv);
   }
 };
 
@@ -190,11 +195,10 @@ struct ShapeRT {
   template <typename C>
   static __device__ C *run(const FftArgs &f, C *a, C *b, int nfft, const C *tw, bool inv) {
     const int N = f.N, NP = padded(N);
-    int Ns = 1;
+    int Ns = 1, off = 0;
     for (int p = 0; p < f.npass; ++p) {
       const int R = f.radix[p];
       const int NR = N / R;
-      const int stride = N / (Ns * R);
       const int total = nfft * NR;
       for (int t = threadIdx.x; t < total; t += blockDim.x) {
         const int fi = t / NR, j = t - fi * NR;
@@ -206,7 +210,7 @@ struct ShapeRT {
           C v[4];
           for (int r = 0; r < R; ++r) {
             C w = x[sidx(j + r * NR)];
-            if (r) w = cmul(w, twiddle(tw, k * r * stride, inv));
+            if (r) w = cmul(w, twiddle(tw, off + r * Ns + k, inv));
             v[r] = w;
           }
           if (R == 4) butterfly<4>(v, inv);
@@ -218,9 +222,11 @@ struct ShapeRT {
             C acc = mk<C>(0.0, 0.0);
             for (int r = 0; r < R; ++r) {
               C v = x[sidx(j + r * NR)];
-              if (r) v = cmul(v, twiddle(tw, k * r * stride, inv));
+              if (r) v = cmul(v, twiddle(tw, off + r * Ns + k, inv));
+              // W_R^{rq} = entry (r q mod R) * (N/R) of the last-pass layout:
+              // use the full-circle table that follows the pass tables
               const int e = (r * q) % R;
-              acc = acc + (e ? cmul(v, twiddle(tw, e * NR, inv)) : v);
+              acc = acc + (e ? cmul(v, twiddle(tw, f.full + e * NR, inv)) : v);
             }
             y[sidx(idx + q * Ns)] = acc;
           }
@@ -230,6 +236,7 @@ struct ShapeRT {
       C *tmp = a;
       a = b;
       b = tmp;
+      off += R * Ns;
       Ns *= R;
     }
     return a;
@@ -245,6 +252,21 @@ typedef ShapeCT<768, 16, 16, 3> Shape768;
 typedef ShapeCT<1536, 16, 16, 2, 3> Shape1536;
 typedef ShapeCT<1920, 16, 8, 3, 5> Shape1920;
 typedef ShapeCT<3840, 16, 16, 3, 5> Shape3840;
+
+// Radix list of the compile-time shape serving N (must match the typedefs
+// above); false for lengths that take the run-time path.
+inline bool ct_radix_list(int N, int *r, int *np) {
+  static const int lists[][6] = {{48, 16, 3}, {96, 16, 2, 3}, {192, 16, 4, 3}, {384, 16, 8, 3}, {768, 16, 16, 3},
+                                 {1536, 16, 16, 2, 3}, {1920, 16, 8, 3, 5}, {3840, 16, 16, 3, 5}};
+  for (const auto &l : lists)
+    if (l[0] == N) {
+      int k = 0;
+      for (int i = 1; i < 6 && l[i]; ++i) r[k++] = l[i];
+      *np = k;
+      return true;
+    }
+  return false;
+}
 
 // Calls f.template operator()<Shape>() with the shape serving length N.
 template <typename Fn> int with_shape(int N, Fn &&fn) {

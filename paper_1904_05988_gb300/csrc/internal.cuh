@@ -69,6 +69,43 @@ template <typename C> __device__ __forceinline__ C cconj(C a) { a.y = -a.y; retu
 template <typename C> __device__ __forceinline__ C times_i(C a) { C r; r.x = -a.y; r.y = a.x; return r; }
 
 // ---------------------------------------------------------------------------
+// double <-> float conversions on the integer pipe.  The hardware conversion
+// instructions issue on the FP64 pipe, which is narrow on this GPU; these do
+// the IEEE-754 format change with integer operations instead.
+// d2f: round to nearest even; |x| below the smallest normal float (2^-126)
+// becomes a signed zero, overflow gives +-inf, NaN stays NaN.
+// f2d: exact (subnormal floats take the hardware path).
+// ---------------------------------------------------------------------------
+__device__ __forceinline__ float d2f_alu(double x) {
+  const unsigned long long b = (unsigned long long)__double_as_longlong(x);
+  const unsigned hi = (unsigned)(b >> 32), lo = (unsigned)b;
+  const unsigned sign = hi & 0x80000000u;
+  const int e = (int)((hi >> 20) & 0x7ffu);
+  const unsigned m = ((hi & 0xFFFFFu) << 3) | (lo >> 29);   // top 23 mantissa bits
+  const unsigned rem = lo & 0x1FFFFFFFu;                     // 29 discarded bits
+  if (e == 0x7ff) return __uint_as_float(sign | 0x7f800000u | ((m | rem) ? 0x400000u : 0u));
+  const int fe = e - 1023 + 127;
+  if (fe <= 0) return __uint_as_float(sign);
+  if (fe >= 255) return __uint_as_float(sign | 0x7f800000u);
+  unsigned r = ((unsigned)fe << 23) | m;
+  if (rem > 0x10000000u || (rem == 0x10000000u && (m & 1u))) r += 1u;   // carry may reach +inf: correct
+  return __uint_as_float(sign | r);
+}
+
+__device__ __forceinline__ double f2d_alu(float f) {
+  const unsigned u = __float_as_uint(f);
+  const unsigned sign = u & 0x80000000u, e = (u >> 23) & 0xffu, m = u & 0x7fffffu;
+  if (e == 0) return m ? (double)f : __hiloint2double((int)sign, 0);
+  if (e == 0xffu) return __hiloint2double((int)(sign | 0x7ff00000u | (m >> 3)), (int)(m << 29));
+  return __hiloint2double((int)(sign | ((e + 896u) << 20) | (m >> 3)), (int)(m << 29));
+}
+
+template <typename M> __device__ __forceinline__ double to_double(M x) { return (double)x; }
+template <> __device__ __forceinline__ double to_double<float>(float x) { return f2d_alu(x); }
+template <typename M> __device__ __forceinline__ M from_double(double x) { return (M)x; }
+template <> __device__ __forceinline__ float from_double<float>(double x) { return d2f_alu(x); }
+
+// ---------------------------------------------------------------------------
 // triangle indexing
 // ---------------------------------------------------------------------------
 // packed offset of order m in a degree-T triangle (the ABI layout)
@@ -85,8 +122,9 @@ constexpr int kMaxPasses = 24;
 struct FftPlan {
   int N = 0;
   int npass = 0;
+  int full = 0;             // offset of the full-circle part of the table
   int radix[kMaxPasses];
-  double2 *tw64 = nullptr;  // exp(-2 pi i e / N), e = 0..N-1
+  double2 *tw64 = nullptr;  // per-pass twiddles, then exp(-2 pi i e / N), e < N
   float2 *tw32 = nullptr;
 };
 
@@ -126,6 +164,8 @@ struct sht_plan {
   double *d_eps = nullptr;          // [ne] eps_n^m = sqrt((n^2-m^2)/(4n^2-1)), extended triangle
   double *d_ilap = nullptr;         // [T+2] 1/(n(n+1)) (0 at n = 0)
   float *d_eps32 = nullptr, *d_ilap32 = nullptr;   // float copies for mixed plans
+  double *d_rowf = nullptr;         // [nh][2]: 1/(1-mu_j^2), w_j (northern rows)
+  float *d_rowf32 = nullptr;        // float copy
   pfsh::FftPlan fft;
   pfsh::TcDir tc[2];                // [0] synthesis, [1] analysis (tensor-core precisions)
   // workspace for one pass of at most max_batch fields
@@ -218,7 +258,7 @@ bool uses_tensor_cores(int prec);
 int ifft_rows(const sht_plan *p, int cols, void *grid, cudaStream_t s);        // F -> grid
 int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s);   // grid -> H
 int grid_rhs(const sht_plan *p, int B, const swe_params &prm, cudaStream_t s); // F -> H (RHS)
-int ifft_rows_f64_raw(int N, int npass, const int *radix, int T, int nlat, int cols, const double2 *F,
+int ifft_rows_f64_raw(int N, int npass, const int *radix, int full, int T, int nlat, int cols, const double2 *F,
                       const double2 *tw, double *grid, cudaStream_t s);
 
 // spectral pre/post processing

@@ -15,11 +15,14 @@
 // memory as ready-made shared-memory images, one per (m, row tile, parity,
 // K chunk of <= 64), bf16 hi followed by bf16 lo, and is fetched with one
 // bulk TMA copy per chunk; the activation side (A operand) is read as fp32
-// by the four warps of the CTA, split into bf16 hi/lo and stored to shared
-// memory.  Two stages overlap the conversion of chunk q+1 with the MMAs of
-// chunk q.  One thread issues the MMAs; accumulators for both parities live
-// in TMEM (2 x N <= 512 columns).  Every wait is bounded; on a timeout the
-// status word records ST_TIMEOUT and the CTA winds down.
+// (column pairs, float2) by the eight warps of the CTA, split into bf16
+// hi/lo and stored to shared memory.  Two stages overlap the conversion of
+// chunk q+1 with the MMAs of chunk q.  One thread issues the MMAs;
+// accumulators for both parities live in TMEM (2 x N <= 512 columns) and are
+// drained by both warpgroups (a warp reads the 32 TMEM lanes of its quadrant,
+// the two warpgroups take alternate 16-column groups).  Every wait is
+// bounded; on a timeout the status word records ST_TIMEOUT and the CTA winds
+// down.
 #include <algorithm>
 #include <vector>
 
@@ -33,8 +36,10 @@ namespace {
 constexpr int KC = 64;      // max K extent of one chunk
 constexpr int MROWS = 128;  // MMA M: real columns per CTA
 
+constexpr int NTHREADS = 256;
+
 template <bool X3, bool FP16, bool ANALYSIS>
-__global__ void __launch_bounds__(128, 1)
+__global__ void __launch_bounds__(NTHREADS, 1)
     k_legendre_tc(int T, int nlat, int cols_real, int ntiles, const float *__restrict__ act,
                   const uint8_t *__restrict__ img, const TcChunk *__restrict__ chunks,
                   const TcWork *__restrict__ work, int Nmax, float *__restrict__ out, int *status) {
@@ -86,33 +91,44 @@ __global__ void __launch_bounds__(128, 1)
       tc::mbar_arrive_expect_tx(&full[s], bytes);
       tc::bulk_g2s(stB[s], img + ch.off, bytes, &full[s]);
     }
-    // produce the activation chunk: rows = 128 real columns, K = KL
+    // produce the activation chunk: rows = 128 real columns, K = KL; one
+    // item = two adjacent columns x 8 consecutive K, loaded as float2
     uint8_t *Ahi = stA[s], *Alo = stA[s] + a_half;
     const int groups = KL >> 3;
-    for (int it = tid; it < MROWS * groups; it += 128) {
-      const int r = it & (MROWS - 1), g = it >> 7;
-      const int c = cb * MROWS + r;
-      uint16_t hi[8], lo[8];
+    for (int it = tid; it < (MROWS / 2) * groups; it += NTHREADS) {
+      const int rp = it & (MROWS / 2 - 1), g = it >> 6;
+      const int r = 2 * rp, c = cb * MROWS + r;
+      float2 v[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
         const int k = ch.kstart + g * 8 + i;
-        float x = 0.f;
+        v[i] = make_float2(0.f, 0.f);
         if (c < cols_real) {
           if (!ANALYSIS) {
             const int noff = 2 * k + ch.p;      // n - m
-            if (noff < m_len) x = act[(eo + noff) * cols_real + c];
+            if (noff < m_len) v[i] = *(const float2 *)(act + (eo + noff) * cols_real + c);
           } else {
-            if (k < nh) x = act[(((size_t)m * 2 + ch.p) * nh + k) * cols_real + c];
+            if (k < nh) v[i] = *(const float2 *)(act + (((size_t)m * 2 + ch.p) * nh + k) * cols_real + c);
           }
         }
-        tc::split2<FP16>(x, hi[i], lo[i]);
       }
-      const uint32_t off = tc::tile_offset(r, g * 8, KL);
-      *(uint4 *)(Ahi + off) = make_uint4(hi[0] | (uint32_t)hi[1] << 16, hi[2] | (uint32_t)hi[3] << 16,
-                                         hi[4] | (uint32_t)hi[5] << 16, hi[6] | (uint32_t)hi[7] << 16);
-      if (X3)
-        *(uint4 *)(Alo + off) = make_uint4(lo[0] | (uint32_t)lo[1] << 16, lo[2] | (uint32_t)lo[3] << 16,
-                                           lo[4] | (uint32_t)lo[5] << 16, lo[6] | (uint32_t)lo[7] << 16);
+      uint16_t h0[8], l0[8], h1[8], l1[8];
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        tc::split2<FP16>(v[i].x, h0[i], l0[i]);
+        tc::split2<FP16>(v[i].y, h1[i], l1[i]);
+      }
+      const uint32_t off0 = tc::tile_offset(r, g * 8, KL), off1 = tc::tile_offset(r + 1, g * 8, KL);
+      *(uint4 *)(Ahi + off0) = make_uint4(h0[0] | (uint32_t)h0[1] << 16, h0[2] | (uint32_t)h0[3] << 16,
+                                          h0[4] | (uint32_t)h0[5] << 16, h0[6] | (uint32_t)h0[7] << 16);
+      *(uint4 *)(Ahi + off1) = make_uint4(h1[0] | (uint32_t)h1[1] << 16, h1[2] | (uint32_t)h1[3] << 16,
+                                          h1[4] | (uint32_t)h1[5] << 16, h1[6] | (uint32_t)h1[7] << 16);
+      if (X3) {
+        *(uint4 *)(Alo + off0) = make_uint4(l0[0] | (uint32_t)l0[1] << 16, l0[2] | (uint32_t)l0[3] << 16,
+                                            l0[4] | (uint32_t)l0[5] << 16, l0[6] | (uint32_t)l0[7] << 16);
+        *(uint4 *)(Alo + off1) = make_uint4(l1[0] | (uint32_t)l1[1] << 16, l1[2] | (uint32_t)l1[3] << 16,
+                                            l1[4] | (uint32_t)l1[5] << 16, l1[6] | (uint32_t)l1[7] << 16);
+      }
     }
     tc::fence_proxy_async();
     __syncthreads();
@@ -143,10 +159,12 @@ __global__ void __launch_bounds__(128, 1)
   ok &= tc::mbar_wait(fin, 0);
   tc::fence_after_sync();
 
-  // epilogue: lane = real column, TMEM column = row of the tile
-  const int c = cb * MROWS + tid;
-  const uint32_t tl = tmem + ((uint32_t)(warp * 32) << 16);
-  for (int c0 = 0; c0 < N; c0 += 16) {
+  // epilogue: lane = real column, TMEM column = row of the tile; warp w reads
+  // the lanes of quadrant w % 4, warpgroup w / 4 takes every other 16 columns
+  const int quad = warp & 3, wg = warp >> 2;
+  const int c = cb * MROWS + quad * 32 + (tid & 31);
+  const uint32_t tl = tmem + ((uint32_t)(quad * 32) << 16);
+  for (int c0 = wg * 16; c0 < N; c0 += 32) {
     float v0[16], v1[16];
     tc::tmem_ld16(tl + c0, v0);
     tc::tmem_ld16(tl + N + c0, v1);
@@ -334,7 +352,7 @@ static int launch_tc(const sht_plan *p, const TcDir &d, int cols, const float *a
   dim3 g((cols_real + MROWS - 1) / MROWS, d.ntiles, p->T + 1);
   {
     PFSH_LAUNCH(name, s);
-    kern<<<g, 128, smem, s>>>(p->T, p->nlat, cols_real, d.ntiles, act, d.img, d.chunks, d.work, d.Nmax, out,
+    kern<<<g, NTHREADS, smem, s>>>(p->T, p->nlat, cols_real, d.ntiles, act, d.img, d.chunks, d.work, d.Nmax, out,
                               device_status());
   }
   PFSH_CHECK_LAUNCH(name);

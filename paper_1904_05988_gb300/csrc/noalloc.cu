@@ -15,6 +15,7 @@
 #include <algorithm>
 #include <string>
 
+#include "fft_core.cuh"
 #include "internal.cuh"
 
 namespace pfsh {
@@ -29,9 +30,15 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 // device object).
 static void *g_noalloc_addr[64] = {nullptr};
 
-// Gaussian latitudes (northern half, Newton on P_nlat) and FFT twiddles
-// exp(-2 pi i e / nlon).
-__global__ void k_noalloc_setup(int nlat, int nlon, double *mu, double2 *tw) {
+struct PassTable {        // twiddle layout of the FFT passes (fft_core.cuh)
+  int npass, full;
+  int R[kMaxPasses], Ns[kMaxPasses], off[kMaxPasses];
+};
+
+// Gaussian latitudes (northern half, Newton on P_nlat) and FFT twiddles:
+// entry off_p + r Ns_p + k of pass p = exp(-2 pi i k r / (Ns_p R_p)), then the
+// full circle exp(-2 pi i e / nlon) from offset `full`.
+__global__ void k_noalloc_setup(int nlat, int nlon, PassTable pt, double *mu, double2 *tw) {
   const int t = blockIdx.x * blockDim.x + threadIdx.x;
   if (t < nlat / 2) {
     double x = cospi((t + 0.75) / (nlat + 0.5));
@@ -48,9 +55,20 @@ __global__ void k_noalloc_setup(int nlat, int nlon, double *mu, double2 *tw) {
     }
     mu[t] = x;
   }
-  if (t < nlon) {
+  if (t < pt.full + nlon) {
+    double num, den;
+    if (t >= pt.full) {
+      num = t - pt.full;
+      den = nlon;
+    } else {
+      int p = 0;
+      while (p + 1 < pt.npass && t >= pt.off[p + 1]) ++p;
+      const int e = t - pt.off[p], r = e / pt.Ns[p], k = e - r * pt.Ns[p];
+      num = (double)k * r;
+      den = (double)pt.Ns[p] * pt.R[p];
+    }
     double sn, cs;
-    sincospi(2.0 * (double)t / (double)nlon, &sn, &cs);
+    sincospi(2.0 * num / den, &sn, &cs);
     tw[t] = make_double2(cs, -sn);
   }
 }
@@ -132,11 +150,26 @@ extern "C" int sht_inverse_noalloc(int T, int nlat, int nlon, const double *spec
   if (batch == 0) return PFSH_OK;
   if (!spec || !grid) return fail(PFSH_EINVAL, "sht_inverse_noalloc: NULL buffer");
   int rad[kMaxPasses], npass = 0;
-  if (radices(nlon, rad, &npass)) return fail(PFSH_EINVAL, "sht_inverse_noalloc: nlon has a prime factor above 61");
+  if (!ct_radix_list(nlon, rad, &npass) && radices(nlon, rad, &npass))
+    return fail(PFSH_EINVAL, "sht_inverse_noalloc: nlon has a prime factor above 61");
+  PassTable pt{};
+  pt.npass = npass;
+  {
+    int Ns = 1, off = 0;
+    for (int p = 0; p < npass; ++p) {
+      pt.R[p] = rad[p];
+      pt.Ns[p] = Ns;
+      pt.off[p] = off;
+      off += rad[p] * Ns;
+      Ns *= rad[p];
+    }
+    pt.full = off;
+  }
+  const int ntw = pt.full + nlon;
   // scratch: mu [nlat/2] | twiddles [nlon] | F [T+1][nlat][batch], each 256-byte aligned
   auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const size_t o_tw = up((size_t)(nlat / 2) * sizeof(double));
-  const size_t o_F = o_tw + up((size_t)nlon * sizeof(double2));
+  const size_t o_F = o_tw + up((size_t)ntw * sizeof(double2));
   const size_t need = o_F + (size_t)(T + 1) * nlat * batch * sizeof(double2);
   if (need > kNoallocScratchBytes)
     return fail(PFSH_EINVAL, "sht_inverse_noalloc: (T+1)*nlat*batch*16 bytes plus nodes and twiddles exceed the "
@@ -156,9 +189,9 @@ extern "C" int sht_inverse_noalloc(int T, int nlat, int nlon, const double *spec
   double2 *F = (double2 *)(base + o_F);
   cudaStream_t s = (cudaStream_t)stream;
   {
-    const int n = std::max(nlat / 2, nlon);
+    const int n = std::max(nlat / 2, ntw);
     PFSH_LAUNCH("k_noalloc_setup", s);
-    k_noalloc_setup<<<(n + 127) / 128, 128, 0, s>>>(nlat, nlon, mu, tw);
+    k_noalloc_setup<<<(n + 127) / 128, 128, 0, s>>>(nlat, nlon, pt, mu, tw);
   }
   PFSH_CHECK_LAUNCH("k_noalloc_setup");
   {
@@ -166,5 +199,5 @@ extern "C" int sht_inverse_noalloc(int T, int nlat, int nlon, const double *spec
     k_noalloc_synth<<<dim3((nlat / 2 + 63) / 64, T + 1), 64, 0, s>>>(T, nlat, batch, mu, (const double2 *)spec, F);
   }
   PFSH_CHECK_LAUNCH("k_noalloc_synth");
-  return ifft_rows_f64_raw(nlon, npass, rad, T, nlat, batch, F, tw, grid, s);
+  return ifft_rows_f64_raw(nlon, npass, rad, pt.full, T, nlat, batch, F, tw, grid, s);
 }

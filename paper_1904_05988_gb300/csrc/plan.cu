@@ -12,6 +12,7 @@
 #include <cmath>
 #include <new>
 
+#include "fft_core.cuh"
 #include "internal.cuh"
 
 namespace pfsh {
@@ -202,36 +203,50 @@ int legendre_table_build(sht_plan *p, cudaStream_t s) {
 int fft_plan_init(FftPlan &f, int N) {
   f.N = N;
   f.npass = 0;
-  int n = N;
-  const int small[] = {4, 2, 3, 5};
-  for (int r : small) {
-    while (n % r == 0) {
-      if (f.npass >= kMaxPasses) return fail(PFSH_EINVAL, "FFT length has too many factors");
-      f.radix[f.npass++] = r;
-      n /= r;
+  if (!ct_radix_list(N, f.radix, &f.npass)) {
+    int n = N;
+    const int small[] = {4, 2, 3, 5};
+    for (int r : small) {
+      while (n % r == 0) {
+        if (f.npass >= kMaxPasses) return fail(PFSH_EINVAL, "FFT length has too many factors");
+        f.radix[f.npass++] = r;
+        n /= r;
+      }
+    }
+    for (int r = 7; n > 1; r += 2) {
+      while (n % r == 0) {
+        if (r > 61) return fail(PFSH_EINVAL, "FFT length has a prime factor above 61");
+        if (f.npass >= kMaxPasses) return fail(PFSH_EINVAL, "FFT length has too many factors");
+        f.radix[f.npass++] = r;
+        n /= r;
+      }
     }
   }
-  for (int r = 7; n > 1; r += 2) {
-    while (n % r == 0) {
-      if (r > 61) return fail(PFSH_EINVAL, "FFT length has a prime factor above 61");
-      if (f.npass >= kMaxPasses) return fail(PFSH_EINVAL, "FFT length has too many factors");
-      f.radix[f.npass++] = r;
-      n /= r;
-    }
-  }
-  std::vector<double2> t64(N);
-  std::vector<float2> t32(N);
+  // per-pass twiddles (entry r*Ns + k of pass (R, Ns) = exp(-2 pi i k r/(Ns R)))
+  // followed by the full circle exp(-2 pi i e/N), e < N; host libm in double
+  std::vector<double2> t64;
   const double two_pi = 6.28318530717958647692;
-  for (int e = 0; e < N; ++e) {
-    // exp(-2 pi i e / N), host libm in double
-    double ang = two_pi * (double)e / (double)N;
-    t64[e] = make_double2(std::cos(ang), -std::sin(ang));
-    t32[e] = make_float2((float)t64[e].x, (float)t64[e].y);
+  int Ns = 1;
+  for (int p = 0; p < f.npass; ++p) {
+    const int R = f.radix[p];
+    for (int r = 0; r < R; ++r)
+      for (int k = 0; k < Ns; ++k) {
+        const double ang = two_pi * (double)(k * r) / (double)(Ns * R);
+        t64.push_back(make_double2(std::cos(ang), -std::sin(ang)));
+      }
+    Ns *= R;
   }
-  PFSH_CUDA(cudaMalloc(&f.tw64, N * sizeof(double2)));
-  PFSH_CUDA(cudaMalloc(&f.tw32, N * sizeof(float2)));
-  PFSH_CUDA(cudaMemcpy(f.tw64, t64.data(), N * sizeof(double2), cudaMemcpyHostToDevice));
-  PFSH_CUDA(cudaMemcpy(f.tw32, t32.data(), N * sizeof(float2), cudaMemcpyHostToDevice));
+  f.full = (int)t64.size();
+  for (int e = 0; e < N; ++e) {
+    const double ang = two_pi * (double)e / (double)N;
+    t64.push_back(make_double2(std::cos(ang), -std::sin(ang)));
+  }
+  std::vector<float2> t32(t64.size());
+  for (size_t i = 0; i < t64.size(); ++i) t32[i] = make_float2((float)t64[i].x, (float)t64[i].y);
+  PFSH_CUDA(cudaMalloc(&f.tw64, t64.size() * sizeof(double2)));
+  PFSH_CUDA(cudaMalloc(&f.tw32, t32.size() * sizeof(float2)));
+  PFSH_CUDA(cudaMemcpy(f.tw64, t64.data(), t64.size() * sizeof(double2), cudaMemcpyHostToDevice));
+  PFSH_CUDA(cudaMemcpy(f.tw32, t32.data(), t32.size() * sizeof(float2), cudaMemcpyHostToDevice));
   return PFSH_OK;
 }
 
@@ -258,6 +273,8 @@ static void plan_free(sht_plan *p) {
   if (p->d_eps) cudaFree(p->d_eps);
   if (p->d_ilap) cudaFree(p->d_ilap);
   if (p->d_eps32) cudaFree(p->d_eps32);
+  if (p->d_rowf) cudaFree(p->d_rowf);
+  if (p->d_rowf32) cudaFree(p->d_rowf32);
   if (p->d_ilap32) cudaFree(p->d_ilap32);
   if (p->ws) cudaFree(p->ws);
   fft_plan_free(p->fft);
@@ -324,6 +341,20 @@ extern "C" int sht_plan_create(sht_plan **out, int T, int nlat, int nlon, int ma
       return rc;
     }
     cudaMemcpy(p->d_eps32, eps32.data(), eps32.size() * sizeof(float), cudaMemcpyHostToDevice);
+    std::vector<double> rowf((size_t)p->nh * 2);
+    for (int j = 0; j < p->nh; ++j) {
+      const double x = p->mu[j];
+      rowf[2 * j] = 1.0 / ((1.0 - x) * (1.0 + x));
+      rowf[2 * j + 1] = p->w[j];
+    }
+    std::vector<float> rowf32(rowf.begin(), rowf.end());
+    if ((rc = alloc((void **)&p->d_rowf, rowf.size() * sizeof(double))) ||
+        (rc = alloc((void **)&p->d_rowf32, rowf32.size() * sizeof(float)))) {
+      plan_free(p);
+      return rc;
+    }
+    cudaMemcpy(p->d_rowf, rowf.data(), rowf.size() * sizeof(double), cudaMemcpyHostToDevice);
+    cudaMemcpy(p->d_rowf32, rowf32.data(), rowf32.size() * sizeof(float), cudaMemcpyHostToDevice);
     cudaMemcpy(p->d_ilap32, ilap32.data(), ilap32.size() * sizeof(float), cudaMemcpyHostToDevice);
   }
   cudaMemcpy(p->d_mu, p->mu.data(), nlat * sizeof(double), cudaMemcpyHostToDevice);

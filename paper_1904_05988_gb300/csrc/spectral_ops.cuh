@@ -28,7 +28,10 @@ template <typename M> struct SpecTables {
 template <typename M>
 __device__ __forceinline__ typename cpx<M>::t ld(const double2 *p) {
   const double2 v = *p;
-  return mk<typename cpx<M>::t>(v.x, v.y);
+  typename cpx<M>::t r;
+  r.x = from_double<M>(v.x);
+  r.y = from_double<M>(v.y);
+  return r;
 }
 
 // X values (eta, Phi', U, V) of coefficient (m, n), n <= T+1, of one state.
@@ -58,8 +61,10 @@ __device__ __forceinline__ void prep_point(int T, int m, int n, const double2 *_
       double2 e = zeta[base + n], q = Phi[base + n];
       if (n == 1) e.x += 2.0 * omega * 0.81649658092772603273;   // 2 Omega mu, mu = P_1^0 / sqrt(3/2)
       if (n == 0) q.x -= 1.41421356237309504880 * phibar;        // 1 = sqrt(2) P_0^0
-      eta = mk<C>(e.x, 0.0);
-      php = mk<C>(q.x, 0.0);
+      eta.x = from_double<M>(e.x);
+      eta.y = 0;
+      php.x = from_double<M>(q.x);
+      php.y = 0;
     } else {
       eta = ld<M>(zeta + base + n);
       php = ld<M>(Phi + base + n);
@@ -92,10 +97,12 @@ __device__ __forceinline__ void assemble_point(int m, int n, const C cur[5], con
   const C A1u = up[0], B1u = up[1], B2u = up[3];
   const C A1d = has_dn ? dn[0] : z, B1d = has_dn ? dn[1] : z, B2d = has_dn ? dn[3] : z;
   const M k = (M)n * (M)(n + 1) * inva2;
-  fe[0] = make_double2(-(-mm * A2.y + cu * B2u.x - cd * B2d.x) * inva, -(mm * A2.x + cu * B2u.y - cd * B2d.y) * inva);
-  fe[1] = make_double2(-(-mm * A1.y + cu * B1u.x - cd * B1d.x) * inva, -(mm * A1.x + cu * B1u.y - cd * B1d.y) * inva);
-  fe[2] = make_double2((-mm * B1.y - cu * A1u.x + cd * A1d.x) * inva + k * E.x,
-                       (mm * B1.x - cu * A1u.y + cd * A1d.y) * inva + k * E.y);
+  fe[0] = make_double2(to_double<M>(-(-mm * A2.y + cu * B2u.x - cd * B2d.x) * inva),
+                       to_double<M>(-(mm * A2.x + cu * B2u.y - cd * B2d.y) * inva));
+  fe[1] = make_double2(to_double<M>(-(-mm * A1.y + cu * B1u.x - cd * B1d.x) * inva),
+                       to_double<M>(-(mm * A1.x + cu * B1u.y - cd * B1d.y) * inva));
+  fe[2] = make_double2(to_double<M>((-mm * B1.y - cu * A1u.x + cd * A1d.x) * inva + k * E.x),
+                       to_double<M>((mm * B1.x - cu * A1u.y + cd * A1d.y) * inva + k * E.y));
   if (m == 0) { fe[0].y = 0.0; fe[1].y = 0.0; fe[2].y = 0.0; }
 }
 
