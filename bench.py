@@ -3,12 +3,15 @@ T127 on 192x384, 32 time slices, 5/3 Gauss-Lobatto nodes, dt = 120 s).
 
 A step is one PFASST iteration (Algorithm 1: fine sweeps, restriction + FAS,
 serial coarse chain, interpolation) over all 32 slices -- every stage of the
-hot path.  The JSON line reports PFASST iterations/s (the headline), SWE RHS
+hot path.  The JSON line reports PFASST iterations/s of the mixed-precision
+path (3xBF16 Legendre GEMMs on tensor cores, FP32 FFT/grid, FP64 spectral
+bookkeeping; the headline), the same for the plain FP64 GPU path and the
+speedup over it, the difference of the two paths' end states, SWE RHS
 evaluations/s at T255 with 32 states per call, an end-to-end block solve
-through the C ABI with host buffers, the roofline of the dominant kernel and
-the FP64 CPU oracle timed on a bounded sample.
+through the C ABI with host buffers, the rooflines of the top kernels and the
+FP64 CPU oracle timed on a bounded sample.
 
-    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec fp64] [--impl reference]
+    python bench.py [--gpus N] [--steps K] [--warmup W] [--prec bf16x3] [--impl reference]
 
 Under torchrun (N > 1) every rank solves an independent replica of the
 workload (different bump location); `value` is the whole-job rate.
@@ -139,6 +142,29 @@ def initial_state(ps, torch, dev, seed: int):
     return st, phibar
 
 
+def time_iterations(ps, torch, pf, stream, steps: int) -> float:
+    """Device time (ms) of `steps` back-to-back iterations on `stream`."""
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    for _ in range(steps):
+        ps.pfasst_iteration(pf, False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    return e0.elapsed_time(e1)
+
+
+def block_solve(ps, torch, pf, h_in, h_out, d_in, d_out):
+    """One block of the user's workflow: H2D initial value, predictor, NPF
+    iterations, D2H of the last slice's end value."""
+    d_in.copy_(h_in, non_blocking=True)
+    ps.pfasst_set_initial(pf, d_in)
+    ps.pfasst_predict(pf)
+    for k in range(NPF):
+        ps.pfasst_iteration(pf, k == NPF - 1)
+    ps.pfasst_get(pf, 0, NTS - 1, NF - 1, d_out)
+    h_out.copy_(d_out, non_blocking=True)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1904_05988_gb300 as ps
@@ -156,8 +182,12 @@ def run_ours(args, rank, world, local_rank):
         torch.cuda.synchronize()
 
     st0, phibar = initial_state(ps, torch, dev, seed=2 + rank)
-    pf = ps.pfasst_create(NTS, NF, NC, TF, *GRID_F, TC, *GRID_C, DT, syn.EARTH_RADIUS, syn.OMEGA, syn.NU,
-                          phibar, args.prec)
+
+    def make(prec):
+        return ps.pfasst_create(NTS, NF, NC, TF, *GRID_F, TC, *GRID_C, DT, syn.EARTH_RADIUS, syn.OMEGA, syn.NU,
+                                phibar, prec)
+
+    pf = make(args.prec)
     d_st0 = torch.tensor(st0, dtype=torch.complex128, device=dev)
     stream = torch.cuda.current_stream()
     ps.pfasst_set_initial(pf, d_st0)
@@ -172,16 +202,11 @@ def run_ours(args, rank, world, local_rank):
     time.sleep(0.3)
     barrier()
     n0 = ps.pfsh_kernel_launches()
-    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     torch.cuda.nvtx.range_push("pfasst_timed")
-    e0.record(stream)
-    for _ in range(args.steps):
-        ps.pfasst_iteration(pf, False)
-    e1.record(stream)
+    ms = time_iterations(ps, torch, pf, stream, args.steps)
     torch.cuda.nvtx.range_pop()
     barrier()
     launches = ps.pfsh_kernel_launches() - n0
-    ms = e0.elapsed_time(e1)
     clk = clocks.stop()
     ps.pfsh_sync_status()
     ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
@@ -192,21 +217,26 @@ def run_ours(args, rank, world, local_rank):
     value = world * args.steps / (ms_max / 1e3)
 
     # ---- SWE RHS evaluations/s at T255, 32 states per call ----
-    plan_r = ps.sht_plan_create(TF, *GRID_F, 5 * NTS, args.prec)
-    ctx_r = ps.swe_ctx_create(plan_r, syn.EARTH_RADIUS, syn.OMEGA, syn.NU, phibar)
-    rhs_in = d_st0[None].repeat(NTS, 1, 1).contiguous()
-    rhs_fe, rhs_fi = torch.empty_like(rhs_in), torch.empty_like(rhs_in)
-    for _ in range(3):
-        ps.swe_rhs(ctx_r, rhs_in, rhs_fe, rhs_fi)
-    torch.cuda.synchronize()
-    r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
-    nrhs = 10
-    r0.record(stream)
-    for _ in range(nrhs):
-        ps.swe_rhs(ctx_r, rhs_in, rhs_fe, rhs_fi)
-    r1.record(stream)
-    torch.cuda.synchronize()
-    rhs_per_s = nrhs * NTS / (r0.elapsed_time(r1) / 1e3)
+    def rhs_rate(prec):
+        plan_r = ps.sht_plan_create(TF, *GRID_F, 5 * NTS, prec)
+        ctx_r = ps.swe_ctx_create(plan_r, syn.EARTH_RADIUS, syn.OMEGA, syn.NU, phibar)
+        rhs_in = d_st0[None].repeat(NTS, 1, 1).contiguous()
+        rhs_fe, rhs_fi = torch.empty_like(rhs_in), torch.empty_like(rhs_in)
+        for _ in range(3):
+            ps.swe_rhs(ctx_r, rhs_in, rhs_fe, rhs_fi)
+        torch.cuda.synchronize()
+        r0, r1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+        nrhs = 10
+        r0.record(stream)
+        for _ in range(nrhs):
+            ps.swe_rhs(ctx_r, rhs_in, rhs_fe, rhs_fi)
+        r1.record(stream)
+        torch.cuda.synchronize()
+        ctx_r.close()
+        plan_r.close()
+        return nrhs * NTS / (r0.elapsed_time(r1) / 1e3)
+
+    rhs_per_s = rhs_rate(args.prec)
 
     # ---- profiled pass (same workload, separate from the timed region) ----
     ps.pfsh_profiler_enable(True)
@@ -214,7 +244,7 @@ def run_ours(args, rank, world, local_rank):
         ps.pfasst_iteration(pf, False)
     ps.pfsh_profiler_enable(False)
     prof = ps.pfsh_profiler_report()
-    roofline = roofline_of(prof, args.prec, 2)
+    rooflines = rooflines_of(prof, args.prec, 2)
 
     # ---- end to end: host initial value -> block solve -> host end value ----
     h_in = torch.tensor(st0, dtype=torch.complex128).pin_memory()
@@ -222,43 +252,69 @@ def run_ours(args, rank, world, local_rank):
     d_in = torch.empty_like(d_st0)
     d_out = torch.empty_like(d_st0)
     blocks = max(1, min(3, args.steps))
+    block_solve(ps, torch, pf, h_in, h_out, d_in, d_out)
     torch.cuda.synchronize()
     b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     b0.record(stream)
     for _ in range(blocks):
-        d_in.copy_(h_in, non_blocking=True)
-        ps.pfasst_set_initial(pf, d_in)
-        ps.pfasst_predict(pf)
-        for k in range(NPF):
-            ps.pfasst_iteration(pf, k == NPF - 1)
-        ps.pfasst_get(pf, 0, NTS - 1, NF - 1, d_out)
-        h_out.copy_(d_out, non_blocking=True)
+        block_solve(ps, torch, pf, h_in, h_out, d_in, d_out)
     b1.record(stream)
     torch.cuda.synchronize()
     ms_block = b0.elapsed_time(b1) / blocks
-    if not np.all(np.isfinite(h_out.numpy().view(np.float64))):
+    end_state = h_out.numpy().copy()
+    if not np.all(np.isfinite(end_state.view(np.float64))):
         raise RuntimeError("non-finite solution")
     e2e_val = world * NPF / (ms_block / 1e3)
     state_bytes = 3 * syn.ncoef(TF) * 16
+    pf.close()
+
+    # ---- the plain FP64 GPU path on the same workload, for the speedup ----
+    fp64 = None
+    if args.prec != "fp64" and not args.no_fp64_path:
+        pf64 = make("fp64")
+        ps.pfasst_set_initial(pf64, d_st0)
+        ps.pfasst_predict(pf64)
+        for _ in range(3):
+            ps.pfasst_iteration(pf64, False)
+        k64 = max(2, min(5, args.steps))
+        ms64 = time_iterations(ps, torch, pf64, stream, k64) / k64
+        block_solve(ps, torch, pf64, h_in, h_out, d_in, d_out)
+        torch.cuda.synchronize()
+        ref = h_out.numpy()
+        diff = float(np.linalg.norm(end_state - ref) / np.linalg.norm(ref))
+        pert = end_state - st0
+        pert_ref = ref - st0
+        diff_pert = float(np.linalg.norm(pert - pert_ref) / np.linalg.norm(pert_ref))
+        pf64.close()
+        fp64 = {"value": world * 1e3 / ms64, "unit": "PFASST iterations/s", "ms_per_step": ms64, "steps": k64,
+                "swe_rhs_evals_per_s": rhs_rate("fp64"),
+                "speedup_of_value": value / (world * 1e3 / ms64),
+                "end_state_rel_l2_vs_fp64": diff, "end_state_change_rel_l2_vs_fp64": diff_pert,
+                "what": f"end value of slice {NTS - 1} after predictor + {NPF} iterations: relative L2 difference of "
+                        "the state, and of its change from the initial value (bump + jet evolution)"}
 
     cpu = cpu_baseline_sample() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
+        dtype = "f64" if args.prec == "fp64" else \
+            f"{args.prec} Legendre GEMMs, f32 FFT/grid, f64 spectral/SDC/FAS"
         line = {
-            "metric": "PFASST iterations/s (T255/T127, 32 slices, 5/3 nodes) and SWE RHS evals/s at T255",
+            "metric": "PFASST iterations/s (T255/T127, 32 slices, 5/3 nodes), mixed precision vs FP64 GPU path; "
+                      "SWE RHS evals/s at T255",
             "value": value, "unit": "PFASST iterations/s", "n_gpus": world, "steps": args.steps,
             "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
-            "vs_baseline": None, "dtype": "f64" if args.prec == "fp64" else f"f64 spectral + {args.prec} Legendre",
-            "data": "synthetic",
+            "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_ts": NTS, "nodes": [NF, NC], "T": [TF, TC],
                        "grid": [list(GRID_F), list(GRID_C)], "dt": DT, "prec": args.prec,
                        "parallelism": f"replicas x{world}", "l2": "working set 1.6 GB > 129 MB L2"},
             "swe_rhs_evals_per_s": rhs_per_s,
+            "fp64_gpu_path": fp64,
             "e2e": {"value": e2e_val, "unit": "PFASST iterations/s", "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes,
                     "what": f"per block: H2D initial value, predictor, {NPF} iterations, D2H last slice end value"},
             "gpu_launches": int(launches),
             "clocks": clk,
-            "roofline": roofline,
+            "roofline": rooflines[0] if rooflines else None,
+            "rooflines_top": rooflines[1:],
             "kernels_ms_per_iteration": {k: round(v[1] / 2, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
             "cpu_baseline": cpu,
         }
@@ -276,58 +332,102 @@ def peaks():
 
 
 FP64_PEAK_TFLOPS = 1.25   # nominal GB300 FP64 rate (no measured copy exists)
+SMS, FP32_LANES, SM_MAX_GHZ = 152, 128, 2.07
+FP32_PEAK_TFLOPS = SMS * FP32_LANES * 2 * SM_MAX_GHZ / 1e3   # 80.5: FMA = 2 flops per lane per clock
 
 
 def rhs_states_per_iteration():
     """RHS evaluations in one (non-final) iteration of Algorithm 1 over all
-    slices: fine = sweep nodes 1..Mf + node 0 after Step D; coarse = every
-    node in Step B + node 0 of slices 1.. in Step C + sweep nodes 1..Mc."""
+    slices: fine = sweep nodes 1..Mf + node 0 after Step D (batched);
+    coarse batched = every node in Step B; coarse chain = node 0 of slices
+    1.. + sweep nodes 1..Mc, one state per call (small-batch kernels)."""
     fine = NTS * (NF - 1) + NTS
-    coarse = NTS * NC + (NTS - 1) + NTS * (NC - 1)
-    return fine, coarse
+    coarse_batched = NTS * NC
+    coarse_chain = (NTS - 1) + NTS * (NC - 1)
+    return fine, coarse_batched, coarse_chain
 
 
 def kernel_work_per_iteration(name: str, prec: str):
-    """(algorithmic work, unit) of all launches of `name` in one iteration."""
-    nf_states, nc_states = rhs_states_per_iteration()
+    """(algorithmic work, unit, bound, note) of all launches of `name` in one
+    iteration; None if the kernel has no model."""
+    nfs, ncb, ncs = rhs_states_per_iteration()
     (nlat_f, _), (nlat_c, _) = GRID_F, GRID_C
+    ncf, ncc = syn.ncoef(TF), syn.ncoef(TC)
+    ncf1, ncc1 = syn.ncoef(TF + 1), syn.ncoef(TC + 1)
     elem = 8 if prec == "fp64" else 4
-    if name.startswith("k_synth"):
-        return nf_states * legendre_flops(TF, nlat_f, 4) + nc_states * legendre_flops(TC, nlat_c, 4), "flop"
-    if name.startswith("k_anal"):
-        return nf_states * legendre_flops(TF, nlat_f, 5) + nc_states * legendre_flops(TC, nlat_c, 5), "flop"
+    st_f, st_c = 48 * ncf, 48 * ncc       # bytes of one FP64 state (3 fields, complex)
+    tc = prec in ("bf16", "fp16", "bf16x3")
+    simt_bound = ("alu", "FP64 pipe") if prec == "fp64" else ("alu", "FP32 pipe")
+    if name.startswith("k_synth") or name.startswith("k_anal"):
+        cols = 4 if name.startswith("k_synth") else 5
+        w = nfs * legendre_flops(TF, nlat_f, cols) + ncb * legendre_flops(TC, nlat_c, cols)
+        if tc:
+            mult = 3 if prec == "bf16x3" else 1
+            return w, "flop", ("tensor", f"{mult} MMA products per algorithmic flop"), None
+        return w, "flop", simt_bound, None
+    if name.startswith("k_small_synth") or name.startswith("k_small_anal"):
+        cols = 4 if "synth" in name else 5
+        return ncs * legendre_flops(TC, nlat_c, cols), "flop", simt_bound, None
     if name == "k_grid_rhs":
-        return (nf_states * grid_rhs_bytes(TF, nlat_f, 1, elem) + nc_states * grid_rhs_bytes(TC, nlat_c, 1, elem),
-                "byte")
-    return None, None
+        return (nfs * grid_rhs_bytes(TF, nlat_f, 1, elem) + (ncb + ncs) * grid_rhs_bytes(TC, nlat_c, 1, elem),
+                "byte", ("hbm", None), None)
+    if name == "k_rhs_prep":
+        return (nfs * (st_f + 4 * ncf1 * 2 * elem) + ncb * (st_c + 4 * ncc1 * 2 * elem), "byte", ("hbm", None), None)
+    if name == "k_rhs_assemble":
+        return (nfs * (5 * ncf1 * 2 * elem + 3 * st_f) + ncb * (5 * ncc1 * 2 * elem + 3 * st_c), "byte",
+                ("hbm", None), None)
+    if name == "k_sdc_old":
+        # fine: theta_0, F_E and F_I at every node in, M "old" arrays out;
+        # coarse: the same plus M FAS arrays in
+        return NTS * ((1 + 2 * NF + (NF - 1)) * st_f + (1 + 2 * NC + 2 * (NC - 1)) * st_c), "byte", ("hbm", None), None
+    if name == "k_sdc_node":
+        mf, mc = NF - 1, NC - 1
+        return NTS * (mf * (mf + 1) * st_f + mc * (mc + 1) * st_c), "byte", ("hbm", None), None
+    if name == "k_interp_inc":
+        return 3 * NTS * (2 * NC + 2 * (NF - 1)) * st_c, "byte", ("hbm", None), None
+    if name == "k_fas":
+        return NTS * (2 * NF + 2 * NC + NC) * st_c, "byte", ("hbm", None), None
+    if name == "k_restrict":
+        return NTS * (NF + NC) * st_c, "byte", ("hbm", None), None
+    if name == "k_node0":
+        return (NTS - 1) * (2 * st_f + st_c), "byte", ("hbm", None), None
+    return None
 
 
-def roofline_of(prof: dict, prec: str, iterations: int) -> dict:
-    """Roofline of the kernel with the largest total time in the profiled
-    pass: algorithmic work of its launches / their summed duration (equal to
-    work per launch / mean launch duration)."""
-    if not prof:
-        return None
-    name, (n, tot_ms) = max(prof.items(), key=lambda kv: kv[1][1])
-    work, unit = kernel_work_per_iteration(name, prec)
-    pk, src = peaks()
+def roofline_entry(name: str, n: int, tot_ms: float, prec: str, iterations: int) -> dict:
     out = {"kernel": name, "launches": n, "mean_launch_ms": tot_ms / n, "traffic": None}
-    if work is None:
+    model = kernel_work_per_iteration(name, prec)
+    if model is None:
         out.update({"bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None})
         return out
+    work, unit, (bound, note), _ = model
     rate = work * iterations / (tot_ms / 1e3)
-    if unit == "flop" and prec == "fp64":
-        out.update({"bound": "alu", "achieved": rate / 1e12, "peak": FP64_PEAK_TFLOPS, "unit": "TFLOP/s",
-                    "frac": rate / 1e12 / FP64_PEAK_TFLOPS,
-                    "peak_source": "nominal FP64 rate of the recipe (1.25 TFLOP/s); no measured FP64 peak"})
-    elif unit == "flop":
+    pk, src = peaks()
+    if bound == "tensor":
         peak = pk["bf16_tflops_sustained"]
         out.update({"bound": "tensor", "achieved": rate / 1e12, "peak": peak, "unit": "TFLOP/s",
-                    "frac": rate / 1e12 / peak, "peak_source": src + " bf16 sustained"})
+                    "frac": rate / 1e12 / peak, "peak_source": f"{src} cuBLAS bf16 sustained",
+                    "note": f"algorithmic Legendre flops; {note}"})
+    elif bound == "alu":
+        peak = FP64_PEAK_TFLOPS if note == "FP64 pipe" else FP32_PEAK_TFLOPS
+        out.update({"bound": "alu", "achieved": rate / 1e12, "peak": peak, "unit": "TFLOP/s",
+                    "frac": rate / 1e12 / peak,
+                    "peak_source": ("nominal GB300 FP64 rate 1.25 TFLOP/s" if note == "FP64 pipe" else
+                                    "152 SMs x 128 FP32 lanes x 2 flops x 2.07 GHz")})
     else:
         out.update({"bound": "hbm", "achieved": rate / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
-                    "frac": rate / 1e9 / pk["hbm_gbs"], "peak_source": src})
+                    "frac": rate / 1e9 / pk["hbm_gbs"], "peak_source": f"{src} copy bandwidth"})
     return out
+
+
+def rooflines_of(prof: dict, prec: str, iterations: int, top: int = 5) -> list:
+    """Rooflines of the `top` kernels by total time in the profiled pass:
+    algorithmic work of their launches / their summed duration (= work per
+    launch / mean launch duration).  The first entry is the dominant kernel."""
+    if not prof:
+        return []
+    items = sorted(prof.items(), key=lambda kv: -kv[1][1])[:top]
+    return [roofline_entry(name, n, tot, prec, iterations) for name, (n, tot) in items]
 
 
 # ---------------------------------------------------------------------------
@@ -396,7 +496,8 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", default="fp64", choices=["fp64", "fp32", "bf16", "fp16", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "fp16", "bf16x3"])
+    ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the FP64 GPU path")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

@@ -182,6 +182,13 @@ typedef struct {
   double dt;                  /* time-step size of every slice [s]         */
   swe_params phys;
   int prec;                   /* pfsh_prec of both levels' transforms      */
+  int slice_groups;           /* pipeline depth of an iteration: slices are
+                               * split into this many groups of consecutive
+                               * slices, and the coarse chain (Step C) of a
+                               * group overlaps Steps A/B of the next ones.
+                               * 0 = automatic (1 for FP64, 2 otherwise);
+                               * clamped so that every group holds >= 4
+                               * slices.  Results do not depend on it.     */
 } pfasst_config;
 
 /* Allocates every slice's fine and coarse space-time arrays. */
@@ -196,7 +203,9 @@ int pfasst_set_initial(pfasst *pf, const double *theta0, pfsh_stream_t stream);
 int pfasst_predict(pfasst *pf, pfsh_stream_t stream);
 
 /* One PFASST iteration (Algorithm 1) over all slices.  last != 0 performs
- * Step A only (the paper's last iteration). */
+ * Step A only (the paper's last iteration).  Work is issued on `stream` and
+ * on an internal stream that joins back into `stream` before the call's
+ * work is complete, so stream order for the caller is unchanged. */
 int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream);
 
 /* Copy one node of one slice to `out` (device, [3][ncoef][2]); level 0 =

@@ -63,7 +63,7 @@ class PfasstConfig(ctypes.Structure):
     _fields_ = [("n_ts", c_int), ("fine_nodes", c_int), ("coarse_nodes", c_int),
                 ("Tf", c_int), ("nlat_f", c_int), ("nlon_f", c_int),
                 ("Tc", c_int), ("nlat_c", c_int), ("nlon_c", c_int),
-                ("dt", c_double), ("phys", SweParams), ("prec", c_int)]
+                ("dt", c_double), ("phys", SweParams), ("prec", c_int), ("slice_groups", c_int)]
 
 
 _sig = {
@@ -279,10 +279,10 @@ def sdc_sweep(level: SdcLevel, theta: torch.Tensor, fE: torch.Tensor, fI: torch.
 
 def pfasst_create(n_ts: int, fine_nodes: int, coarse_nodes: int, Tf: int, nlat_f: int, nlon_f: int,
                   Tc: int, nlat_c: int, nlon_c: int, dt: float, a: float, omega: float, nu: float,
-                  phibar: float, prec: int | str = PFSH_FP64) -> Pfasst:
+                  phibar: float, prec: int | str = PFSH_FP64, slice_groups: int = 0) -> Pfasst:
     prec = PREC_NAMES[prec] if isinstance(prec, str) else prec
     cfg = PfasstConfig(n_ts, fine_nodes, coarse_nodes, Tf, nlat_f, nlon_f, Tc, nlat_c, nlon_c, dt,
-                       SweParams(a, omega, nu, phibar), prec)
+                       SweParams(a, omega, nu, phibar), prec, slice_groups)
     h = c_void_p()
     _check(_lib.pfasst_create(ctypes.byref(h), ctypes.byref(cfg)))
     return Pfasst(h.value, cfg)

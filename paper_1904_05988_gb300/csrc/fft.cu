@@ -106,58 +106,9 @@ __global__ void __launch_bounds__(256) k_grid_rhs(FftArgs f, int T, int nlat, in
                                                   const Rl *__restrict__ rowf,
                                                   const typename cpx<Rl>::t *__restrict__ tw,
                                                   typename cpx<Rl>::t *__restrict__ H) {
-  typedef typename cpx<Rl>::t C;
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int N = Shape::n(f), NP = padded(N);
-  C *A = reinterpret_cast<C *>(smem_raw);  // 5 padded transforms
-  C *Bf = A + 5 * NP;                       // 5 padded transforms
-  const int j = blockIdx.x, b = blockIdx.y, js = nlat - 1 - j;
-  const int colsF = 4 * B, colsH = 5 * B;
-  for (int t = threadIdx.x; t < 4 * NP; t += blockDim.x) A[t] = mk<C>(0.0, 0.0);
-  __syncthreads();
-  for (int t = threadIdx.x; t < 4 * (T + 1); t += blockDim.x) {
-    const int m = t >> 2, fld = t & 3;     // consecutive threads: the 4 fields of one m
-    C fn = F[((size_t)m * nlat + j) * colsF + b * 4 + fld];
-    C fs = F[((size_t)m * nlat + js) * colsF + b * 4 + fld];
-    C *z = A + fld * NP;
-    if (m == 0) {
-      z[0] = mk<C>(fn.x, fs.x);
-    } else {
-      z[sidx(m)] = mk<C>(fn.x - fs.y, fn.y + fs.x);
-      z[sidx(N - m)] = mk<C>(fn.x + fs.y, -fn.y + fs.x);
-    }
-  }
-  __syncthreads();
-  C *g = Shape::run(f, A, Bf, 4, tw, true);
-  C *o = (g == A) ? Bf : A;
-  const Rl inv = rowf[2 * j];                // 1/(1 - mu_j^2)
-  const Rl h = (Rl)0.5 * inv;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    const int e = sidx(k);
-    const C eta = g[e], php = g[NP + e], U = g[2 * NP + e], V = g[3 * NP + e];
-    const Rl Ui = U.x * inv, Us = U.y * inv, Vi = V.x * inv, Vs = V.y * inv;
-    o[e] = mk<C>(eta.x * Ui, eta.y * Us);
-    o[NP + e] = mk<C>(eta.x * Vi, eta.y * Vs);
-    o[2 * NP + e] = mk<C>(php.x * Ui, php.y * Us);
-    o[3 * NP + e] = mk<C>(php.x * Vi, php.y * Vs);
-    o[4 * NP + e] = mk<C>((U.x * U.x + V.x * V.x) * h, (U.y * U.y + V.y * V.y) * h);
-  }
-  __syncthreads();
-  C *Z = Shape::run(f, o, g, 5, tw, false);
-  const Rl half = (Rl)0.5 / (Rl)N;
-  const Rl wj = rowf[2 * j + 1];
-  const int nh = nlat / 2;
-  for (int t = threadIdx.x; t < 5 * (T + 1); t += blockDim.x) {
-    const int m = t / 5, fld = t - 5 * m;   // consecutive threads: the 5 fields of one m
-    const C *z = Z + fld * NP;
-    C zm = z[sidx(m)];
-    C zc = cconj(z[sidx(m == 0 ? 0 : N - m)]);
-    C gn = half * (zm + zc);
-    C gs = half * times_i(zc - zm);
-    C he = wj * (gn + gs), ho = wj * (gn - gs);
-    H[(((size_t)m * 2 + 0) * nh + j) * colsH + b * 5 + fld] = he;
-    H[(((size_t)m * 2 + 1) * nh + j) * colsH + b * 5 + fld] = ho;
-  }
+  grid_rhs_body<Rl, Shape>(f, T, nlat, B, blockIdx.x, blockIdx.y, F, rowf, tw, H,
+                           reinterpret_cast<typename cpx<Rl>::t *>(smem_raw));
 }
 
 // ---------------------------------------------------------------------------

@@ -216,9 +216,30 @@ struct pfasst {
   int calls[2] = {0, 0};
   unsigned long long glaunches[2] = {0, 0};
   bool graphs = true;
+  // Step C runs on its own stream with its own coarse plan/context/level so
+  // that it overlaps Steps A and B of later slice groups (see pfasst.cu).
+  static constexpr int kMaxGroups = 32;
+  int groups = 1;
+  cudaStream_t chain_stream = nullptr;
+  sht_plan *plan_cc = nullptr;
+  swe_ctx *ctx_cc = nullptr;
+  sdc_level *lev_cc = nullptr;
+  cudaEvent_t ev_fork = nullptr, ev_B[kMaxGroups] = {}, ev_C[kMaxGroups] = {};
 };
 
 namespace pfsh {
+
+// ---------------------------------------------------------------------------
+// SDC node-update coefficients (dt folded in); see spectral.cu
+// ---------------------------------------------------------------------------
+struct SdcCoef {
+  double cE[16][16];  // dt (Q - QE') for the "old" right-hand sides
+  double cI[16][16];  // dt (Q - QI')
+  double nE[16][16];  // dt QE  (new explicit terms, j < i)
+  double nI[16][16];  // dt QI  (new implicit terms, j < i)
+  double h[16];       // dt QI[i][i]
+};
+SdcCoef sdc_coef(const sdc_level *l);
 
 // ---------------------------------------------------------------------------
 // kernels / launchers (defined in the .cu files)
@@ -279,11 +300,13 @@ int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const
 int sdc_build_matrices(sdc_level *l, int nodes);
 void lagrange_matrix(const double *src, int ns, const double *dst, int nd, double out[16][16]);
 
+// Step C of Algorithm 1 for slices n0..n1-1 with fused per-order launches
+// (small.cu); strides in doubles
+int chain_sweeps(sdc_level *l, double *th, double *fe, double *fi, const double *tau, size_t node_stride,
+                 size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s);
+
 // PFASST transfer kernels
 int restrict_launch(const double *Rt, int nf, int nc, const double *xf, size_t fstride,
                     double *xc, size_t cstride, int Tf, int Tc, int B, cudaStream_t s);
-int fas_launch(const pfasst *pf, cudaStream_t s);
-int interp_increment_launch(const pfasst *pf, cudaStream_t s);
-int node0_update_launch(const pfasst *pf, cudaStream_t s);
 
 }  // namespace pfsh

@@ -4,8 +4,16 @@
 // The paper's processors P_n become slice indices of node-major arrays
 // [node][slice][3][ncoef]; a "send" to the next processor is a device copy.
 // Step A (fine sweep) and Step B (restriction, coarse F, FAS) run batched
-// over all slices; Step C (coarse sweeps) is a chain in slice order; Step D
-// (interpolation of increments, new initial values, node-0 F) is batched.
+// over a group of consecutive slices; Step C (coarse sweeps) is a chain in
+// slice order; Step D (interpolation of increments, new initial values,
+// node-0 F) is batched over a group again.
+//
+// Within one iteration Step C of group g depends only on Steps A/B of group
+// g and on Step C of group g-1, so the chain runs on a second stream and
+// overlaps Steps A/B of the later groups; Step D of group g waits for Step C
+// of group g.  The arithmetic of every slice is the same for any grouping
+// as long as each group holds at least kMinGroupSlices slices (the RHS path
+// for batches of one or two states differs from the batched one).
 #include <math.h>
 
 #include <stdlib.h>
@@ -16,6 +24,8 @@
 #include "internal.cuh"
 
 namespace pfsh {
+
+constexpr int kMinGroupSlices = 4;
 
 struct Mat16 {
   double v[16][16];
@@ -132,11 +142,12 @@ __global__ void k_pred_interp(int Tf, int Tc, int nts, int nf, int ncn, Mat16 Pt
 }
 
 // Step D, last line of Algorithm 1: theta_f^{n,0} = sent^{n-1} +
-// Z(theta_c^{n,0} - D sent^{n-1}) for slices n >= 1.
-__global__ void k_node0(int Tf, int Tc, int nts, const double2 *__restrict__ sent, const double2 *__restrict__ thc0,
-                        double2 *__restrict__ thf0) {
+// Z(theta_c^{n,0} - D sent^{n-1}) for slices n >= 1; slice b = first +
+// blockIdx.y relative to the base pointers (sent[b-1] must exist).
+__global__ void k_node0(int Tf, int Tc, int first, const double2 *__restrict__ sent,
+                        const double2 *__restrict__ thc0, double2 *__restrict__ thf0) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int b = blockIdx.y + 1;
+  int b = blockIdx.y + first;
   const int ncc = ncoef_of(Tc), ncf = ncoef_of(Tf);
   if (idx >= ncf) return;
   const int m = tri_m2(idx, Tf);
@@ -164,6 +175,15 @@ static void pf_free(pfasst *pf) {
   for (int i = 0; i < 2; ++i)
     if (pf->gexec[i]) cudaGraphExecDestroy(pf->gexec[i]);
   if (pf->cap_stream) cudaStreamDestroy(pf->cap_stream);
+  if (pf->chain_stream) cudaStreamDestroy(pf->chain_stream);
+  if (pf->ev_fork) cudaEventDestroy(pf->ev_fork);
+  for (int g = 0; g < pfasst::kMaxGroups; ++g) {
+    if (pf->ev_B[g]) cudaEventDestroy(pf->ev_B[g]);
+    if (pf->ev_C[g]) cudaEventDestroy(pf->ev_C[g]);
+  }
+  sdc_level_destroy(pf->lev_cc);
+  swe_ctx_destroy(pf->ctx_cc);
+  sht_plan_destroy(pf->plan_cc);
   sdc_level_destroy(pf->lev_f);
   sdc_level_destroy(pf->lev_c);
   swe_ctx_destroy(pf->ctx_f);
@@ -180,6 +200,7 @@ extern "C" int pfasst_create(pfasst **out, const pfasst_config *cfg) {
   if (c.n_ts < 1 || c.fine_nodes < 2 || c.fine_nodes > 9 || c.coarse_nodes < 2 || c.coarse_nodes > 9)
     return fail(PFSH_EINVAL, "pfasst_create: need n_ts >= 1 and 2..9 nodes per level");
   if (c.Tc > c.Tf || c.Tc < 1) return fail(PFSH_EINVAL, "pfasst_create: need 1 <= Tc <= Tf");
+  if (c.slice_groups < 0) return fail(PFSH_EINVAL, "pfasst_create: slice_groups must be >= 0");
   if (!(c.dt > 0)) return fail(PFSH_EINVAL, "pfasst_create: dt must be > 0");
   pfasst *pf = new (std::nothrow) pfasst();
   if (!pf) return fail(PFSH_ENOMEM, "pfasst_create");
@@ -196,7 +217,10 @@ extern "C" int pfasst_create(pfasst **out, const pfasst_config *cfg) {
       (rc = swe_ctx_create(&pf->ctx_f, pf->plan_f, &c.phys)) ||
       (rc = swe_ctx_create(&pf->ctx_c, pf->plan_c, &c.phys)) ||
       (rc = sdc_level_create(&pf->lev_f, pf->ctx_f, c.fine_nodes, c.dt, nts)) ||
-      (rc = sdc_level_create(&pf->lev_c, pf->ctx_c, c.coarse_nodes, c.dt, nts))) {
+      (rc = sdc_level_create(&pf->lev_c, pf->ctx_c, c.coarse_nodes, c.dt, nts)) ||
+      (rc = sht_plan_create(&pf->plan_cc, c.Tc, c.nlat_c, c.nlon_c, 5, c.prec)) ||
+      (rc = swe_ctx_create(&pf->ctx_cc, pf->plan_cc, &c.phys)) ||
+      (rc = sdc_level_create(&pf->lev_cc, pf->ctx_cc, c.coarse_nodes, c.dt, 1))) {
     pf_free(pf);
     return rc;
   }
@@ -220,14 +244,28 @@ extern "C" int pfasst_create(pfasst **out, const pfasst_config *cfg) {
     }
     cudaMemset(*a.p, 0, a.n * sizeof(double));
   }
-  if (cudaStreamCreateWithFlags(&pf->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+  int prio_lo = 0, prio_hi = 0;
+  cudaDeviceGetStreamPriorityRange(&prio_lo, &prio_hi);
+  bool ok = cudaStreamCreateWithFlags(&pf->cap_stream, cudaStreamNonBlocking) == cudaSuccess &&
+            cudaStreamCreateWithPriority(&pf->chain_stream, cudaStreamNonBlocking, prio_hi) == cudaSuccess &&
+            cudaEventCreateWithFlags(&pf->ev_fork, cudaEventDisableTiming) == cudaSuccess;
+  for (int g = 0; ok && g < pfasst::kMaxGroups; ++g)
+    ok = cudaEventCreateWithFlags(&pf->ev_B[g], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&pf->ev_C[g], cudaEventDisableTiming) == cudaSuccess;
+  if (!ok) {
     cudaGetLastError();
     pf_free(pf);
-    return fail(PFSH_ECUDA, "pfasst_create: capture stream");
+    return fail(PFSH_ECUDA, "pfasst_create: streams/events");
   }
   {
     const char *e = getenv("PFSH_NO_GRAPH");
     pf->graphs = !(e && e[0] && e[0] != '0');
+    // slice groups, each of >= kMinGroupSlices slices; by default 2 for the
+    // mixed forms (their fine sweeps leave room for the chain), 1 for FP64
+    // (its FP64-bound fine sweeps lose more from smaller batches than the
+    // overlap gains)
+    const int g = c.slice_groups > 0 ? c.slice_groups : (c.prec == PFSH_FP64 ? 1 : 2);
+    pf->groups = std::max(1, std::min(g, std::min(pfasst::kMaxGroups, nts / kMinGroupSlices)));
   }
   lagrange_matrix(pf->lev_f->tau_nodes, c.fine_nodes, pf->lev_c->tau_nodes, c.coarse_nodes, pf->Rt);
   lagrange_matrix(pf->lev_c->tau_nodes, c.coarse_nodes, pf->lev_f->tau_nodes, c.fine_nodes, pf->Pt);
@@ -246,15 +284,6 @@ extern "C" int pfasst_set_initial(pfasst *pf, const double *theta0, pfsh_stream_
   if (!pf || !theta0) return fail(PFSH_EINVAL, "pfasst_set_initial: NULL argument");
   PFSH_CUDA(cudaMemcpyAsync(pf->theta0, theta0, pf->sf * 8, cudaMemcpyDeviceToDevice, (cudaStream_t)stream));
   return PFSH_OK;
-}
-
-static int restrict_all(pfasst *pf, const double *xf, double *xc, cudaStream_t s) {
-  const int nts = pf->cfg.n_ts;
-  double R[16 * 16];
-  for (int i = 0; i < 16; ++i)
-    for (int k = 0; k < 16; ++k) R[i * 16 + k] = pf->Rt[i][k];
-  return restrict_launch(R, pf->Mf + 1, pf->Mc + 1, xf, (size_t)nts * pf->sf, xc, (size_t)nts * pf->sc,
-                         pf->cfg.Tf, pf->cfg.Tc, nts, s);
 }
 
 extern "C" int pfasst_predict(pfasst *pf, pfsh_stream_t stream) {
@@ -308,91 +337,137 @@ extern "C" int pfasst_predict(pfasst *pf, pfsh_stream_t stream) {
   return rhs_eval(pf->ctx_f, pf->th_f, pf->fe_f, pf->fi_f, (Mf + 1) * nts, s);
 }
 
-static int iteration_body(pfasst *pf, int last, cudaStream_t s) {
+// Steps A and B for slices [g0, g0 + cnt): fine sweep, send, restriction,
+// coarse F at every node, saved copies, FAS correction.
+static int steps_AB(pfasst *pf, int g0, int cnt, cudaStream_t s) {
   const pfasst_config &c = pf->cfg;
   const int nts = c.n_ts, Mc = pf->Mc, Mf = pf->Mf;
   const size_t sc = pf->sc, sf = pf->sf;
   const size_t cnode = (size_t)nts * sc, fnode = (size_t)nts * sf;
   int rc;
-  // A) fine sweep of every slice
-  if ((rc = sdc_sweep_strided(pf->lev_f, pf->th_f, pf->fe_f, pf->fi_f, nullptr, fnode, nts, s))) return rc;
-  if (last) return PFSH_OK;
-  PFSH_CUDA(cudaMemcpyAsync(pf->sent, pf->th_f + Mf * fnode, fnode * 8, cudaMemcpyDeviceToDevice, s));
-  // B) restrict, coarse F at every node, save, FAS
-  if ((rc = restrict_all(pf, pf->th_f, pf->th_c, s))) return rc;
-  if ((rc = rhs_eval(pf->ctx_c, pf->th_c, pf->fe_c, pf->fi_c, (Mc + 1) * nts, s))) return rc;
-  const size_t cbytes = (size_t)(Mc + 1) * cnode * 8;
-  PFSH_CUDA(cudaMemcpyAsync(pf->th_cs, pf->th_c, cbytes, cudaMemcpyDeviceToDevice, s));
-  PFSH_CUDA(cudaMemcpyAsync(pf->fe_cs, pf->fe_c, cbytes, cudaMemcpyDeviceToDevice, s));
-  PFSH_CUDA(cudaMemcpyAsync(pf->fi_cs, pf->fi_c, cbytes, cudaMemcpyDeviceToDevice, s));
+  if ((rc = sdc_sweep_strided(pf->lev_f, pf->th_f + g0 * sf, pf->fe_f + g0 * sf, pf->fi_f + g0 * sf, nullptr, fnode,
+                              cnt, s)))
+    return rc;
+  PFSH_CUDA(cudaMemcpyAsync(pf->sent + g0 * sf, pf->th_f + Mf * fnode + g0 * sf, cnt * sf * 8,
+                            cudaMemcpyDeviceToDevice, s));
   {
-    Mat16 RQf, Qc;
+    double R[16 * 16];
     for (int i = 0; i < 16; ++i)
-      for (int k = 0; k < 16; ++k) {
-        RQf.v[i][k] = 0.0;
-        Qc.v[i][k] = 0.0;
-      }
-    for (int i = 0; i <= Mc; ++i) {
-      for (int k = 0; k <= Mf; ++k) {
-        double acc = 0.0;
-        for (int q = 0; q <= Mf; ++q) acc += pf->Rt[i][q] * pf->lev_f->Q[q][k];
-        RQf.v[i][k] = acc;
-      }
-      for (int k = 0; k <= Mc; ++k) Qc.v[i][k] = pf->lev_c->Q[i][k];
-    }
-    dim3 g((ncoef_of(c.Tc) + 255) / 256, nts);
-    {
-      PFSH_LAUNCH("k_fas", s);
-      k_fas<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, c.dt, RQf, Qc, (const double2 *)pf->fe_f,
-                              (const double2 *)pf->fi_f, (const double2 *)pf->fe_c, (const double2 *)pf->fi_c,
-                              (double2 *)pf->tau);
-    }
-    PFSH_CHECK_LAUNCH("k_fas");
-  }
-  // C) coarse chain in slice order
-  for (int n = 0; n < nts; ++n) {
-    if (n > 0) {
-      PFSH_CUDA(cudaMemcpyAsync(pf->th_c + n * sc, pf->th_c + Mc * cnode + (n - 1) * sc, sc * 8,
-                                cudaMemcpyDeviceToDevice, s));
-      if ((rc = rhs_eval(pf->ctx_c, pf->th_c + n * sc, pf->fe_c + n * sc, pf->fi_c + n * sc, 1, s))) return rc;
-    }
-    if ((rc = sdc_sweep_strided(pf->lev_c, pf->th_c + n * sc, pf->fe_c + n * sc, pf->fi_c + n * sc,
-                                pf->tau + n * sc, cnode, 1, s)))
+      for (int k = 0; k < 16; ++k) R[i * 16 + k] = pf->Rt[i][k];
+    if ((rc = restrict_launch(R, Mf + 1, Mc + 1, pf->th_f + g0 * sf, fnode, pf->th_c + g0 * sc, cnode, c.Tf, c.Tc,
+                              cnt, s)))
       return rc;
   }
-  // D) interpolate increments (nodes >= 1), new initial values, node-0 F
-  {
-    Mat16 P;
-    for (int i = 0; i < 16; ++i)
-      for (int k = 0; k < 16; ++k) P.v[i][k] = pf->Pt[i][k];
-    dim3 g((ncoef_of(c.Tc) + 255) / 256, nts);
-    const double *xc[3] = {pf->th_c, pf->fe_c, pf->fi_c};
-    const double *xs[3] = {pf->th_cs, pf->fe_cs, pf->fi_cs};
-    double *xf[3] = {pf->th_f, pf->fe_f, pf->fi_f};
-    for (int q = 0; q < 3; ++q) {
-      {
-        PFSH_LAUNCH("k_interp_inc", s);
-        k_interp_inc<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, 1, P, (const double2 *)xc[q],
-                                       (const double2 *)xs[q], (double2 *)xf[q]);
-      }
-      PFSH_CHECK_LAUNCH("k_interp_inc");
-    }
-    if (nts > 1) {
-      dim3 g0((ncoef_of(c.Tf) + 255) / 256, nts - 1);
-      {
-        PFSH_LAUNCH("k_node0", s);
-        k_node0<<<g0, 256, 0, s>>>(c.Tf, c.Tc, nts, (const double2 *)pf->sent, (const double2 *)pf->th_c,
-                                   (double2 *)pf->th_f);
-      }
-      PFSH_CHECK_LAUNCH("k_node0");
-    }
+  for (int i = 0; i <= Mc; ++i) {
+    const size_t o = i * cnode + g0 * sc;
+    if ((rc = rhs_eval(pf->ctx_c, pf->th_c + o, pf->fe_c + o, pf->fi_c + o, cnt, s))) return rc;
   }
-  return rhs_eval(pf->ctx_f, pf->th_f, pf->fe_f, pf->fi_f, nts, s);
+  const double *src[3] = {pf->th_c, pf->fe_c, pf->fi_c};
+  double *dst[3] = {pf->th_cs, pf->fe_cs, pf->fi_cs};
+  for (int q = 0; q < 3; ++q)
+    PFSH_CUDA(cudaMemcpy2DAsync(dst[q] + g0 * sc, cnode * 8, src[q] + g0 * sc, cnode * 8, cnt * sc * 8, Mc + 1,
+                                cudaMemcpyDeviceToDevice, s));
+  Mat16 RQf, Qc;
+  for (int i = 0; i < 16; ++i)
+    for (int k = 0; k < 16; ++k) {
+      RQf.v[i][k] = 0.0;
+      Qc.v[i][k] = 0.0;
+    }
+  for (int i = 0; i <= Mc; ++i) {
+    for (int k = 0; k <= Mf; ++k) {
+      double acc = 0.0;
+      for (int q = 0; q <= Mf; ++q) acc += pf->Rt[i][q] * pf->lev_f->Q[q][k];
+      RQf.v[i][k] = acc;
+    }
+    for (int k = 0; k <= Mc; ++k) Qc.v[i][k] = pf->lev_c->Q[i][k];
+  }
+  dim3 g((ncoef_of(c.Tc) + 255) / 256, cnt);
+  {
+    PFSH_LAUNCH("k_fas", s);
+    k_fas<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, c.dt, RQf, Qc, (const double2 *)(pf->fe_f + g0 * sf),
+                            (const double2 *)(pf->fi_f + g0 * sf), (const double2 *)(pf->fe_c + g0 * sc),
+                            (const double2 *)(pf->fi_c + g0 * sc), (double2 *)(pf->tau + g0 * sc));
+  }
+  PFSH_CHECK_LAUNCH("k_fas");
+  return PFSH_OK;
 }
 
-// The iteration is a fixed sequence of ~600 launches on fixed buffers, so it
-// is recorded once into a CUDA graph (on a private capture stream) and
-// replayed on the caller's stream; the first call of each kind runs eagerly,
+// Step C for slices [g0, g0 + cnt) in slice order: receive slice n-1's coarse
+// end value (with its right-hand sides), one coarse sweep with the FAS term.
+static int step_C(pfasst *pf, int g0, int cnt, cudaStream_t s) {
+  const size_t sc = pf->sc, cnode = (size_t)pf->cfg.n_ts * sc;
+  return chain_sweeps(pf->lev_cc, pf->th_c, pf->fe_c, pf->fi_c, pf->tau, cnode, sc, g0, g0 + cnt, g0 > 0, s);
+}
+
+// Step D for slices [g0, g0 + cnt): interpolate the coarse increments into
+// fine nodes >= 1, new fine initial values (slices >= 1), fine node-0 F.
+static int step_D(pfasst *pf, int g0, int cnt, cudaStream_t s) {
+  const pfasst_config &c = pf->cfg;
+  const int nts = c.n_ts, Mc = pf->Mc, Mf = pf->Mf;
+  const size_t sc = pf->sc, sf = pf->sf;
+  Mat16 P;
+  for (int i = 0; i < 16; ++i)
+    for (int k = 0; k < 16; ++k) P.v[i][k] = pf->Pt[i][k];
+  dim3 g((ncoef_of(c.Tc) + 255) / 256, cnt);
+  const double *xc[3] = {pf->th_c, pf->fe_c, pf->fi_c};
+  const double *xs[3] = {pf->th_cs, pf->fe_cs, pf->fi_cs};
+  double *xf[3] = {pf->th_f, pf->fe_f, pf->fi_f};
+  for (int q = 0; q < 3; ++q) {
+    {
+      PFSH_LAUNCH("k_interp_inc", s);
+      k_interp_inc<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, 1, P, (const double2 *)(xc[q] + g0 * sc),
+                                     (const double2 *)(xs[q] + g0 * sc), (double2 *)(xf[q] + g0 * sf));
+    }
+    PFSH_CHECK_LAUNCH("k_interp_inc");
+  }
+  const int first = g0 == 0 ? 1 : 0;
+  if (cnt - first > 0) {
+    dim3 g0d((ncoef_of(c.Tf) + 255) / 256, cnt - first);
+    {
+      PFSH_LAUNCH("k_node0", s);
+      k_node0<<<g0d, 256, 0, s>>>(c.Tf, c.Tc, first, (const double2 *)(pf->sent + g0 * sf),
+                                  (const double2 *)(pf->th_c + g0 * sc), (double2 *)(pf->th_f + g0 * sf));
+    }
+    PFSH_CHECK_LAUNCH("k_node0");
+  }
+  return rhs_eval(pf->ctx_f, pf->th_f + g0 * sf, pf->fe_f + g0 * sf, pf->fi_f + g0 * sf, cnt, s);
+}
+
+static int iteration_body(pfasst *pf, int last, cudaStream_t s) {
+  const int nts = pf->cfg.n_ts;
+  if (last)   // the last iteration ends after the fine sweep (Step A)
+    return sdc_sweep_strided(pf->lev_f, pf->th_f, pf->fe_f, pf->fi_f, nullptr, (size_t)nts * pf->sf, nts, s);
+  const int G = pf->groups;
+  auto group = [&](int g, int *g0, int *cnt) {
+    *g0 = (int)((long)nts * g / G);
+    *cnt = (int)((long)nts * (g + 1) / G) - *g0;
+  };
+  // with the event profiler on, everything runs on `s` so that per-launch
+  // durations are not stretched by the overlap
+  cudaStream_t cs = profiler_on() ? s : pf->chain_stream;
+  PFSH_CUDA(cudaEventRecord(pf->ev_fork, s));
+  PFSH_CUDA(cudaStreamWaitEvent(cs, pf->ev_fork, 0));
+  int rc, g0, cnt;
+  for (int g = 0; g < G; ++g) {
+    group(g, &g0, &cnt);
+    if ((rc = steps_AB(pf, g0, cnt, s))) return rc;
+    PFSH_CUDA(cudaEventRecord(pf->ev_B[g], s));
+    PFSH_CUDA(cudaStreamWaitEvent(cs, pf->ev_B[g], 0));
+    if ((rc = step_C(pf, g0, cnt, cs))) return rc;
+    PFSH_CUDA(cudaEventRecord(pf->ev_C[g], cs));
+  }
+  for (int g = 0; g < G; ++g) {
+    group(g, &g0, &cnt);
+    PFSH_CUDA(cudaStreamWaitEvent(s, pf->ev_C[g], 0));
+    if ((rc = step_D(pf, g0, cnt, s))) return rc;
+  }
+  return PFSH_OK;
+}
+
+// The iteration is a fixed sequence of several hundred launches on fixed
+// buffers over two streams, so it is recorded once into a CUDA graph (on a
+// private capture stream, joined by the chain stream) and replayed on the
+// caller's stream; the first call of each kind runs eagerly,
 // which also sets every kernel attribute before capture.  Profiling or
 // PFSH_NO_GRAPH=1 keeps the eager path.
 extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
@@ -417,7 +492,7 @@ extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
     return rc;
   }
   if (e != cudaSuccess) return cuda_fail(e, "pfasst_iteration: cudaStreamEndCapture");
-  e = cudaGraphInstantiate(&pf->gexec[k], g, 0);
+  e = cudaGraphInstantiateWithFlags(&pf->gexec[k], g, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(g);
   if (e != cudaSuccess) {
     pf->gexec[k] = nullptr;

@@ -1,188 +1,96 @@
-// RHS evaluation for one or two states (the serial coarse chain of PFASST
-// runs one time slice per call): three launches instead of five.
+// One or two states per call.
 //
-//   k_small_synth  per order m: the coefficient rows of eta, Phi', U, V
-//                  (velocity recovery of Section 2) are computed once into
-//                  shared memory, then every northern latitude accumulates
-//                  the even and odd Legendre sums (K split across thread
-//                  groups to shorten the dependent chain) -> F(+-mu).
-//   k_grid_rhs     unchanged (fft.cu).
-//   k_small_anal   per order m: one warp per degree contracts the
-//                  hemispheric sums over latitude into shared memory, then
-//                  the div/curl stencil assembles F_E and F_I for that order.
+// 1. RHS evaluation (swe_rhs and the sweeps with B <= 2): three launches
+//    instead of five.
+//      k_small_synth  per order m: coefficient rows of eta, Phi', U, V
+//                     (velocity recovery of Section 2) in shared memory,
+//                     then even/odd Legendre sums at every northern latitude
+//                     -> F(+-mu).
+//      k_grid_rhs     FFT / grid products / FFT per latitude pair (fft.cu).
+//      k_small_anal   per order m: hemispheric sums contracted over latitude,
+//                     then the div/curl stencil assembles F_E and F_I.
 //
-// The arithmetic is that of k_rhs_prep / legendre_* / k_rhs_assemble, in the
-// plan's real type for the contractions (fp64 for FP64 plans, fp32 otherwise)
-// and fp64 for the spectral parts.
+// 2. Step C of Algorithm 1 (the serial coarse chain), one slice after the
+//    other.  Everything between two grid stages touches only coefficients of
+//    one order m -- the analysis and assembly of node i, the node update and
+//    implicit solve of node i+1 (Section 5.1.1), the velocity recovery and
+//    synthesis of node i+1 -- so one launch per order does all of it and
+//    stages the order's Legendre rows once for both transforms:
+//      k_chain_node   [analysis of the previous node] [receive] [old part]
+//                     [update + solve of node k] [synthesis of node k]
+//    A slice's sweep is then k_chain_node / k_grid_rhs pairs, one per node.
+//    The right-hand side of the received value (node 0 of slice n) is the
+//    right-hand side the sender evaluated at its last node: the same state
+//    through the same kernels, so it is copied with the state instead of
+//    being evaluated again.
+//
+// The arithmetic is that of the batched path's kernels, in the plan's real
+// type for the contractions (fp64 for FP64 plans, fp32 otherwise) and fp64
+// for the spectral parts.
 #include "internal.cuh"
+#include "small_ops.cuh"
 #include "spectral_ops.cuh"
 
 namespace pfsh {
 
 constexpr int kSmallMaxStates = 2;
+constexpr int kSynthThreads = 256, kAnalThreads = 512, kChainThreads = 512;
+constexpr size_t kStageBudget = 100 * 1024;   // two blocks per SM
+constexpr size_t kChainBudget = 200 * 1024;   // one block per SM
 
 template <typename R, int NB>
-__global__ void __launch_bounds__(256) k_small_synth(int T, int nlat, int B, R ma2, R inva, double omega,
-                                                     double phibar, SpecTables<R> tb, const R *__restrict__ P,
-                                                     const double2 *__restrict__ state,
-                                                     typename cpx<R>::t *__restrict__ F) {
-  typedef typename cpx<R>::t C;
-  constexpr int NC = 4 * NB;
+__global__ void __launch_bounds__(kSynthThreads) k_small_synth(int T, int nlat, int B, int rows, R ma2, R inva,
+                                                               double omega, double phibar, SpecTables<R> tb,
+                                                               const R *__restrict__ P,
+                                                               const double2 *__restrict__ state,
+                                                               typename cpx<R>::t *__restrict__ F) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = blockIdx.x, nh = nlat / 2, K = T + 2 - m, cols = 4 * B;
-  const int parts = max(1, (int)blockDim.x / nh);
-  const int Kc = ((K + parts - 1) / parts + 1) & ~1;          // even chunk length
-  C *Xs = reinterpret_cast<C *>(smem_raw);                    // [K][cols]
-  C *Ps = Xs + (size_t)K * cols;                               // [parts][nh][2][cols]
-  const int nc = ncoef_of(T);
-  const int base = poff(T, m) - m;
-  const size_t e0 = (size_t)poff(T + 1, m);
-  // 1. coefficient rows for this order
-  for (int t = threadIdx.x; t < K * B; t += blockDim.x) {
-    const int i = t / B, b = t - i * B;
-    const double2 *Phi = state + (size_t)b * 3 * nc;
-    prep_point<R>(T, m, m + i, Phi, Phi + nc, Phi + 2 * nc, base, e0 + i, tb, ma2, inva, omega, phibar,
-                  Xs + (size_t)i * cols + b * 4);
-  }
-  __syncthreads();
-  // 2. even/odd Legendre sums per latitude and K chunk
-  const size_t row0 = (size_t)eoff(T, m);
-  for (int t = threadIdx.x; t < nh * parts; t += blockDim.x) {
-    const int j = t % nh, part = t / nh;
-    const int i0 = part * Kc, i1 = min(K, i0 + Kc);
-    C e[NC], o[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) e[c] = o[c] = mk<C>(0.0, 0.0);
-    for (int i = i0; i < i1; i += 2) {
-      const R pe = P[(row0 + i) * nh + j];
-      const R po = (i + 1 < i1) ? P[(row0 + i + 1) * nh + j] : (R)0;
-      const C *xe = Xs + (size_t)i * cols, *xo = xe + cols;
-#pragma unroll
-      for (int c = 0; c < NC; ++c)
-        if (c < cols) {
-          const C u = xe[c];
-          e[c].x += pe * u.x;
-          e[c].y += pe * u.y;
-          if (i + 1 < i1) {
-            const C v = xo[c];
-            o[c].x += po * v.x;
-            o[c].y += po * v.y;
-          }
-        }
-    }
-    C *ps = Ps + ((size_t)part * nh + j) * 2 * cols;
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (c < cols) {
-        ps[c] = e[c];
-        ps[cols + c] = o[c];
-      }
-  }
-  __syncthreads();
-  for (int t = threadIdx.x; t < nh * cols; t += blockDim.x) {
-    const int j = t / cols, c = t - j * cols;
-    C E = mk<C>(0.0, 0.0), O = mk<C>(0.0, 0.0);
-    for (int part = 0; part < parts; ++part) {
-      const C *ps = Ps + ((size_t)part * nh + j) * 2 * cols;
-      E = E + ps[c];
-      O = O + ps[cols + c];
-    }
-    F[((size_t)m * nlat + j) * cols + c] = E + O;
-    F[((size_t)m * nlat + (nlat - 1 - j)) * cols + c] = E - O;
-  }
+  R *Pst = reinterpret_cast<R *>(smem_raw);
+  small_synth_body<R, NB>(blockIdx.x, T, nlat, B, rows, Pst, false, ma2, inva, omega, phibar, tb, P, state, F,
+                          smem_raw + small_stage_bytes<R>(nlat, rows));
 }
 
 template <typename R, int NB>
-__global__ void __launch_bounds__(512) k_small_anal(int T, int nlat, int B, R inva, R inva2, double dinva2, double nu,
-                                                    double phibar, const R *__restrict__ eps,
-                                                    const R *__restrict__ P, const typename cpx<R>::t *__restrict__ H,
-                                                    const double2 *__restrict__ state, double2 *__restrict__ fE,
-                                                    double2 *__restrict__ fI) {
-  typedef typename cpx<R>::t C;
-  constexpr int NC = 5 * NB;
+__global__ void __launch_bounds__(kAnalThreads) k_small_anal(int T, int nlat, int B, int rows, R inva, R inva2,
+                                                             double dinva2, double nu, double phibar,
+                                                             const R *__restrict__ eps, const R *__restrict__ P,
+                                                             const typename cpx<R>::t *__restrict__ H,
+                                                             const double2 *__restrict__ state,
+                                                             double2 *__restrict__ fE, double2 *__restrict__ fI) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = blockIdx.x, nh = nlat / 2, K = T + 2 - m, cols = 5 * B;
-  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nwarps = blockDim.x >> 5;
-  C *Ys = reinterpret_cast<C *>(smem_raw);     // [K][cols]
-  const size_t row0 = (size_t)eoff(T, m);
-  // 1. analysis of every degree of this order
-  for (int i = warp; i < K; i += nwarps) {
-    const int p = i & 1;
-    const C *h = H + ((size_t)m * 2 + p) * nh * cols;
-    C acc[NC];
-#pragma unroll
-    for (int c = 0; c < NC; ++c) acc[c] = mk<C>(0.0, 0.0);
-    for (int j = lane; j < nh; j += 32) {
-      const R pv = P[(row0 + i) * nh + j];
-#pragma unroll
-      for (int c = 0; c < NC; ++c)
-        if (c < cols) {
-          const C v = h[(size_t)j * cols + c];
-          acc[c].x += pv * v.x;
-          acc[c].y += pv * v.y;
-        }
-    }
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-#pragma unroll
-      for (int d = 16; d > 0; d >>= 1) {
-        acc[c].x += __shfl_xor_sync(0xffffffffu, acc[c].x, d);
-        acc[c].y += __shfl_xor_sync(0xffffffffu, acc[c].y, d);
-      }
-#pragma unroll
-    for (int c = 0; c < NC; ++c)
-      if (lane == c && c < cols) Ys[(size_t)i * cols + c] = acc[c];
-  }
-  __syncthreads();
-  // 2. assembly of F_E and F_I for n = m..T
-  const int nc = ncoef_of(T);
-  const size_t e0 = (size_t)poff(T + 1, m);
-  const int pidx0 = poff(T, m);
-  for (int t = threadIdx.x; t < (T + 1 - m) * B; t += blockDim.x) {
-    const int i = t / B, b = t - i * B, n = m + i;
-    C cur[5], up[5], dn[5];
-#pragma unroll
-    for (int f = 0; f < 5; ++f) {
-      cur[f] = Ys[(size_t)i * cols + b * 5 + f];
-      up[f] = Ys[(size_t)(i + 1) * cols + b * 5 + f];
-      dn[f] = i ? Ys[(size_t)(i - 1) * cols + b * 5 + f] : mk<C>(0.0, 0.0);
-    }
-    double2 fe[3];
-    assemble_point<R, C>(m, n, cur, up, dn, i > 0, eps[e0 + i + 1], eps[e0 + i], inva, inva2, fe);
-    const size_t idx = (size_t)pidx0 + i;
-    double2 *oE = fE + (size_t)b * 3 * nc;
-    oE[idx] = fe[0];
-    oE[nc + idx] = fe[1];
-    oE[2 * nc + idx] = fe[2];
-    if (fI) linear_point(m, n, state + (size_t)b * 3 * nc, nc, idx, dinva2, nu, phibar, fI + (size_t)b * 3 * nc);
-  }
+  R *Pst = reinterpret_cast<R *>(smem_raw);
+  small_anal_body<R, NB>(blockIdx.x, T, nlat, B, rows, Pst, inva, inva2, dinva2, nu, phibar, eps, P, H, state, fE,
+                         fI, smem_raw + small_stage_bytes<R>(nlat, rows));
 }
 
 template <typename R, int NB>
 static int small_launch(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
                         const R *P, SpecTables<R> tb, cudaStream_t s) {
   typedef typename cpx<R>::t C;
-  const int nh = p->nh, K = p->T + 2;
-  const int parts = std::max(1, 256 / nh);
-  const size_t sm1 = ((size_t)K * 4 * B + (size_t)parts * nh * 2 * 4 * B) * sizeof(C);
+  const int T = p->T, nlat = p->nlat;
+  const size_t w1 = small_synth_work<R>(T, nlat, B, kSynthThreads);
+  const int r1 = small_stage_rows<R>(w1, T, nlat, kStageBudget);
+  const size_t sm1 = w1 + small_stage_bytes<R>(nlat, r1);
   int rc = ensure_smem((const void *)k_small_synth<R, NB>, sm1);
   if (rc) return rc;
   {
     PFSH_LAUNCH("k_small_synth", s);
-    k_small_synth<R, NB><<<p->T + 1, 256, sm1, s>>>(p->T, p->nlat, B, (R)(-prm.a * prm.a), (R)(1.0 / prm.a),
-                                                    prm.omega, prm.phibar, tb, P, (const double2 *)state,
-                                                    (C *)p->F);
+    k_small_synth<R, NB><<<T + 1, kSynthThreads, sm1, s>>>(T, nlat, B, r1, (R)(-prm.a * prm.a), (R)(1.0 / prm.a),
+                                                           prm.omega, prm.phibar, tb, P, (const double2 *)state,
+                                                           (C *)p->F);
   }
   PFSH_CHECK_LAUNCH("k_small_synth");
   if ((rc = grid_rhs(p, B, prm, s))) return rc;
-  const size_t sm3 = (size_t)K * 5 * B * sizeof(C);
+  const size_t w3 = small_anal_work<R>(T, nlat, B, kAnalThreads);
+  const int r3 = small_stage_rows<R>(w3, T, nlat, kStageBudget);
+  const size_t sm3 = w3 + small_stage_bytes<R>(nlat, r3);
   if ((rc = ensure_smem((const void *)k_small_anal<R, NB>, sm3))) return rc;
   const double inva2 = 1.0 / (prm.a * prm.a);
   {
     PFSH_LAUNCH("k_small_anal", s);
-    k_small_anal<R, NB><<<p->T + 1, 512, sm3, s>>>(p->T, p->nlat, B, (R)(1.0 / prm.a), (R)inva2, inva2, prm.nu,
-                                                   prm.phibar, tb.eps, P, (const C *)p->H, (const double2 *)state,
-                                                   (double2 *)fE, (double2 *)fI);
+    k_small_anal<R, NB><<<T + 1, kAnalThreads, sm3, s>>>(T, nlat, B, r3, (R)(1.0 / prm.a), (R)inva2, inva2,
+                                                         prm.nu, prm.phibar, tb.eps, P, (const C *)p->H,
+                                                         (const double2 *)state, (double2 *)fE, (double2 *)fI);
   }
   PFSH_CHECK_LAUNCH("k_small_anal");
   return PFSH_OK;
@@ -199,6 +107,163 @@ int rhs_small(const sht_plan *p, const double *state, double *fE, double *fI, in
                   : small_launch<double, 2>(p, state, fE, fI, B, prm, p->d_P, t64, s);
   return B == 1 ? small_launch<float, 1>(p, state, fE, fI, B, prm, p->d_P32, t32, s)
                 : small_launch<float, 2>(p, state, fE, fI, B, prm, p->d_P32, t32, s);
+}
+
+// ---------------------------------------------------------------------------
+// fused single-slice sweep step (Step C)
+// ---------------------------------------------------------------------------
+struct ChainStep {
+  // analysis + assembly of one node: its state (for F_I) and outputs
+  const double2 *a_th;        // nullptr: no analysis in this launch
+  double2 *a_fe, *a_fi;
+  // receive: copy theta, F_E, F_I of (slice n-1, last node) to (slice n, node 0)
+  const double2 *r_th, *r_fe, *r_fi;   // nullptr: no receive
+  // sweep of one slice: node 0 at th/fe/fi, nodes ns complex apart
+  double2 *th, *fe, *fi;
+  const double2 *tau;         // FAS term of the slice (node 0), nullable
+  double2 *O;                 // [M][3 nc] old parts
+  size_t ns;
+  int k, M;                   // node to update (0: none) and last node
+  double hphibar;             // dt QI[k][k] Phibar
+  const double4_32a *fac;     // solve factors of node k [T+1]
+};
+
+template <typename R>
+struct ChainGeo {
+  int T, nlat, rows;
+  R ma2, inva, inva2;
+  double dinva2, omega, nu, phibar;
+  SpecTables<R> tb;
+  const R *P;
+  typename cpx<R>::t *F;
+  const typename cpx<R>::t *H;
+};
+
+template <typename R>
+__global__ void __launch_bounds__(kChainThreads) k_chain_node(ChainStep st, ChainGeo<R> g, SdcCoef c) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  const int m = blockIdx.x, T = g.T, nc = ncoef_of(T);
+  R *Pst = reinterpret_cast<R *>(smem_raw);
+  unsigned char *work = smem_raw + small_stage_bytes<R>(g.nlat, g.rows);
+  const bool anal = st.a_th != nullptr;
+  if (anal)
+    small_anal_body<R, 1>(m, T, g.nlat, 1, g.rows, Pst, g.inva, g.inva2, g.dinva2, g.nu, g.phibar, g.tb.eps, g.P,
+                          g.H, st.a_th, st.a_fe, st.a_fi, work);
+  if (st.k == 0) return;
+  const int p0 = poff(T, m), len = T + 1 - m;
+  if (st.r_th) {
+    for (int t = threadIdx.x; t < 3 * len; t += blockDim.x) {
+      const int fld = t / len;
+      const size_t e = (size_t)fld * nc + p0 + (t - fld * len);
+      st.th[e] = st.r_th[e];
+      st.fe[e] = st.r_fe[e];
+      st.fi[e] = st.r_fi[e];
+    }
+    __syncthreads();
+  }
+  if (st.k == 1) {
+    order_old_part<8>(m, T, st.M, st.ns, c, st.th, st.fe, st.fi, st.tau, st.O);
+    __syncthreads();
+  }
+  order_node_update(m, T, st.k, st.ns, c, st.hphibar, st.fac, st.O + (size_t)(st.k - 1) * 3 * nc, st.fe, st.fi,
+                    st.th);
+  __syncthreads();
+  const bool staged = anal && (T + 2 - m) <= g.rows;
+  small_synth_body<R, 1>(m, T, g.nlat, 1, g.rows, Pst, staged, g.ma2, g.inva, g.omega, g.phibar, g.tb, g.P,
+                         st.th + (size_t)st.k * st.ns, g.F, work);
+}
+
+template <typename R>
+static int chain_node_launch(const ChainStep &st, ChainGeo<R> g, const SdcCoef &c, cudaStream_t s) {
+  const size_t work = std::max(small_synth_work<R>(g.T, g.nlat, 1, kChainThreads),
+                               small_anal_work<R>(g.T, g.nlat, 1, kChainThreads));
+  g.rows = small_stage_rows<R>(work, g.T, g.nlat, kChainBudget);
+  const size_t smem = work + small_stage_bytes<R>(g.nlat, g.rows);
+  int rc = ensure_smem((const void *)k_chain_node<R>, smem);
+  if (rc) return rc;
+  {
+    PFSH_LAUNCH("k_chain_node", s);
+    k_chain_node<R><<<g.T + 1, kChainThreads, smem, s>>>(st, g, c);
+  }
+  PFSH_CHECK_LAUNCH("k_chain_node");
+  return PFSH_OK;
+}
+
+template <typename R>
+static ChainGeo<R> chain_geo(const sht_plan *p, const swe_params &prm, const R *P, SpecTables<R> tb) {
+  typedef typename cpx<R>::t C;
+  const double inva2 = 1.0 / (prm.a * prm.a);
+  return ChainGeo<R>{p->T, p->nlat, 0, (R)(-prm.a * prm.a), (R)(1.0 / prm.a), (R)inva2, inva2, prm.omega, prm.nu,
+                     prm.phibar, tb, P, (C *)p->F, (const C *)p->H};
+}
+
+template <typename R>
+static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, double *fi, const double *tau,
+                       size_t node_stride, size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s) {
+  const swe_ctx *ctx = l->ctx;
+  const sht_plan *p = ctx->plan;
+  const int M = l->nodes - 1;
+  const SdcCoef c = sdc_coef(l);
+  const size_t ns = node_stride / 2, ss = slice_stride / 2;
+  double2 *TH = (double2 *)th, *FE = (double2 *)fe, *FI = (double2 *)fi;
+  const double2 *TAU = (const double2 *)tau;
+  int rc;
+  for (int n = n0; n < n1; ++n) {
+    for (int k = 1; k <= M; ++k) {
+      ChainStep st = {};
+      st.th = TH + n * ss;
+      st.fe = FE + n * ss;
+      st.fi = FI + n * ss;
+      st.tau = TAU ? TAU + n * ss : nullptr;
+      st.O = (double2 *)l->d_old;
+      st.ns = ns;
+      st.k = k;
+      st.M = M;
+      st.hphibar = c.h[k] * ctx->prm.phibar;
+      st.fac = (const double4_32a *)l->d_fac + (size_t)k * (p->T + 1);
+      const bool recv = k == 1 && (n > n0 || recv_first);
+      if (k > 1) {                                   // analysis of node k-1 of this slice
+        st.a_th = st.th + (k - 1) * ns;
+        st.a_fe = st.fe + (k - 1) * ns;
+        st.a_fi = st.fi + (k - 1) * ns;
+      } else if (n > n0) {                           // analysis of the sender's last node
+        st.a_th = TH + (n - 1) * ss + M * ns;
+        st.a_fe = FE + (n - 1) * ss + M * ns;
+        st.a_fi = FI + (n - 1) * ss + M * ns;
+      }
+      if (recv) {
+        st.r_th = TH + (n - 1) * ss + M * ns;
+        st.r_fe = FE + (n - 1) * ss + M * ns;
+        st.r_fi = FI + (n - 1) * ss + M * ns;
+      }
+      if ((rc = chain_node_launch<R>(st, g, c, s))) return rc;
+      if ((rc = grid_rhs(p, 1, ctx->prm, s))) return rc;
+    }
+  }
+  if (n1 > n0) {   // analysis of the last slice's last node
+    ChainStep st = {};
+    st.a_th = TH + (n1 - 1) * ss + M * ns;
+    st.a_fe = FE + (n1 - 1) * ss + M * ns;
+    st.a_fi = FI + (n1 - 1) * ss + M * ns;
+    if ((rc = chain_node_launch<R>(st, g, c, s))) return rc;
+  }
+  return PFSH_OK;
+}
+
+// Step C for slices n0..n1-1 of node-major arrays (node stride node_stride,
+// slice stride slice_stride, in doubles): slice n receives the last node of
+// slice n-1 (theta, F_E, F_I; for n = n0 only if recv_first) and performs one
+// sweep with its FAS term.  The level must hold one state (B = 1).
+int chain_sweeps(sdc_level *l, double *th, double *fe, double *fi, const double *tau, size_t node_stride,
+                 size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s) {
+  const sht_plan *p = l->ctx->plan;
+  if (l->nodes - 1 > 8) return fail(PFSH_EUNSUPPORTED, "chain_sweeps: more than 9 nodes");
+  const swe_params &prm = l->ctx->prm;
+  if (p->prec == PFSH_FP64)
+    return chain_typed<double>(l, chain_geo<double>(p, prm, p->d_P, SpecTables<double>{p->d_eps, p->d_ilap}), th,
+                               fe, fi, tau, node_stride, slice_stride, n0, n1, recv_first, s);
+  return chain_typed<float>(l, chain_geo<float>(p, prm, p->d_P32, SpecTables<float>{p->d_eps32, p->d_ilap32}), th,
+                            fe, fi, tau, node_stride, slice_stride, n0, n1, recv_first, s);
 }
 
 }  // namespace pfsh

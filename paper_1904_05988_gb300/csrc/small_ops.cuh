@@ -1,0 +1,352 @@
+// Block-level bodies for one or two states per call, one block per order m:
+// velocity recovery + Legendre synthesis, Legendre analysis + assembly of
+// F_E and F_I, and the IMEX-SDC node update restricted to the coefficients
+// of order m.  Used by the batch-1/2 RHS kernels and by the fused
+// single-slice sweep kernel of the PFASST coarse chain (small.cu).
+//
+// The Legendre rows P_n^m(mu_j), n = m..T+1, of the block's order are staged
+// in shared memory once per call with asynchronous copies, at a padded row
+// stride (nh + 1) so that lanes that index consecutive degrees hit distinct
+// banks (analysis) and lanes that index consecutive latitudes do as well
+// (synthesis).  When an order has more rows than the staging buffer holds,
+// the rows are processed in chunks.
+#pragma once
+
+#include "internal.cuh"
+#include "spectral_ops.cuh"
+
+namespace pfsh {
+
+// ---------------------------------------------------------------------------
+// asynchronous global -> shared staging (cp.async; every thread of the block
+// takes part; completion by stage_wait)
+// ---------------------------------------------------------------------------
+template <typename T>
+__device__ __forceinline__ void stage_async(T *dst, const T *src, int n) {
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  const size_t bytes = (size_t)n * sizeof(T);
+  if ((((uintptr_t)src | (uintptr_t)d | bytes) & 15) == 0) {
+    const char *s8 = reinterpret_cast<const char *>(src);
+    for (size_t t = threadIdx.x; t < bytes / 16; t += blockDim.x)
+      asm volatile("cp.async.cg.shared.global [%0], [%1], 16;" ::"r"(d + (uint32_t)(16 * t)), "l"(s8 + 16 * t)
+                   : "memory");
+  } else {
+    constexpr int E = (int)sizeof(T);
+    static_assert(E == 4 || E == 8 || E == 16, "element size");
+    for (int t = threadIdx.x; t < n; t += blockDim.x)
+      asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d + (uint32_t)(E * t)), "l"(src + t), "n"(E)
+                   : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+// rows [0, nrows) of nh values each -> dst at row stride nh + 1
+template <typename R>
+__device__ __forceinline__ void stage_rows_async(R *dst, const R *src, int nrows, int nh) {
+  constexpr int E = (int)sizeof(R);
+  const uint32_t d = (uint32_t)__cvta_generic_to_shared(dst);
+  for (int t = threadIdx.x; t < nrows * nh; t += blockDim.x) {
+    const int i = t / nh, j = t - i * nh;
+    asm volatile("cp.async.ca.shared.global [%0], [%1], %2;" ::"r"(d + (uint32_t)(E * (i * (nh + 1) + j))),
+                 "l"(src + t), "n"(E)
+                 : "memory");
+  }
+  asm volatile("cp.async.commit_group;" ::: "memory");
+}
+
+__device__ __forceinline__ void stage_wait() {
+  asm volatile("cp.async.wait_all;" ::: "memory");
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// shared-memory budgets (bytes); region sizes are rounded to 16 bytes
+// ---------------------------------------------------------------------------
+__host__ __device__ inline size_t align16(size_t b) { return (b + 15) & ~(size_t)15; }
+
+template <typename R>
+__host__ __device__ inline size_t small_stage_bytes(int nlat, int rows) {
+  return align16((size_t)rows * (nlat / 2 + 1) * sizeof(R));
+}
+template <typename R>
+__host__ __device__ inline size_t small_synth_work(int T, int nlat, int B, int threads) {
+  const int nh = nlat / 2, parts = (threads / nh) > 1 ? threads / nh : 1;
+  typedef typename cpx<R>::t C;
+  return align16((size_t)(T + 2) * 4 * B * sizeof(C)) + align16((size_t)parts * nh * 2 * 4 * B * sizeof(C));
+}
+template <typename R>
+__host__ __device__ inline size_t small_anal_work(int T, int nlat, int B, int threads) {
+  typedef typename cpx<R>::t C;
+  const int nh = nlat / 2;
+  return align16((size_t)(T + 2) * 5 * B * sizeof(C)) + align16((size_t)2 * nh * 5 * B * sizeof(C)) +
+         align16((size_t)threads * 5 * B * sizeof(C));
+}
+// Largest even row count <= T+2 whose staging fits in `budget` bytes besides
+// `fixed` (at least 2).
+template <typename R>
+__host__ inline int small_stage_rows(size_t fixed, int T, int nlat, size_t budget) {
+  const size_t row = (size_t)(nlat / 2 + 1) * sizeof(R);
+  long r = budget > fixed + 16 ? (long)((budget - fixed - 16) / row) : 0;
+  r = r > T + 2 ? T + 2 : r;
+  r &= ~1L;
+  return r < 2 ? 2 : (int)r;
+}
+
+// ---------------------------------------------------------------------------
+// velocity recovery + Legendre synthesis of order m for B <= NB states
+//   Pst:  staging buffer of `rows` rows; if `staged`, it already holds rows
+//         [0, K) of order m (K = T+2-m <= rows required)
+//   work: [K][4B] coefficient rows | [parts][nh][2][4B] partial sums
+// Called by every thread of a block.
+// ---------------------------------------------------------------------------
+template <typename R, int NB>
+__device__ __forceinline__ void small_synth_body(int m, int T, int nlat, int B, int rows, R *Pst, bool staged,
+                                                 R ma2, R inva, double omega, double phibar, SpecTables<R> tb,
+                                                 const R *__restrict__ P, const double2 *__restrict__ state,
+                                                 typename cpx<R>::t *__restrict__ F, void *work) {
+  typedef typename cpx<R>::t C;
+  constexpr int NC = 4 * NB;
+  const int nh = nlat / 2, K = T + 2 - m, cols = 4 * B, ld = nh + 1;
+  const int parts = max(1, (int)blockDim.x / nh);
+  C *Xs = reinterpret_cast<C *>(work);                                               // [K][cols]
+  C *Ps = reinterpret_cast<C *>(reinterpret_cast<char *>(work) +
+                                align16((size_t)(T + 2) * 4 * B * sizeof(C)));      // [parts][nh][2][cols]
+  const int nc = ncoef_of(T);
+  const int base = poff(T, m) - m;
+  const size_t e0 = (size_t)poff(T + 1, m);
+  const R *Pm = P + (size_t)eoff(T, m) * nh;
+  // 1. first chunk of Legendre rows in flight while the coefficient rows
+  //    (velocity recovery) are computed
+  if (!staged) stage_rows_async(Pst, Pm, min(K, rows), nh);
+  for (int t = threadIdx.x; t < K * B; t += blockDim.x) {
+    const int i = t / B, b = t - i * B;
+    const double2 *Phi = state + (size_t)b * 3 * nc;
+    prep_point<R>(T, m, m + i, Phi, Phi + nc, Phi + 2 * nc, base, e0 + i, tb, ma2, inva, omega, phibar,
+                  Xs + (size_t)i * cols + b * 4);
+  }
+  for (int t = threadIdx.x; t < parts * nh * 2 * cols; t += blockDim.x) Ps[t] = mk<C>(0.0, 0.0);
+  if (!staged) stage_wait();
+  else __syncthreads();
+  // 2. even/odd Legendre sums per latitude; each chunk is split among `parts`
+  //    thread groups, partial sums accumulate in Ps
+  for (int c0 = 0; c0 < K; c0 += rows) {
+    const int cl = min(rows, K - c0);
+    const int Kc = ((cl + parts - 1) / parts + 1) & ~1;        // even
+    for (int t = threadIdx.x; t < nh * parts; t += blockDim.x) {
+      const int j = t % nh, part = t / nh;
+      const int i0 = part * Kc, i1 = min(cl, i0 + Kc);
+      C e[NC], o[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) e[c] = o[c] = mk<C>(0.0, 0.0);
+      for (int i = i0; i < i1; i += 2) {
+        const R pe = Pst[(size_t)i * ld + j];
+        const bool odd = i + 1 < i1;
+        const R po = odd ? Pst[(size_t)(i + 1) * ld + j] : (R)0;
+        const C *xe = Xs + (size_t)(c0 + i) * cols, *xo = xe + cols;
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (c < cols) {
+            const C u = xe[c];
+            e[c].x += pe * u.x;
+            e[c].y += pe * u.y;
+            if (odd) {
+              const C v = xo[c];
+              o[c].x += po * v.x;
+              o[c].y += po * v.y;
+            }
+          }
+      }
+      C *ps = Ps + ((size_t)part * nh + j) * 2 * cols;
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (c < cols) {
+          ps[c] = ps[c] + e[c];
+          ps[cols + c] = ps[cols + c] + o[c];
+        }
+    }
+    if (c0 + rows < K) {
+      __syncthreads();
+      stage_rows_async(Pst, Pm + (size_t)(c0 + rows) * nh, min(rows, K - c0 - rows), nh);
+      stage_wait();
+    }
+  }
+  __syncthreads();
+  for (int t = threadIdx.x; t < nh * cols; t += blockDim.x) {
+    const int j = t / cols, c = t - j * cols;
+    C E = mk<C>(0.0, 0.0), O = mk<C>(0.0, 0.0);
+    for (int part = 0; part < parts; ++part) {
+      const C *ps = Ps + ((size_t)part * nh + j) * 2 * cols;
+      E = E + ps[c];
+      O = O + ps[cols + c];
+    }
+    F[((size_t)m * nlat + j) * cols + c] = E + O;
+    F[((size_t)m * nlat + (nlat - 1 - j)) * cols + c] = E - O;
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// Legendre analysis of order m + div/curl assembly of F_E and F_I for
+// n = m..T, B <= NB states.  Thread groups split the latitudes: thread
+// (s, i) sums latitudes [s nh/S, (s+1) nh/S) of degree row i; the S partial
+// sums are added in shared memory (no warp-wide butterfly).
+//   Pst:  staging buffer of `rows` rows; on return it holds the last chunk
+//         (all K rows when K <= rows), so a following synthesis of the same
+//         order may reuse it
+//   work: [K][5B] analysed rows | [2][nh][5B] hemispheric sums of order m |
+//         [threads][5B] partial sums
+// Called by every thread of a block.
+// ---------------------------------------------------------------------------
+template <typename R, int NB>
+__device__ __forceinline__ void small_anal_body(int m, int T, int nlat, int B, int rows, R *Pst, R inva, R inva2,
+                                                double dinva2, double nu, double phibar, const R *__restrict__ eps,
+                                                const R *__restrict__ P, const typename cpx<R>::t *__restrict__ H,
+                                                const double2 *__restrict__ state, double2 *__restrict__ fE,
+                                                double2 *__restrict__ fI, void *work) {
+  typedef typename cpx<R>::t C;
+  constexpr int NC = 5 * NB;
+  const int nh = nlat / 2, K = T + 2 - m, cols = 5 * B, ld = nh + 1;
+  char *w = reinterpret_cast<char *>(work);
+  C *Ys = reinterpret_cast<C *>(w);                                               // [K][cols]
+  w += align16((size_t)(T + 2) * 5 * B * sizeof(C));
+  C *Hs = reinterpret_cast<C *>(w);                                               // [2][nh][cols]
+  w += align16((size_t)2 * nh * 5 * B * sizeof(C));
+  C *Ws = reinterpret_cast<C *>(w);                                               // [threads][cols]
+  const R *Pm = P + (size_t)eoff(T, m) * nh;
+  stage_async(Hs, H + (size_t)m * 2 * nh * cols, 2 * nh * cols);
+  stage_rows_async(Pst, Pm, min(K, rows), nh);
+  stage_wait();
+  // 1. analysis of every degree row of this order
+  for (int c0 = 0; c0 < K; c0 += rows) {
+    const int cl = min(rows, K - c0);
+    const int kw = (cl + 31) & ~31;                                 // rows per latitude group (warp multiple)
+    const int S = max(1, min((int)blockDim.x / kw, nh));
+    const int t = threadIdx.x, s = t / kw, il = t - s * kw;
+    if (s < S && il < cl) {
+      const int i = c0 + il, p = i & 1;
+      const int j0 = (int)(((long)nh * s) / S), j1 = (int)(((long)nh * (s + 1)) / S);
+      const C *h = Hs + (size_t)p * nh * cols;
+      const R *pr = Pst + (size_t)il * ld;
+      C acc[NC];
+#pragma unroll
+      for (int c = 0; c < NC; ++c) acc[c] = mk<C>(0.0, 0.0);
+      for (int j = j0; j < j1; ++j) {
+        const R pv = pr[j];
+#pragma unroll
+        for (int c = 0; c < NC; ++c)
+          if (c < cols) {
+            const C v = h[(size_t)j * cols + c];
+            acc[c].x += pv * v.x;
+            acc[c].y += pv * v.y;
+          }
+      }
+#pragma unroll
+      for (int c = 0; c < NC; ++c)
+        if (c < cols) Ws[(size_t)t * cols + c] = acc[c];
+    }
+    __syncthreads();
+    for (int u = threadIdx.x; u < cl * cols; u += blockDim.x) {
+      const int il2 = u / cols, c = u - il2 * cols;
+      C a = mk<C>(0.0, 0.0);
+      for (int s2 = 0; s2 < S; ++s2) a = a + Ws[(size_t)(s2 * kw + il2) * cols + c];
+      Ys[(size_t)(c0 + il2) * cols + c] = a;
+    }
+    if (c0 + rows < K) {
+      __syncthreads();
+      stage_rows_async(Pst, Pm + (size_t)(c0 + rows) * nh, min(rows, K - c0 - rows), nh);
+      stage_wait();
+    }
+  }
+  __syncthreads();
+  // 2. assembly of F_E and F_I for n = m..T
+  const int nc = ncoef_of(T);
+  const size_t e0 = (size_t)poff(T + 1, m);
+  const int pidx0 = poff(T, m);
+  for (int t = threadIdx.x; t < (T + 1 - m) * B; t += blockDim.x) {
+    const int i = t / B, b = t - i * B, n = m + i;
+    C cur[5], up[5], dn[5];
+#pragma unroll
+    for (int f = 0; f < 5; ++f) {
+      cur[f] = Ys[(size_t)i * cols + b * 5 + f];
+      up[f] = Ys[(size_t)(i + 1) * cols + b * 5 + f];
+      dn[f] = i ? Ys[(size_t)(i - 1) * cols + b * 5 + f] : mk<C>(0.0, 0.0);
+    }
+    double2 fe[3];
+    assemble_point<R, C>(m, n, cur, up, dn, i > 0, eps[e0 + i + 1], eps[e0 + i], inva, inva2, fe);
+    const size_t idx = (size_t)pidx0 + i;
+    double2 *oE = fE + (size_t)b * 3 * nc;
+    oE[idx] = fe[0];
+    oE[nc + idx] = fe[1];
+    oE[2 * nc + idx] = fe[2];
+    if (fI) linear_point(m, n, state + (size_t)b * 3 * nc, nc, idx, dinva2, nu, phibar, fI + (size_t)b * 3 * nc);
+  }
+  __syncthreads();
+}
+
+// ---------------------------------------------------------------------------
+// IMEX-SDC sweep pieces for the coefficients of order m of one state whose
+// node arrays are `ns` complex elements apart (Section 5.1.1); the same
+// arithmetic as the element-wise sweep kernels.
+// ---------------------------------------------------------------------------
+// O_i = theta_0 (+ tau_i) + sum_j cE[i][j] F_E,j + cI[i][j] F_I,j, i = 1..M
+template <int MAXM>
+__device__ __forceinline__ void order_old_part(int m, int T, int M, size_t ns, const SdcCoef &c,
+                                               const double2 *__restrict__ th, const double2 *__restrict__ fe,
+                                               const double2 *__restrict__ fi, const double2 *__restrict__ tau,
+                                               double2 *__restrict__ O) {
+  const int nc = ncoef_of(T), p0 = poff(T, m), len = T + 1 - m;
+  for (int t = threadIdx.x; t < 3 * len; t += blockDim.x) {
+    const int fld = t / len;
+    const size_t e = (size_t)fld * nc + p0 + (t - fld * len);
+    double2 acc[MAXM + 1];
+    const double2 t0 = th[e];
+#pragma unroll
+    for (int i = 1; i <= MAXM; ++i)
+      if (i <= M) acc[i] = tau ? t0 + tau[(size_t)i * ns + e] : t0;
+#pragma unroll
+    for (int j = 0; j <= MAXM; ++j) {
+      if (j > M) break;
+      const double2 a = fe[(size_t)j * ns + e], f = fi[(size_t)j * ns + e];
+#pragma unroll
+      for (int i = 1; i <= MAXM; ++i)
+        if (i <= M) {
+          acc[i].x += c.cE[i][j] * a.x + c.cI[i][j] * f.x;
+          acc[i].y += c.cE[i][j] * a.y + c.cI[i][j] * f.y;
+        }
+    }
+#pragma unroll
+    for (int i = 1; i <= MAXM; ++i)
+      if (i <= M) O[(size_t)(i - 1) * 3 * nc + e] = acc[i];
+  }
+}
+
+// theta_i = solve(O_i + sum_{1<=j<i} nE[i][j] F_E,j + nI[i][j] F_I,j, h_i)
+// with fac[n] = {s = 1 + h nu k, 1/s, 1/(s^2 + h^2 Phibar k), h k} of node i
+__device__ __forceinline__ void order_node_update(int m, int T, int i, size_t ns, const SdcCoef &c, double hphibar,
+                                                  const double4_32a *__restrict__ fac, const double2 *__restrict__ O,
+                                                  const double2 *__restrict__ fe, const double2 *__restrict__ fi,
+                                                  double2 *__restrict__ th) {
+  const int nc = ncoef_of(T), p0 = poff(T, m), len = T + 1 - m;
+  double2 *out = th + (size_t)i * ns;
+  for (int t = threadIdx.x; t < len; t += blockDim.x) {
+    const int n = m + t;
+    const size_t idx = (size_t)p0 + t;
+    double2 r[3];
+    for (int f = 0; f < 3; ++f) {
+      const size_t e = (size_t)f * nc + idx;
+      double2 v = O[e];
+      for (int j = 1; j < i; ++j) {
+        const double2 a = fe[(size_t)j * ns + e], g = fi[(size_t)j * ns + e];
+        v.x += c.nE[i][j] * a.x + c.nI[i][j] * g.x;
+        v.y += c.nE[i][j] * a.y + c.nI[i][j] * g.y;
+      }
+      r[f] = v;
+    }
+    const double4_32a q = fac[n];
+    out[idx] = make_double2((q.x * r[0].x - hphibar * r[2].x) * q.z, (q.x * r[0].y - hphibar * r[2].y) * q.z);
+    out[nc + idx] = make_double2(r[1].x * q.y, r[1].y * q.y);
+    out[2 * nc + idx] = make_double2((q.x * r[2].x + q.w * r[0].x) * q.z, (q.x * r[2].y + q.w * r[0].y) * q.z);
+  }
+}
+
+}  // namespace pfsh

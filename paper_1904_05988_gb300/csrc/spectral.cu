@@ -228,13 +228,7 @@ int implicit_solve_launch(int T, const double *b, double *x, double h, int B, co
 // ---------------------------------------------------------------------------
 // SDC: constants of every node update from the old iterate, then node updates
 // ---------------------------------------------------------------------------
-struct SdcCoef {
-  double cE[16][16];  // dt (Q - QE') for the "old" right-hand sides
-  double cI[16][16];  // dt (Q - QI')
-  double nE[16][16];  // dt QE  (new explicit terms, j < i)
-  double nI[16][16];  // dt QI  (new implicit terms, j < i)
-  double h[16];       // dt QI[i][i]
-};
+
 
 // O_i = theta_0 + sum_j cE[i][j] FE_j + cI[i][j] FI_j (+ tau_i),  i = 1..M
 // (M <= MAXM; compile-time bound keeps the accumulators in registers)
@@ -270,7 +264,7 @@ __global__ void __launch_bounds__(128) k_sdc_old(int nc3, int B, int M, size_t n
 // with the per-degree solve factors of node i precomputed in FP64:
 // fac[n] = {s = 1 + h nu k, 1/s, 1/(s^2 + h^2 Phibar k), h k}
 __global__ void __launch_bounds__(128) k_sdc_node(int T, int B, int i, size_t nstride, SdcCoef c, double hphibar,
-                                                  const double4 *__restrict__ fac, const double2 *__restrict__ O,
+                                                  const double4_32a *__restrict__ fac, const double2 *__restrict__ O,
                                                   const double2 *__restrict__ fe, const double2 *__restrict__ fi,
                                                   double2 *__restrict__ th) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
@@ -290,21 +284,16 @@ __global__ void __launch_bounds__(128) k_sdc_node(int T, int B, int i, size_t ns
     }
     r[f] = v;
   }
-  const double4 q = fac[n];   // s, 1/s, 1/det, h k
+  const double4_32a q = fac[n];   // s, 1/s, 1/det, h k
   double2 *out = th + (size_t)i * nstride + (size_t)b * 3 * nc;
   out[idx] = make_double2((q.x * r[0].x - hphibar * r[2].x) * q.z, (q.x * r[0].y - hphibar * r[2].y) * q.z);
   out[nc + idx] = make_double2(r[1].x * q.y, r[1].y * q.y);
   out[2 * nc + idx] = make_double2((q.x * r[2].x + q.w * r[0].x) * q.z, (q.x * r[2].y + q.w * r[0].y) * q.z);
 }
 
-int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const double *tau, size_t node_stride,
-                      int B, cudaStream_t s) {
-  const swe_ctx *ctx = l->ctx;
-  const int T = ctx->plan->T;
-  const int nc = ncoef_of(T);
-  const int M = l->nodes - 1;
-  if (B > l->max_batch) return fail(PFSH_EINVAL, "sdc_sweep: batch larger than the level's max_batch");
+SdcCoef sdc_coef(const sdc_level *l) {
   SdcCoef c;
+  const int M = l->nodes - 1;
   for (int i = 0; i < 16; ++i) {
     c.h[i] = 0.0;
     for (int j = 0; j < 16; ++j) c.cE[i][j] = c.cI[i][j] = c.nE[i][j] = c.nI[i][j] = 0.0;
@@ -323,6 +312,17 @@ int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const
     }
     c.h[i] = dt * l->QI[i][i];
   }
+  return c;
+}
+
+int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const double *tau, size_t node_stride,
+                      int B, cudaStream_t s) {
+  const swe_ctx *ctx = l->ctx;
+  const int T = ctx->plan->T;
+  const int nc = ncoef_of(T);
+  const int M = l->nodes - 1;
+  if (B > l->max_batch) return fail(PFSH_EINVAL, "sdc_sweep: batch larger than the level's max_batch");
+  const SdcCoef c = sdc_coef(l);
   // node stride in complex elements
   const size_t ns = node_stride / 2;
   const int nc3 = 3 * nc;
@@ -341,7 +341,7 @@ int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const
     {
       PFSH_LAUNCH("k_sdc_node", s);
       k_sdc_node<<<g, 128, 0, s>>>(T, B, i, ns, c, c.h[i] * ctx->prm.phibar,
-                                   (const double4 *)l->d_fac + (size_t)i * (T + 1),
+                                   (const double4_32a *)l->d_fac + (size_t)i * (T + 1),
                                    (const double2 *)l->d_old + (size_t)(i - 1) * nc3 * B, (const double2 *)fE,
                                    (const double2 *)fI, (double2 *)theta);
     }

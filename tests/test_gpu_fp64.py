@@ -215,12 +215,14 @@ def test_sdc_sweep_with_tau_and_batch_matches_oracle():
 # ---------------------------------------------------------------------------
 # PFASST
 # ---------------------------------------------------------------------------
-@pytest.mark.parametrize("Tf,Tc,nts", [(21, 10, 4), (31, 31, 3)])
-def test_pfasst_predict_and_iterations_match_oracle(Tf, Tc, nts):
+@pytest.mark.parametrize("Tf,Tc,nts,groups", [(21, 10, 4, 0), (31, 31, 3, 0), (21, 10, 9, 2)])
+def test_pfasst_predict_and_iterations_match_oracle(Tf, Tc, nts, groups):
+    """groups = 2 with 9 slices: the coarse chain of slices 0-3 overlaps the
+    fine sweep of slices 4-8 (uneven groups of 4 and 5)."""
     dt, nf, nc, iters = 600.0, 5, 3, 3
     gf, gc = syn.gaussian_grid_size(Tf), syn.gaussian_grid_size(Tc)
     st0 = state_of(Tf, 21)[0]
-    pf = ps.pfasst_create(nts, nf, nc, Tf, *gf, Tc, *gc, dt, A, OM, syn.NU, PHIBAR, "fp64")
+    pf = ps.pfasst_create(nts, nf, nc, Tf, *gf, Tc, *gc, dt, A, OM, syn.NU, PHIBAR, "fp64", slice_groups=groups)
     ps.pfasst_set_initial(pf, cuda(st0))
     ps.pfasst_predict(pf)
     p = SWEParams(a=A, omega=OM, g=G, nu=syn.NU, phibar=PHIBAR)
@@ -244,3 +246,32 @@ def test_pfasst_predict_and_iterations_match_oracle(Tf, Tc, nts):
         o.iteration(last)
         ps.pfsh_sync_status()
         compare(1e-11)
+
+
+@pytest.mark.parametrize("form", ["fp64", "bf16x3"])
+def test_pfasst_slice_groups_leave_results_unchanged(form):
+    """The pipelined iteration (coarse chain of a slice group overlapping the
+    fine sweeps of the next groups) computes exactly what the one-group
+    iteration computes: same kernels, same batch paths, same order of
+    arithmetic per slice."""
+    if form not in ps.available_precisions():
+        pytest.skip(f"{form} not built")
+    Tf, Tc, nts, dt = 63, 31, 12, 600.0
+    gf, gc = syn.gaussian_grid_size(Tf), syn.gaussian_grid_size(Tc)
+    st0 = cuda(state_of(Tf, 23)[0])
+    outs = []
+    for groups in (1, 3):
+        pf = ps.pfasst_create(nts, 5, 3, Tf, *gf, Tc, *gc, dt, A, OM, syn.NU, PHIBAR, form, slice_groups=groups)
+        ps.pfasst_set_initial(pf, st0)
+        ps.pfasst_predict(pf)
+        for it in range(3):   # eager, graph capture, graph replay
+            ps.pfasst_iteration(pf, False)
+        ps.pfasst_iteration(pf, True)
+        res = torch.empty((nts, 5, 3, syn.ncoef(Tf)), dtype=torch.complex128, device=DEV)
+        for n in range(nts):
+            for k in range(5):
+                ps.pfasst_get(pf, 0, n, k, res[n, k])
+        ps.pfsh_sync_status()
+        outs.append(res.cpu().numpy())
+        pf.close()
+    assert np.array_equal(outs[0], outs[1])
