@@ -310,8 +310,8 @@ __device__ __forceinline__ void order_old_part(int m, int T, int M, size_t ns, c
 #pragma unroll
       for (int i = 1; i <= MAXM; ++i)
         if (i <= M) {
-          acc[i].x += c.cE[i][j] * a.x + c.cI[i][j] * f.x;
-          acc[i].y += c.cE[i][j] * a.y + c.cI[i][j] * f.y;
+          acc[i].x = fma(c.cI[i][j], f.x, fma(c.cE[i][j], a.x, acc[i].x));
+          acc[i].y = fma(c.cI[i][j], f.y, fma(c.cE[i][j], a.y, acc[i].y));
         }
     }
 #pragma unroll
@@ -337,8 +337,8 @@ __device__ __forceinline__ void order_node_update(int m, int T, int i, size_t ns
       double2 v = O[e];
       for (int j = 1; j < i; ++j) {
         const double2 a = fe[(size_t)j * ns + e], g = fi[(size_t)j * ns + e];
-        v.x += c.nE[i][j] * a.x + c.nI[i][j] * g.x;
-        v.y += c.nE[i][j] * a.y + c.nI[i][j] * g.y;
+        v.x = fma(c.nI[i][j], g.x, fma(c.nE[i][j], a.x, v.x));
+        v.y = fma(c.nI[i][j], g.y, fma(c.nE[i][j], a.y, v.y));
       }
       r[f] = v;
     }

@@ -231,33 +231,39 @@ int implicit_solve_launch(int T, const double *b, double *x, double h, int B, co
 
 
 // O_i = theta_0 + sum_j cE[i][j] FE_j + cI[i][j] FI_j (+ tau_i),  i = 1..M
-// (M <= MAXM; compile-time bound keeps the accumulators in registers)
-template <int MAXM>
-__global__ void __launch_bounds__(128) k_sdc_old(int nc3, int B, int M, size_t nstride, SdcCoef c,
+// (M a template parameter: the accumulators stay in registers and no FP64
+// issue slot is spent on masked-off terms)
+template <int M>
+__global__ void __launch_bounds__(128) k_sdc_old(int nc3, int B, size_t nstride, SdcCoef c,
                                                  const double2 *__restrict__ th, const double2 *__restrict__ fe,
                                                  const double2 *__restrict__ fi, const double2 *__restrict__ tau,
                                                  size_t tstride, double2 *__restrict__ O) {
   size_t t = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
   if (t >= (size_t)nc3 * B) return;
-  double2 acc[MAXM + 1];
+  double2 acc[M + 1];
   const double2 t0 = th[t];
 #pragma unroll
-  for (int i = 1; i <= MAXM; ++i)
-    if (i <= M) acc[i] = tau ? t0 + tau[(size_t)i * tstride + t] : t0;
+  for (int i = 1; i <= M; ++i) acc[i] = tau ? t0 + tau[(size_t)i * tstride + t] : t0;
 #pragma unroll
-  for (int j = 0; j <= MAXM; ++j) {
-    if (j > M) break;
+  for (int j = 0; j <= M; ++j) {
     const double2 e = fe[(size_t)j * nstride + t], f = fi[(size_t)j * nstride + t];
 #pragma unroll
-    for (int i = 1; i <= MAXM; ++i)
-      if (i <= M) {
-        acc[i].x += c.cE[i][j] * e.x + c.cI[i][j] * f.x;
-        acc[i].y += c.cE[i][j] * e.y + c.cI[i][j] * f.y;
-      }
+    for (int i = 1; i <= M; ++i) {
+      acc[i].x = fma(c.cI[i][j], f.x, fma(c.cE[i][j], e.x, acc[i].x));
+      acc[i].y = fma(c.cI[i][j], f.y, fma(c.cE[i][j], e.y, acc[i].y));
+    }
   }
 #pragma unroll
-  for (int i = 1; i <= MAXM; ++i)
-    if (i <= M) O[(size_t)(i - 1) * nc3 * B + t] = acc[i];
+  for (int i = 1; i <= M; ++i) O[(size_t)(i - 1) * nc3 * B + t] = acc[i];
+}
+
+template <int M>
+static void sdc_old_launch(int nc3, int B, size_t ns, const SdcCoef &c, const double *theta, const double *fE,
+                           const double *fI, const double *tau, double *O, cudaStream_t s) {
+  const size_t total = (size_t)nc3 * B;
+  k_sdc_old<M><<<(unsigned)((total + 127) / 128), 128, 0, s>>>(nc3, B, ns, c, (const double2 *)theta,
+                                                              (const double2 *)fE, (const double2 *)fI,
+                                                              (const double2 *)tau, ns, (double2 *)O);
 }
 
 // theta_i = solve(O_i + sum_{1<=j<i} nE[i][j] FE_j^new + nI[i][j] FI_j^new, h_i)
@@ -279,8 +285,8 @@ __global__ void __launch_bounds__(128) k_sdc_node(int T, int B, int i, size_t ns
     double2 v = O[t];
     for (int j = 1; j < i; ++j) {
       const double2 e = fe[(size_t)j * nstride + t], g = fi[(size_t)j * nstride + t];
-      v.x += c.nE[i][j] * e.x + c.nI[i][j] * g.x;
-      v.y += c.nE[i][j] * e.y + c.nI[i][j] * g.y;
+      v.x = fma(c.nI[i][j], g.x, fma(c.nE[i][j], e.x, v.x));
+      v.y = fma(c.nI[i][j], g.y, fma(c.nE[i][j], e.y, v.y));
     }
     r[f] = v;
   }
@@ -327,15 +333,20 @@ int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const
   const size_t ns = node_stride / 2;
   const int nc3 = 3 * nc;
   {
-    size_t total = (size_t)nc3 * B;
-    {
-      PFSH_LAUNCH("k_sdc_old", s);
-      k_sdc_old<8><<<(unsigned)((total + 127) / 128), 128, 0, s>>>(nc3, B, M, ns, c, (const double2 *)theta,
-                                                               (const double2 *)fE, (const double2 *)fI,
-                                                               (const double2 *)tau, ns, (double2 *)l->d_old);
+    PFSH_LAUNCH("k_sdc_old", s);
+    double *O = l->d_old;
+    switch (M) {
+      case 1: sdc_old_launch<1>(nc3, B, ns, c, theta, fE, fI, tau, O, s); break;
+      case 2: sdc_old_launch<2>(nc3, B, ns, c, theta, fE, fI, tau, O, s); break;
+      case 3: sdc_old_launch<3>(nc3, B, ns, c, theta, fE, fI, tau, O, s); break;
+      case 4: sdc_old_launch<4>(nc3, B, ns, c, theta, fE, fI, tau, O, s); break;
+      case 5: sdc_old_launch<5>(nc3, B, ns, c, theta, fE, fI, tau, O, s); break;
+      case 6: sdc_old_launch<6>(nc3, B, ns, c, theta, fE, fI, tau, O, s); break;
+      case 7: sdc_old_launch<7>(nc3, B, ns, c, theta, fE, fI, tau, O, s); break;
+      default: sdc_old_launch<8>(nc3, B, ns, c, theta, fE, fI, tau, O, s); break;
     }
-    PFSH_CHECK_LAUNCH("k_sdc_old");
   }
+  PFSH_CHECK_LAUNCH("k_sdc_old");
   for (int i = 1; i <= M; ++i) {
     dim3 g((nc + 127) / 128, B);
     {
