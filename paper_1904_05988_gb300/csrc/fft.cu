@@ -107,6 +107,7 @@ __global__ void __launch_bounds__(256) k_grid_rhs(FftArgs f, int T, int nlat, in
                                                   const typename cpx<Rl>::t *__restrict__ tw,
                                                   typename cpx<Rl>::t *__restrict__ H) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
   grid_rhs_body<Rl, Shape>(f, T, nlat, B, blockIdx.x, blockIdx.y, F, rowf, tw, H,
                            reinterpret_cast<typename cpx<Rl>::t *>(smem_raw));
 }
@@ -179,7 +180,7 @@ int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s) {
 
 template <typename Rl>
 static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typename cpx<Rl>::t *tw, const Rl *rowf,
-                       cudaStream_t s) {
+                       cudaStream_t s, bool pdl) {
   typedef typename cpx<Rl>::t C;
   const size_t sm = 10 * (size_t)padded(f.N) * sizeof(C);
   return with_shape(f.N, [&]<typename Shape>() -> int {
@@ -187,18 +188,24 @@ static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typenam
     if (rc) return rc;
     {
       PFSH_LAUNCH("k_grid_rhs", s);
-      k_grid_rhs<Rl, Shape><<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw,
-                                                            (C *)p->H);
+      if (pdl) {
+        cudaError_t e = launch_pdl(k_grid_rhs<Rl, Shape>, dim3(p->nh, B), dim3(256), sm, s, f, p->T, p->nlat, B,
+                                   (const C *)p->F, rowf, tw, (C *)p->H);
+        if (e != cudaSuccess) return cuda_fail(e, "k_grid_rhs");
+      } else {
+        k_grid_rhs<Rl, Shape><<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw,
+                                                              (C *)p->H);
+      }
     }
     PFSH_CHECK_LAUNCH("k_grid_rhs");
     return PFSH_OK;
   });
 }
 
-int grid_rhs(const sht_plan *p, int B, const swe_params &, cudaStream_t s) {
+int grid_rhs(const sht_plan *p, int B, const swe_params &, cudaStream_t s, bool pdl) {
   FftArgs f = fft_args(p->fft);
-  if (p->prec == PFSH_FP64) return grid_launch<double>(p, f, B, p->fft.tw64, p->d_rowf, s);
-  return grid_launch<float>(p, f, B, p->fft.tw32, p->d_rowf32, s);
+  if (p->prec == PFSH_FP64) return grid_launch<double>(p, f, B, p->fft.tw64, p->d_rowf, s, pdl);
+  return grid_launch<float>(p, f, B, p->fft.tw32, p->d_rowf32, s, pdl);
 }
 
 }  // namespace pfsh

@@ -1,6 +1,8 @@
 // Internal declarations of the PFASST-SH CUDA library (not part of the ABI).
 #pragma once
 
+#include <utility>
+
 #include <cuda_runtime.h>
 #include <stdint.h>
 
@@ -41,6 +43,34 @@ struct LaunchScope {
   int slot;
 };
 #define PFSH_LAUNCH(name, stream) ::pfsh::LaunchScope pfsh_scope_(name, stream)
+
+// Programmatic dependent launch: a kernel launched with launch_pdl is set up
+// while the previous kernel of its stream drains and runs only independent
+// work (tables, constants) before pdl_wait(), which returns once that kernel
+// has completed and its writes are visible.  Every kernel that can be
+// launched this way calls pdl_wait() (also when it reads nothing the previous
+// kernel wrote) so that completion stays ordered along the stream.  No kernel
+// triggers its dependents early: dependents that became resident early and
+// waited held SM resources that the concurrently running fine sweeps need
+// (measured: 169 vs 182 iterations/s).  Without a programmatic predecessor
+// pdl_wait() is a no-op.
+__device__ __forceinline__ void pdl_wait() { asm volatile("griddepcontrol.wait;" ::: "memory"); }
+
+template <typename... KArgs, typename... Args>
+cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t smem, cudaStream_t s,
+                       Args &&...args) {
+  cudaLaunchConfig_t cfg = {};
+  cfg.gridDim = grid;
+  cfg.blockDim = block;
+  cfg.dynamicSmemBytes = smem;
+  cfg.stream = s;
+  cudaLaunchAttribute at[1];
+  at[0].id = cudaLaunchAttributeProgrammaticStreamSerialization;
+  at[0].val.programmaticStreamSerializationAllowed = 1;
+  cfg.attrs = at;
+  cfg.numAttrs = 1;
+  return cudaLaunchKernelEx(&cfg, kern, std::forward<Args>(args)...);
+}
 
 // sticky device status word shared by every object of the library
 int *device_status();
@@ -278,7 +308,8 @@ int legendre_analysis(const sht_plan *p, int cols, cudaStream_t s);
 bool uses_tensor_cores(int prec);
 int ifft_rows(const sht_plan *p, int cols, void *grid, cudaStream_t s);        // F -> grid
 int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s);   // grid -> H
-int grid_rhs(const sht_plan *p, int B, const swe_params &prm, cudaStream_t s); // F -> H (RHS)
+int grid_rhs(const sht_plan *p, int B, const swe_params &prm, cudaStream_t s,
+             bool pdl = false);   // F -> H (RHS)
 int ifft_rows_f64_raw(int N, int npass, const int *radix, int full, int T, int nlat, int cols, const double2 *F,
                       const double2 *tw, double *grid, cudaStream_t s);
 

@@ -46,8 +46,8 @@ __global__ void __launch_bounds__(kSynthThreads) k_small_synth(int T, int nlat, 
                                                                typename cpx<R>::t *__restrict__ F) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *Pst = reinterpret_cast<R *>(smem_raw);
-  small_synth_body<R, NB>(blockIdx.x, T, nlat, B, rows, Pst, false, ma2, inva, omega, phibar, tb, P, state, F,
-                          smem_raw + small_stage_bytes<R>(nlat, rows));
+  small_synth_body<R, NB>(blockIdx.x, T, nlat, B, rows, Pst, STAGE_SELF, ma2, inva, omega, phibar, tb, P, state,
+                          nullptr, F, smem_raw + small_stage_bytes<R>(nlat, rows));
 }
 
 template <typename R, int NB>
@@ -59,8 +59,8 @@ __global__ void __launch_bounds__(kAnalThreads) k_small_anal(int T, int nlat, in
                                                              double2 *__restrict__ fE, double2 *__restrict__ fI) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *Pst = reinterpret_cast<R *>(smem_raw);
-  small_anal_body<R, NB>(blockIdx.x, T, nlat, B, rows, Pst, inva, inva2, dinva2, nu, phibar, eps, P, H, state, fE,
-                         fI, smem_raw + small_stage_bytes<R>(nlat, rows));
+  small_anal_body<R, NB>(blockIdx.x, T, nlat, B, rows, Pst, false, inva, inva2, dinva2, nu, phibar, eps, P, H,
+                         state, fE, fI, smem_raw + small_stage_bytes<R>(nlat, rows));
 }
 
 template <typename R, int NB>
@@ -131,6 +131,7 @@ struct ChainStep {
 template <typename R>
 struct ChainGeo {
   int T, nlat, rows;
+  size_t work;                // bytes of the body work region
   R ma2, inva, inva2;
   double dinva2, omega, nu, phibar;
   SpecTables<R> tb;
@@ -142,14 +143,22 @@ struct ChainGeo {
 template <typename R>
 __global__ void __launch_bounds__(kChainThreads) k_chain_node(ChainStep st, ChainGeo<R> g, SdcCoef c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int m = blockIdx.x, T = g.T, nc = ncoef_of(T);
+  const int m = blockIdx.x, T = g.T, nc = ncoef_of(T), K = T + 2 - m;
   R *Pst = reinterpret_cast<R *>(smem_raw);
   unsigned char *work = smem_raw + small_stage_bytes<R>(g.nlat, g.rows);
+  double2 *thk = reinterpret_cast<double2 *>(work + g.work);   // [3][T+1-m] state of node k, order m
   const bool anal = st.a_th != nullptr;
+  // independent prologue: the order's Legendre rows (a table), then wait for
+  // the previous kernel of the stream (programmatic dependent launch)
+  stage_rows_async(Pst, g.P + (size_t)eoff(T, m) * (g.nlat / 2), min(K, g.rows), g.nlat / 2);
+  pdl_wait();
   if (anal)
-    small_anal_body<R, 1>(m, T, g.nlat, 1, g.rows, Pst, g.inva, g.inva2, g.dinva2, g.nu, g.phibar, g.tb.eps, g.P,
-                          g.H, st.a_th, st.a_fe, st.a_fi, work);
-  if (st.k == 0) return;
+    small_anal_body<R, 1>(m, T, g.nlat, 1, g.rows, Pst, true, g.inva, g.inva2, g.dinva2, g.nu, g.phibar, g.tb.eps,
+                          g.P, g.H, st.a_th, st.a_fe, st.a_fi, work);
+  if (st.k == 0) {
+    if (!anal) stage_wait();
+    return;
+  }
   const int p0 = poff(T, m), len = T + 1 - m;
   if (st.r_th) {
     for (int t = threadIdx.x; t < 3 * len; t += blockDim.x) {
@@ -166,24 +175,31 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_node(ChainStep st, Chai
     __syncthreads();
   }
   order_node_update(m, T, st.k, st.ns, c, st.hphibar, st.fac, st.O + (size_t)(st.k - 1) * 3 * nc, st.fe, st.fi,
-                    st.th);
+                    st.th, thk);
   __syncthreads();
-  const bool staged = anal && (T + 2 - m) <= g.rows;
-  small_synth_body<R, 1>(m, T, g.nlat, 1, g.rows, Pst, staged, g.ma2, g.inva, g.omega, g.phibar, g.tb, g.P,
-                         st.th + (size_t)st.k * st.ns, g.F, work);
+  // rows issued in the prologue: complete after the analysis, else in flight
+  const int pmode = anal ? (K <= g.rows ? STAGE_DONE : STAGE_SELF) : STAGE_ISSUED;
+  small_synth_body<R, 1>(m, T, g.nlat, 1, g.rows, Pst, pmode, g.ma2, g.inva, g.omega, g.phibar, g.tb, g.P,
+                         st.th + (size_t)st.k * st.ns, thk, g.F, work);
 }
 
 template <typename R>
-static int chain_node_launch(const ChainStep &st, ChainGeo<R> g, const SdcCoef &c, cudaStream_t s) {
-  const size_t work = std::max(small_synth_work<R>(g.T, g.nlat, 1, kChainThreads),
-                               small_anal_work<R>(g.T, g.nlat, 1, kChainThreads));
-  g.rows = small_stage_rows<R>(work, g.T, g.nlat, kChainBudget);
-  const size_t smem = work + small_stage_bytes<R>(g.nlat, g.rows);
+static int chain_node_launch(const ChainStep &st, ChainGeo<R> g, const SdcCoef &c, cudaStream_t s, bool pdl) {
+  g.work = std::max(small_synth_work<R>(g.T, g.nlat, 1, kChainThreads),
+                    small_anal_work<R>(g.T, g.nlat, 1, kChainThreads));
+  const size_t thk = align16((size_t)3 * (g.T + 1) * sizeof(double2));
+  g.rows = small_stage_rows<R>(g.work + thk, g.T, g.nlat, kChainBudget);
+  const size_t smem = g.work + thk + small_stage_bytes<R>(g.nlat, g.rows);
   int rc = ensure_smem((const void *)k_chain_node<R>, smem);
   if (rc) return rc;
   {
     PFSH_LAUNCH("k_chain_node", s);
-    k_chain_node<R><<<g.T + 1, kChainThreads, smem, s>>>(st, g, c);
+    if (pdl) {
+      cudaError_t e = launch_pdl(k_chain_node<R>, dim3(g.T + 1), dim3(kChainThreads), smem, s, st, g, c);
+      if (e != cudaSuccess) return cuda_fail(e, "k_chain_node");
+    } else {
+      k_chain_node<R><<<g.T + 1, kChainThreads, smem, s>>>(st, g, c);
+    }
   }
   PFSH_CHECK_LAUNCH("k_chain_node");
   return PFSH_OK;
@@ -193,7 +209,7 @@ template <typename R>
 static ChainGeo<R> chain_geo(const sht_plan *p, const swe_params &prm, const R *P, SpecTables<R> tb) {
   typedef typename cpx<R>::t C;
   const double inva2 = 1.0 / (prm.a * prm.a);
-  return ChainGeo<R>{p->T, p->nlat, 0, (R)(-prm.a * prm.a), (R)(1.0 / prm.a), (R)inva2, inva2, prm.omega, prm.nu,
+  return ChainGeo<R>{p->T, p->nlat, 0, 0, (R)(-prm.a * prm.a), (R)(1.0 / prm.a), (R)inva2, inva2, prm.omega, prm.nu,
                      prm.phibar, tb, P, (C *)p->F, (const C *)p->H};
 }
 
@@ -236,8 +252,9 @@ static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, doub
         st.r_fe = FE + (n - 1) * ss + M * ns;
         st.r_fi = FI + (n - 1) * ss + M * ns;
       }
-      if ((rc = chain_node_launch<R>(st, g, c, s))) return rc;
-      if ((rc = grid_rhs(p, 1, ctx->prm, s))) return rc;
+      // the first launch of the chain follows other work of the stream
+      if ((rc = chain_node_launch<R>(st, g, c, s, n > n0 || k > 1))) return rc;
+      if ((rc = grid_rhs(p, 1, ctx->prm, s, true))) return rc;
     }
   }
   if (n1 > n0) {   // analysis of the last slice's last node
@@ -245,7 +262,7 @@ static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, doub
     st.a_th = TH + (n1 - 1) * ss + M * ns;
     st.a_fe = FE + (n1 - 1) * ss + M * ns;
     st.a_fi = FI + (n1 - 1) * ss + M * ns;
-    if ((rc = chain_node_launch<R>(st, g, c, s))) return rc;
+    if ((rc = chain_node_launch<R>(st, g, c, s, true))) return rc;
   }
   return PFSH_OK;
 }

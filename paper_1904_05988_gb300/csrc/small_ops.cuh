@@ -94,16 +94,23 @@ __host__ inline int small_stage_rows(size_t fixed, int T, int nlat, size_t budge
 
 // ---------------------------------------------------------------------------
 // velocity recovery + Legendre synthesis of order m for B <= NB states
-//   Pst:  staging buffer of `rows` rows; if `staged`, it already holds rows
-//         [0, K) of order m (K = T+2-m <= rows required)
-//   work: [K][4B] coefficient rows | [parts][nh][2][4B] partial sums
+//   Pst:   staging buffer of `rows` rows of order m; pmode says who fills the
+//          first chunk: STAGE_SELF (this body), STAGE_ISSUED (the caller has
+//          issued the copies, this body waits for them) or STAGE_DONE (rows
+//          [0, K) are complete, K = T+2-m <= rows required)
+//   sm_th: optional shared-memory copy of the state's order-m coefficients
+//          ([field][n - m], B = 1); read instead of `state` when given
+//   work:  [K][4B] coefficient rows | [parts][nh][2][4B] partial sums
 // Called by every thread of a block.
 // ---------------------------------------------------------------------------
+enum { STAGE_SELF = 0, STAGE_ISSUED = 1, STAGE_DONE = 2 };
+
 template <typename R, int NB>
-__device__ __forceinline__ void small_synth_body(int m, int T, int nlat, int B, int rows, R *Pst, bool staged,
+__device__ __forceinline__ void small_synth_body(int m, int T, int nlat, int B, int rows, R *Pst, int pmode,
                                                  R ma2, R inva, double omega, double phibar, SpecTables<R> tb,
                                                  const R *__restrict__ P, const double2 *__restrict__ state,
-                                                 typename cpx<R>::t *__restrict__ F, void *work) {
+                                                 const double2 *sm_th, typename cpx<R>::t *__restrict__ F,
+                                                 void *work) {
   typedef typename cpx<R>::t C;
   constexpr int NC = 4 * NB;
   const int nh = nlat / 2, K = T + 2 - m, cols = 4 * B, ld = nh + 1;
@@ -117,15 +124,21 @@ __device__ __forceinline__ void small_synth_body(int m, int T, int nlat, int B, 
   const R *Pm = P + (size_t)eoff(T, m) * nh;
   // 1. first chunk of Legendre rows in flight while the coefficient rows
   //    (velocity recovery) are computed
-  if (!staged) stage_rows_async(Pst, Pm, min(K, rows), nh);
+  if (pmode == STAGE_SELF) stage_rows_async(Pst, Pm, min(K, rows), nh);
+  const int len = T + 1 - m;
   for (int t = threadIdx.x; t < K * B; t += blockDim.x) {
     const int i = t / B, b = t - i * B;
-    const double2 *Phi = state + (size_t)b * 3 * nc;
-    prep_point<R>(T, m, m + i, Phi, Phi + nc, Phi + 2 * nc, base, e0 + i, tb, ma2, inva, omega, phibar,
-                  Xs + (size_t)i * cols + b * 4);
+    if (sm_th) {
+      prep_point<R>(T, m, m + i, sm_th, sm_th + len, sm_th + 2 * len, -m, e0 + i, tb, ma2, inva, omega, phibar,
+                    Xs + (size_t)i * cols);
+    } else {
+      const double2 *Phi = state + (size_t)b * 3 * nc;
+      prep_point<R>(T, m, m + i, Phi, Phi + nc, Phi + 2 * nc, base, e0 + i, tb, ma2, inva, omega, phibar,
+                    Xs + (size_t)i * cols + b * 4);
+    }
   }
   for (int t = threadIdx.x; t < parts * nh * 2 * cols; t += blockDim.x) Ps[t] = mk<C>(0.0, 0.0);
-  if (!staged) stage_wait();
+  if (pmode != STAGE_DONE) stage_wait();
   else __syncthreads();
   // 2. even/odd Legendre sums per latitude; each chunk is split among `parts`
   //    thread groups, partial sums accumulate in Ps
@@ -190,15 +203,17 @@ __device__ __forceinline__ void small_synth_body(int m, int T, int nlat, int B, 
 // n = m..T, B <= NB states.  Thread groups split the latitudes: thread
 // (s, i) sums latitudes [s nh/S, (s+1) nh/S) of degree row i; the S partial
 // sums are added in shared memory (no warp-wide butterfly).
-//   Pst:  staging buffer of `rows` rows; on return it holds the last chunk
-//         (all K rows when K <= rows), so a following synthesis of the same
-//         order may reuse it
+//   Pst:  staging buffer of `rows` rows (the first chunk's copies already
+//         issued by the caller when p_issued); on return it holds the last
+//         chunk (all K rows when K <= rows), so a following synthesis of the
+//         same order may reuse it
 //   work: [K][5B] analysed rows | [2][nh][5B] hemispheric sums of order m |
 //         [threads][5B] partial sums
 // Called by every thread of a block.
 // ---------------------------------------------------------------------------
 template <typename R, int NB>
-__device__ __forceinline__ void small_anal_body(int m, int T, int nlat, int B, int rows, R *Pst, R inva, R inva2,
+__device__ __forceinline__ void small_anal_body(int m, int T, int nlat, int B, int rows, R *Pst, bool p_issued,
+                                                R inva, R inva2,
                                                 double dinva2, double nu, double phibar, const R *__restrict__ eps,
                                                 const R *__restrict__ P, const typename cpx<R>::t *__restrict__ H,
                                                 const double2 *__restrict__ state, double2 *__restrict__ fE,
@@ -214,7 +229,7 @@ __device__ __forceinline__ void small_anal_body(int m, int T, int nlat, int B, i
   C *Ws = reinterpret_cast<C *>(w);                                               // [threads][cols]
   const R *Pm = P + (size_t)eoff(T, m) * nh;
   stage_async(Hs, H + (size_t)m * 2 * nh * cols, 2 * nh * cols);
-  stage_rows_async(Pst, Pm, min(K, rows), nh);
+  if (!p_issued) stage_rows_async(Pst, Pm, min(K, rows), nh);
   stage_wait();
   // 1. analysis of every degree row of this order
   for (int c0 = 0; c0 < K; c0 += rows) {
@@ -322,10 +337,11 @@ __device__ __forceinline__ void order_old_part(int m, int T, int M, size_t ns, c
 
 // theta_i = solve(O_i + sum_{1<=j<i} nE[i][j] F_E,j + nI[i][j] F_I,j, h_i)
 // with fac[n] = {s = 1 + h nu k, 1/s, 1/(s^2 + h^2 Phibar k), h k} of node i
+// (also written to sm_th[field][n - m] when given)
 __device__ __forceinline__ void order_node_update(int m, int T, int i, size_t ns, const SdcCoef &c, double hphibar,
                                                   const double4_32a *__restrict__ fac, const double2 *__restrict__ O,
                                                   const double2 *__restrict__ fe, const double2 *__restrict__ fi,
-                                                  double2 *__restrict__ th) {
+                                                  double2 *__restrict__ th, double2 *sm_th) {
   const int nc = ncoef_of(T), p0 = poff(T, m), len = T + 1 - m;
   double2 *out = th + (size_t)i * ns;
   for (int t = threadIdx.x; t < len; t += blockDim.x) {
@@ -343,9 +359,17 @@ __device__ __forceinline__ void order_node_update(int m, int T, int i, size_t ns
       r[f] = v;
     }
     const double4_32a q = fac[n];
-    out[idx] = make_double2((q.x * r[0].x - hphibar * r[2].x) * q.z, (q.x * r[0].y - hphibar * r[2].y) * q.z);
-    out[nc + idx] = make_double2(r[1].x * q.y, r[1].y * q.y);
-    out[2 * nc + idx] = make_double2((q.x * r[2].x + q.w * r[0].x) * q.z, (q.x * r[2].y + q.w * r[0].y) * q.z);
+    const double2 x0 = make_double2((q.x * r[0].x - hphibar * r[2].x) * q.z, (q.x * r[0].y - hphibar * r[2].y) * q.z);
+    const double2 x1 = make_double2(r[1].x * q.y, r[1].y * q.y);
+    const double2 x2 = make_double2((q.x * r[2].x + q.w * r[0].x) * q.z, (q.x * r[2].y + q.w * r[0].y) * q.z);
+    out[idx] = x0;
+    out[nc + idx] = x1;
+    out[2 * nc + idx] = x2;
+    if (sm_th) {
+      sm_th[t] = x0;
+      sm_th[len + t] = x1;
+      sm_th[2 * len + t] = x2;
+    }
   }
 }
 
