@@ -70,7 +70,10 @@ typedef enum {
  * bookkeeping in float64 and run FFTs and grid products in float32:
  *   PFSH_FP32   Legendre in float32 on CUDA cores,
  *   PFSH_BF16   Legendre on tensor cores, bf16 operands, fp32 accumulation,
- *   PFSH_FP16   as BF16 with fp16 operands (power-of-two scaled),
+ *   PFSH_FP16   as BF16 with fp16 operands; transforms only: inputs must lie
+ *               in the fp16 range (|x| < 65504, relative precision lost
+ *               below 6e-5), which the right-hand side's flux products do
+ *               not, so swe_ctx_create refuses FP16 plans (EUNSUPPORTED),
  *   PFSH_BF16X3 split bf16 hi/lo products (hi*hi + hi*lo + lo*hi), fp32 acc. */
 typedef enum {
   PFSH_FP64 = 0,

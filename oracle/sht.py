@@ -159,6 +159,23 @@ class SHT:
 # Layout helpers (library boundary convention)
 # --------------------------------------------------------------------------
 
+def synthesis_rows(c: np.ndarray, mu: np.ndarray, nlon: int) -> np.ndarray:
+    """The synthesis of Section 3 evaluated on chosen latitudes only.
+
+    Dense coefficients c [..., m, n] -> real grid rows [..., len(mu), nlon]
+    at the points (lambda_k = 2 pi k / nlon, mu): the same definition as
+    SHT.synthesis, with the Legendre table built for the requested mu alone,
+    so that sample rows of a high truncation cost a single table column.
+    """
+    L = c.shape[-1]
+    P = legendre_table(L, np.atleast_1d(np.asarray(mu, dtype=np.float64)))
+    F = np.einsum("...mn,mnj->...jm", c, P)
+    X = np.zeros(F.shape[:-1] + (nlon // 2 + 1,), dtype=np.complex128)
+    X[..., :L] = F
+    X[..., 0] = X[..., 0].real
+    return nlon * np.fft.irfft(X, n=nlon, axis=-1)
+
+
 def pack(c: np.ndarray, T: int) -> np.ndarray:
     """Dense [..., m, n] -> packed m-major triangle [..., (T+1)(T+2)/2]."""
     parts = [c[..., m, m:T + 1] for m in range(T + 1)]

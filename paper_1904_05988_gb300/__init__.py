@@ -108,7 +108,7 @@ def available_precisions() -> list[str]:
     return [name for name, code in PREC_NAMES.items() if code in _BUILT_PRECISIONS]
 
 
-_BUILT_PRECISIONS = {PFSH_FP64, PFSH_FP32, PFSH_BF16, PFSH_BF16X3}
+_BUILT_PRECISIONS = {PFSH_FP64, PFSH_FP32, PFSH_BF16, PFSH_FP16, PFSH_BF16X3}
 
 
 def last_error() -> str:

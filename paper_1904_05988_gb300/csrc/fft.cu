@@ -112,6 +112,18 @@ __global__ void __launch_bounds__(256) k_grid_rhs(FftArgs f, int T, int nlat, in
                            reinterpret_cast<typename cpx<Rl>::t *>(smem_raw));
 }
 
+template <typename Rl, typename Shape>
+__global__ void __launch_bounds__(256) k_grid_rhs_long(FftArgs f, int T, int nlat, int B,
+                                                       const typename cpx<Rl>::t *__restrict__ F,
+                                                       const Rl *__restrict__ rowf,
+                                                       const typename cpx<Rl>::t *__restrict__ tw,
+                                                       typename cpx<Rl>::t *__restrict__ H) {
+  extern __shared__ __align__(16) unsigned char smem_raw[];
+  pdl_wait();
+  grid_rhs_body_long<Rl, Shape>(f, T, nlat, B, blockIdx.x, blockIdx.y, F, rowf, tw, H,
+                                reinterpret_cast<typename cpx<Rl>::t *>(smem_raw));
+}
+
 // ---------------------------------------------------------------------------
 // launchers
 // ---------------------------------------------------------------------------
@@ -178,23 +190,30 @@ int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s) {
   return fft_launch<float>(f, p->T, p->nlat, cols, (const float *)grid, p->d_w, p->fft.tw32, (float2 *)p->H, s);
 }
 
+constexpr size_t kGridSmemLimit = 227 * 1024;
+
+// Rows whose 10 padded transforms fit in shared memory take k_grid_rhs,
+// longer ones k_grid_rhs_long (6 transforms).
 template <typename Rl>
 static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typename cpx<Rl>::t *tw, const Rl *rowf,
                        cudaStream_t s, bool pdl) {
   typedef typename cpx<Rl>::t C;
-  const size_t sm = 10 * (size_t)padded(f.N) * sizeof(C);
+  const size_t sm10 = 10 * (size_t)padded(f.N) * sizeof(C), sm6 = 6 * (size_t)padded(f.N) * sizeof(C);
+  const bool longrows = sm10 > kGridSmemLimit;
+  if (longrows && sm6 > kGridSmemLimit) return fail(PFSH_EUNSUPPORTED, "grid stage: nlon too long for this precision");
+  const size_t sm = longrows ? sm6 : sm10;
   return with_shape(f.N, [&]<typename Shape>() -> int {
-    int rc = set_smem((const void *)k_grid_rhs<Rl, Shape>, sm);
+    auto kern = longrows ? k_grid_rhs_long<Rl, Shape> : k_grid_rhs<Rl, Shape>;
+    int rc = set_smem((const void *)kern, sm);
     if (rc) return rc;
     {
-      PFSH_LAUNCH("k_grid_rhs", s);
+      PFSH_LAUNCH(longrows ? "k_grid_rhs_long" : "k_grid_rhs", s);
       if (pdl) {
-        cudaError_t e = launch_pdl(k_grid_rhs<Rl, Shape>, dim3(p->nh, B), dim3(256), sm, s, f, p->T, p->nlat, B,
-                                   (const C *)p->F, rowf, tw, (C *)p->H);
+        cudaError_t e = launch_pdl(kern, dim3(p->nh, B), dim3(256), sm, s, f, p->T, p->nlat, B, (const C *)p->F,
+                                   rowf, tw, (C *)p->H);
         if (e != cudaSuccess) return cuda_fail(e, "k_grid_rhs");
       } else {
-        k_grid_rhs<Rl, Shape><<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw,
-                                                              (C *)p->H);
+        kern<<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw, (C *)p->H);
       }
     }
     PFSH_CHECK_LAUNCH("k_grid_rhs");

@@ -253,6 +253,68 @@ typedef ShapeCT<1536, 16, 16, 2, 3> Shape1536;
 typedef ShapeCT<1920, 16, 8, 3, 5> Shape1920;
 typedef ShapeCT<3840, 16, 16, 3, 5> Shape3840;
 
+// Row means of NF padded transforms in `o` (elements sidx(k), k < N):
+// subtracted in place, and stashed in the last slot (NP - 1) of each
+// transform of both `o` and `g`, which the passes never touch, so that the
+// unpack of the forward transform can add N * mean back to wavenumber 0
+// whichever buffer the result lands in.  `g` is free on entry (the first
+// nwarps * NF elements serve as reduction scratch).  Removing the mean keeps
+// the rounding of a large zonal mean out of the other wavenumbers: the last
+// Stockham pass of radix R mixes wavenumbers j + q N/R, and with R = 5
+// (nlon = 1920, 3840) those land inside the retained band, where the
+// derivatives of the assembly amplify them.
+template <typename C, int NF>
+__device__ __forceinline__ void subtract_row_means(C *o, C *g, int N, int NP) {
+  typedef decltype(o[0].x) R;
+  R sx[NF], sy[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) sx[f] = sy[f] = (R)0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const int e = sidx(k);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      const C v = o[f * NP + e];
+      sx[f] += v.x;
+      sy[f] += v.y;
+    }
+  }
+#pragma unroll
+  for (int f = 0; f < NF; ++f)
+#pragma unroll
+    for (int d = 16; d > 0; d >>= 1) {
+      sx[f] += __shfl_xor_sync(0xffffffffu, sx[f], d);
+      sy[f] += __shfl_xor_sync(0xffffffffu, sy[f], d);
+    }
+  const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0)
+#pragma unroll
+    for (int f = 0; f < NF; ++f) g[warp * NF + f] = mk<C>(sx[f], sy[f]);
+  __syncthreads();
+  C mean[NF];
+#pragma unroll
+  for (int f = 0; f < NF; ++f) {
+    R ax = (R)0, ay = (R)0;
+    for (int w = 0; w < nw; ++w) {
+      ax += g[w * NF + f].x;
+      ay += g[w * NF + f].y;
+    }
+    mean[f] = mk<C>(ax / (R)N, ay / (R)N);
+  }
+  __syncthreads();
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const int e = sidx(k);
+#pragma unroll
+    for (int f = 0; f < NF; ++f) o[f * NP + e] = o[f * NP + e] - mean[f];
+  }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int f = 0; f < NF; ++f) {
+      o[f * NP + NP - 1] = mean[f];
+      g[f * NP + NP - 1] = mean[f];
+    }
+  __syncthreads();
+}
+
 // RHS grid stage for one latitude pair (j, nlat-1-j) of state b: 4 spectra
 // (eta, Phi', U, V) -> inverse FFTs -> products
 //   A1 = eta U/(1-mu^2), B1 = eta V/(1-mu^2), A2 = Phi' U/(1-mu^2),
@@ -301,6 +363,7 @@ __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat,
     o[4 * NP + e] = mk<C>((U.x * U.x + V.x * V.x) * h, (U.y * U.y + V.y * V.y) * h);
   }
   __syncthreads();
+  subtract_row_means<C, 5>(o, g, N, NP);
   C *Z = Shape::run(f, o, g, 5, tw, false);
   const Rl half = (Rl)0.5 / (Rl)N;
   const Rl wj = rowf[2 * j + 1];
@@ -310,6 +373,11 @@ __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat,
     const C *z = Z + fld * NP;
     C zm = z[sidx(m)];
     C zc = cconj(z[sidx(m == 0 ? 0 : N - m)]);
+    if (m == 0) {                           // the row mean taken out before the transform
+      const C dc = (Rl)N * z[NP - 1];
+      zm = zm + dc;
+      zc = zc + cconj(dc);
+    }
     C gn = half * (zm + zc);
     C gs = half * times_i(zc - zm);
     C he = wj * (gn + gs), ho = wj * (gn - gs);
@@ -317,6 +385,84 @@ __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat,
     H[(((size_t)m * 2 + 1) * nh + j) * colsH + b * 5 + fld] = ho;
   }
   __syncthreads();
+}
+
+// The same grid stage for long rows (shared memory for 6 instead of 10
+// padded transforms): the 4 inverse transforms stay resident in G, then the
+// 5 products are formed, transformed and unpacked one after the other in the
+// two work buffers W0/W1.  Same arithmetic per element as grid_rhs_body.
+template <typename Rl, typename Shape>
+__device__ __forceinline__ void grid_rhs_body_long(const FftArgs &f, int T, int nlat, int B, int j, int b,
+                                                   const typename cpx<Rl>::t *__restrict__ F,
+                                                   const Rl *__restrict__ rowf,
+                                                   const typename cpx<Rl>::t *__restrict__ tw,
+                                                   typename cpx<Rl>::t *__restrict__ H, typename cpx<Rl>::t *smem) {
+  typedef typename cpx<Rl>::t C;
+  const int N = Shape::n(f), NP = padded(N);
+  C *G = smem;             // 4 padded transforms
+  C *W0 = G + 4 * NP, *W1 = W0 + NP;
+  const int js = nlat - 1 - j;
+  const int colsF = 4 * B, colsH = 5 * B;
+  for (int fld = 0; fld < 4; ++fld) {
+    C *z = G + fld * NP;
+    for (int t = threadIdx.x; t < NP; t += blockDim.x) z[t] = mk<C>(0.0, 0.0);
+    __syncthreads();
+    for (int m = threadIdx.x; m <= T; m += blockDim.x) {
+      C fn = F[((size_t)m * nlat + j) * colsF + b * 4 + fld];
+      C fs = F[((size_t)m * nlat + js) * colsF + b * 4 + fld];
+      if (m == 0) {
+        z[0] = mk<C>(fn.x, fs.x);
+      } else {
+        z[sidx(m)] = mk<C>(fn.x - fs.y, fn.y + fs.x);
+        z[sidx(N - m)] = mk<C>(fn.x + fs.y, -fn.y + fs.x);
+      }
+    }
+    __syncthreads();
+    C *r = Shape::run(f, z, W0, 1, tw, true);
+    if (r != z) {
+      for (int k = threadIdx.x; k < N; k += blockDim.x) z[sidx(k)] = r[sidx(k)];
+      __syncthreads();
+    }
+  }
+  const Rl inv = rowf[2 * j];                // 1/(1 - mu_j^2)
+  const Rl h = (Rl)0.5 * inv;
+  const Rl half = (Rl)0.5 / (Rl)N;
+  const Rl wj = rowf[2 * j + 1];
+  const int nh = nlat / 2;
+  for (int fld = 0; fld < 5; ++fld) {
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+      const int e = sidx(k);
+      const C eta = G[e], php = G[NP + e], U = G[2 * NP + e], V = G[3 * NP + e];
+      const Rl Ui = U.x * inv, Us = U.y * inv, Vi = V.x * inv, Vs = V.y * inv;
+      C o;
+      switch (fld) {
+        case 0: o = mk<C>(eta.x * Ui, eta.y * Us); break;
+        case 1: o = mk<C>(eta.x * Vi, eta.y * Vs); break;
+        case 2: o = mk<C>(php.x * Ui, php.y * Us); break;
+        case 3: o = mk<C>(php.x * Vi, php.y * Vs); break;
+        default: o = mk<C>((U.x * U.x + V.x * V.x) * h, (U.y * U.y + V.y * V.y) * h); break;
+      }
+      W0[e] = o;
+    }
+    __syncthreads();
+    subtract_row_means<C, 1>(W0, W1, N, NP);
+    const C *Z = Shape::run(f, W0, W1, 1, tw, false);
+    for (int m = threadIdx.x; m <= T; m += blockDim.x) {
+      C zm = Z[sidx(m)];
+      C zc = cconj(Z[sidx(m == 0 ? 0 : N - m)]);
+      if (m == 0) {
+        const C dc = (Rl)N * Z[NP - 1];
+        zm = zm + dc;
+        zc = zc + cconj(dc);
+      }
+      C gn = half * (zm + zc);
+      C gs = half * times_i(zc - zm);
+      C he = wj * (gn + gs), ho = wj * (gn - gs);
+      H[(((size_t)m * 2 + 0) * nh + j) * colsH + b * 5 + fld] = he;
+      H[(((size_t)m * 2 + 1) * nh + j) * colsH + b * 5 + fld] = ho;
+    }
+    __syncthreads();
+  }
 }
 
 // Radix list of the compile-time shape serving N (must match the typedefs

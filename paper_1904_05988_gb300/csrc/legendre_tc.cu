@@ -364,6 +364,7 @@ int synth_tc(const sht_plan *p, int cols, cudaStream_t s) {
   float *F = (float *)p->F;
   switch (p->prec) {
     case PFSH_BF16: return launch_tc<false, false, false>(p, p->tc[0], cols, X, F, s, "k_synth_bf16");
+    case PFSH_FP16: return launch_tc<false, true, false>(p, p->tc[0], cols, X, F, s, "k_synth_fp16");
     case PFSH_BF16X3: return launch_tc<true, false, false>(p, p->tc[0], cols, X, F, s, "k_synth_bf16x3");
     default: return fail(PFSH_EUNSUPPORTED, "synth_tc: precision");
   }
@@ -374,6 +375,7 @@ int analysis_tc(const sht_plan *p, int cols, cudaStream_t s) {
   float *Y = (float *)p->Y;
   switch (p->prec) {
     case PFSH_BF16: return launch_tc<false, false, true>(p, p->tc[1], cols, H, Y, s, "k_anal_bf16");
+    case PFSH_FP16: return launch_tc<false, true, true>(p, p->tc[1], cols, H, Y, s, "k_anal_fp16");
     case PFSH_BF16X3: return launch_tc<true, false, true>(p, p->tc[1], cols, H, Y, s, "k_anal_bf16x3");
     default: return fail(PFSH_EUNSUPPORTED, "analysis_tc: precision");
   }

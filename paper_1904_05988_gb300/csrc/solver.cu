@@ -146,6 +146,9 @@ extern "C" int swe_ctx_create(swe_ctx **out, sht_plan *plan, const swe_params *p
   if (!out || !plan || !prm) return fail(PFSH_EINVAL, "swe_ctx_create: NULL argument");
   if (!(prm->a > 0) || !(prm->nu >= 0)) return fail(PFSH_EINVAL, "swe_ctx_create: need a > 0, nu >= 0");
   if (plan->max_batch < 5) return fail(PFSH_EINVAL, "swe_ctx_create: plan max_batch must be >= 5");
+  if (plan->prec == PFSH_FP16)
+    return fail(PFSH_EUNSUPPORTED, "swe_ctx_create: the FP16 form serves transforms only (the flux products "
+                                   "of the right-hand side exceed the fp16 range)");
   swe_ctx *c = new (std::nothrow) swe_ctx();
   if (!c) return fail(PFSH_ENOMEM, "swe_ctx_create");
   c->plan = plan;

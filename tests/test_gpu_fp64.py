@@ -115,6 +115,27 @@ def test_swe_rhs_t255_full_grid():
     assert rel(fE.cpu().numpy()[1], pack(FE, T)) < RHS_TOL
 
 
+def test_swe_rhs_t511_long_rows():
+    """T511 on 768 x 1536 in FP64: ten padded transforms of 1536 points exceed
+    the shared memory of a block, so the grid stage takes the long-row kernel
+    (products transformed one after the other).  Batched path (3 states) and
+    batch-1 path (1 state) against the oracle on the same state."""
+    T = 511
+    nlat, nlon = syn.gaussian_grid_size(T)
+    plan = ps.sht_plan_create(T, nlat, nlon, 15, "fp64")
+    ctx = ps.swe_ctx_create(plan, A, OM, syn.NU, PHIBAR)
+    st = state_of(T, 511, 3)
+    fE3 = torch.empty((3, 3, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    fE1 = torch.empty((1, 3, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    ps.swe_rhs(ctx, cuda(st), fE3, None)
+    ps.swe_rhs(ctx, cuda(st[:1]), fE1, None)
+    ps.pfsh_sync_status()
+    p = SWEParams(a=A, omega=OM, g=G, nu=syn.NU, phibar=PHIBAR)
+    FE, _ = rhs(unpack(st[0], T), SHT(T, nlat, nlon), p)
+    assert rel(fE3.cpu().numpy()[0], pack(FE, T)) < RHS_TOL
+    assert rel(fE1.cpu().numpy()[0], pack(FE, T)) < RHS_TOL
+
+
 def test_balanced_jet_is_steady_on_gpu():
     T = 63
     nlat, nlon = syn.gaussian_grid_size(T)

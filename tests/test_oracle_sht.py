@@ -11,7 +11,7 @@ import numpy as np
 import pytest
 from scipy.special import lpmv
 
-from oracle.sht import SHT, gauss_legendre, legendre_table, pack, unpack, area_mean_square
+from oracle.sht import synthesis_rows, SHT, gauss_legendre, legendre_table, pack, unpack, area_mean_square
 import synthetic as syn
 
 
@@ -137,6 +137,20 @@ def test_synthesis_matches_brute_force_sum(T):
     c = unpack(syn.random_spectrum(T, (1,), seed=11, nmin=0)[0], T)
     g = s.synthesis(c)
     ref = brute_force_synthesis(c, T, s.mu, s.lam)
+    assert np.max(np.abs(g - ref)) < 1e-13 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("T", [7, 15])
+def test_synthesis_rows_match_brute_force_sum_at_arbitrary_latitudes(T):
+    """Rows at points that are not Gaussian latitudes (the table is built for
+    the requested mu alone) against the brute-force double sum."""
+    nlon = 4 * (T + 1)
+    mu = np.array([0.93, -0.41, 0.05, -0.999])
+    lam = 2.0 * np.pi * np.arange(nlon) / nlon
+    c = unpack(syn.random_spectrum(T, (1,), seed=12, nmin=0)[0], T)
+    g = synthesis_rows(c, mu, nlon)
+    ref = brute_force_synthesis(c, T, mu, lam)
+    assert g.shape == (mu.size, nlon)
     assert np.max(np.abs(g - ref)) < 1e-13 * np.max(np.abs(ref))
 
 
