@@ -143,14 +143,26 @@ def initial_state(ps, torch, dev, seed: int):
 
 
 def time_iterations(ps, torch, pf, stream, steps: int) -> float:
-    """Device time (ms) of `steps` back-to-back iterations on `stream`."""
+    """Device time (ms) of one block of `steps` iterations on `stream` (one
+    CUDA-graph launch once the block has been captured)."""
     e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     e0.record(stream)
-    for _ in range(steps):
-        ps.pfasst_iteration(pf, False)
+    ps.pfasst_iterations(pf, steps, False)
     e1.record(stream)
     torch.cuda.synchronize()
     return e0.elapsed_time(e1)
+
+
+def prepare_block(ps, pf, steps: int, warmup: int) -> int:
+    """Untimed: `warmup` single iterations, then the block of `steps`
+    iterations twice (its first call runs eagerly, the second records the
+    graph that the timed call replays).  Returns the iterations run."""
+    for _ in range(warmup):
+        ps.pfasst_iteration(pf, False)
+    for _ in range(2):
+        ps.pfasst_iterations(pf, steps, False)
+    ps.pfsh_sync_status()
+    return warmup + 2 * steps
 
 
 def block_solve(ps, torch, pf, h_in, h_out, d_in, d_out):
@@ -159,8 +171,7 @@ def block_solve(ps, torch, pf, h_in, h_out, d_in, d_out):
     d_in.copy_(h_in, non_blocking=True)
     ps.pfasst_set_initial(pf, d_in)
     ps.pfasst_predict(pf)
-    for k in range(NPF):
-        ps.pfasst_iteration(pf, k == NPF - 1)
+    ps.pfasst_iterations(pf, NPF, True)
     ps.pfasst_get(pf, 0, NTS - 1, NF - 1, d_out)
     h_out.copy_(d_out, non_blocking=True)
 
@@ -192,9 +203,7 @@ def run_ours(args, rank, world, local_rank):
     stream = torch.cuda.current_stream()
     ps.pfasst_set_initial(pf, d_st0)
     ps.pfasst_predict(pf)
-    for _ in range(args.warmup):
-        ps.pfasst_iteration(pf, False)
-    ps.pfsh_sync_status()
+    warmup_run = prepare_block(ps, pf, args.steps, args.warmup)
 
     # ---- timed region: K iterations of Algorithm 1 over all slices ----
     clocks = ClockSampler(local_rank)
@@ -240,8 +249,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- profiled pass (same workload, separate from the timed region) ----
     ps.pfsh_profiler_enable(True)
-    for _ in range(2):
-        ps.pfasst_iteration(pf, False)
+    ps.pfasst_iterations(pf, 2, False)
     ps.pfsh_profiler_enable(False)
     prof = ps.pfsh_profiler_report()
     rooflines = rooflines_of(prof, args.prec, 2)
@@ -252,7 +260,8 @@ def run_ours(args, rank, world, local_rank):
     d_in = torch.empty_like(d_st0)
     d_out = torch.empty_like(d_st0)
     blocks = max(1, min(3, args.steps))
-    block_solve(ps, torch, pf, h_in, h_out, d_in, d_out)
+    for _ in range(2):   # eager run, graph capture
+        block_solve(ps, torch, pf, h_in, h_out, d_in, d_out)
     torch.cuda.synchronize()
     b0, b1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
     b0.record(stream)
@@ -274,9 +283,8 @@ def run_ours(args, rank, world, local_rank):
         pf64 = make("fp64")
         ps.pfasst_set_initial(pf64, d_st0)
         ps.pfasst_predict(pf64)
-        for _ in range(3):
-            ps.pfasst_iteration(pf64, False)
         k64 = max(2, min(5, args.steps))
+        prepare_block(ps, pf64, k64, 1)
         ms64 = time_iterations(ps, torch, pf64, stream, k64) / k64
         block_solve(ps, torch, pf64, h_in, h_out, d_in, d_out)
         torch.cuda.synchronize()
@@ -301,11 +309,13 @@ def run_ours(args, rank, world, local_rank):
             "metric": "PFASST iterations/s (T255/T127, 32 slices, 5/3 nodes), mixed precision vs FP64 GPU path; "
                       "SWE RHS evals/s at T255",
             "value": value, "unit": "PFASST iterations/s", "n_gpus": world, "steps": args.steps,
-            "warmup": args.warmup, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
+            "warmup": warmup_run, "ms_per_step": ms_per_step, "higher_is_better": True, "scaling": "weak",
             "vs_baseline": None, "dtype": dtype, "data": "synthetic",
             "config": {"workload": WORKLOAD, "n_ts": NTS, "nodes": [NF, NC], "T": [TF, TC],
                        "grid": [list(GRID_F), list(GRID_C)], "dt": DT, "prec": args.prec,
-                       "parallelism": f"replicas x{world}", "l2": "working set 1.6 GB > 129 MB L2"},
+                       "parallelism": f"replicas x{world}", "l2": "working set 1.6 GB > 129 MB L2",
+                       "timed": f"one pfasst_iterations block of {args.steps} iterations (one CUDA-graph launch, "
+                                "slice groups in a wavefront across iterations)"},
             "swe_rhs_evals_per_s": rhs_per_s,
             "fp64_gpu_path": fp64,
             "e2e": {"value": e2e_val, "unit": "PFASST iterations/s", "h2d_bytes_per_step": state_bytes,

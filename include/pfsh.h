@@ -211,6 +211,14 @@ int pfasst_predict(pfasst *pf, pfsh_stream_t stream);
  * work is complete, so stream order for the caller is unchanged. */
 int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream);
 
+/* `count` consecutive PFASST iterations (Algorithm 1), the last of them Step A
+ * only when last != 0; the same results as `count` calls of pfasst_iteration.
+ * Within the block the slice groups form a wavefront across iterations: the
+ * fine sweep of group g in iteration k+1 starts as soon as the coarse chain
+ * of group g in iteration k has finished, beside the chain of the later
+ * groups.  Stream semantics as pfasst_iteration.  EINVAL if count < 1. */
+int pfasst_iterations(pfasst *pf, int count, int last, pfsh_stream_t stream);
+
 /* Copy one node of one slice to `out` (device, [3][ncoef][2]); level 0 =
  * fine, 1 = coarse. */
 int pfasst_get(pfasst *pf, int level, int slice, int node, double *out,

@@ -28,7 +28,7 @@ EXPORTED = ["sht_plan_create", "sht_plan_destroy", "sht_plan_query", "sht_invers
             "swe_ctx_create", "swe_ctx_destroy", "swe_rhs", "swe_implicit_solve",
             "sdc_level_create", "sdc_level_destroy", "sdc_spread", "sdc_sweep",
             "pfasst_create", "pfasst_destroy", "pfasst_set_initial", "pfasst_predict",
-            "pfasst_iteration", "pfasst_get", "pfsh_sync_status", "pfsh_last_error",
+            "pfasst_iteration", "pfasst_iterations", "pfasst_get", "pfsh_sync_status", "pfsh_last_error",
             "pfsh_kernel_launches", "pfsh_profiler_enable", "pfsh_profiler_report", "sht_inverse_noalloc"]
 
 
@@ -85,6 +85,7 @@ _sig = {
     "pfasst_set_initial": [c_void_p, c_void_p, c_void_p],
     "pfasst_predict": [c_void_p, c_void_p],
     "pfasst_iteration": [c_void_p, c_int, c_void_p],
+    "pfasst_iterations": [c_void_p, c_int, c_int, c_void_p],
     "pfasst_get": [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p],
     "pfsh_sync_status": [c_void_p],
     "sht_inverse_noalloc": [c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p],
@@ -298,6 +299,10 @@ def pfasst_predict(pf: Pfasst, stream=None) -> None:
 
 def pfasst_iteration(pf: Pfasst, last: bool = False, stream=None) -> None:
     _check(_lib.pfasst_iteration(pf.ptr, 1 if last else 0, _stream(stream)))
+
+
+def pfasst_iterations(pf: Pfasst, count: int, last: bool = False, stream=None) -> None:
+    _check(_lib.pfasst_iterations(pf.ptr, count, 1 if last else 0, _stream(stream)))
 
 
 def pfasst_get(pf: Pfasst, level: int, slice_: int, node: int, out: torch.Tensor, stream=None) -> torch.Tensor:

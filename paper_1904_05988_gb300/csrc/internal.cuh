@@ -240,11 +240,15 @@ struct pfasst {
   double *base_c;             // [n_ts][coarse state] restricted initial value
   double *theta0;             // [fine state]
   double Rt[16][16], Pt[16][16];   // time restriction / interpolation
-  // CUDA-graph replay of pfasst_iteration ([0] full iteration, [1] last)
+  // CUDA graphs of iteration blocks, keyed by (iterations, last)
+  struct GraphEntry {
+    int count = 0, last = 0, calls = 0;
+    cudaGraphExec_t exec = nullptr;
+    unsigned long long launches = 0;
+  };
+  static constexpr int kMaxGraphs = 8;
+  GraphEntry graph_cache[kMaxGraphs];
   cudaStream_t cap_stream = nullptr;
-  cudaGraphExec_t gexec[2] = {nullptr, nullptr};
-  int calls[2] = {0, 0};
-  unsigned long long glaunches[2] = {0, 0};
   bool graphs = true;
   // Step C runs on its own stream with its own coarse plan/context/level so
   // that it overlaps Steps A and B of later slice groups (see pfasst.cu).
@@ -254,7 +258,7 @@ struct pfasst {
   sht_plan *plan_cc = nullptr;
   swe_ctx *ctx_cc = nullptr;
   sdc_level *lev_cc = nullptr;
-  cudaEvent_t ev_fork = nullptr, ev_B[kMaxGroups] = {}, ev_C[kMaxGroups] = {};
+  cudaEvent_t ev_fork = nullptr, ev_B[kMaxGroups] = {}, ev_C[kMaxGroups] = {}, ev_R[kMaxGroups] = {};
 };
 
 namespace pfsh {
@@ -334,7 +338,8 @@ void lagrange_matrix(const double *src, int ns, const double *dst, int nd, doubl
 // Step C of Algorithm 1 for slices n0..n1-1 with fused per-order launches
 // (small.cu); strides in doubles
 int chain_sweeps(sdc_level *l, double *th, double *fe, double *fi, const double *tau, size_t node_stride,
-                 size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s);
+                 size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s,
+                 cudaEvent_t after_first = nullptr);
 
 // PFASST transfer kernels
 int restrict_launch(const double *Rt, int nf, int nc, const double *xf, size_t fstride,

@@ -172,14 +172,15 @@ static void pf_free(pfasst *pf) {
                     pf->fe_cs, pf->fi_cs, pf->tau, pf->sent, pf->base_c, pf->theta0};
   for (double *b : bufs)
     if (b) cudaFree(b);
-  for (int i = 0; i < 2; ++i)
-    if (pf->gexec[i]) cudaGraphExecDestroy(pf->gexec[i]);
+  for (auto &e : pf->graph_cache)
+    if (e.exec) cudaGraphExecDestroy(e.exec);
   if (pf->cap_stream) cudaStreamDestroy(pf->cap_stream);
   if (pf->chain_stream) cudaStreamDestroy(pf->chain_stream);
   if (pf->ev_fork) cudaEventDestroy(pf->ev_fork);
   for (int g = 0; g < pfasst::kMaxGroups; ++g) {
     if (pf->ev_B[g]) cudaEventDestroy(pf->ev_B[g]);
     if (pf->ev_C[g]) cudaEventDestroy(pf->ev_C[g]);
+    if (pf->ev_R[g]) cudaEventDestroy(pf->ev_R[g]);
   }
   sdc_level_destroy(pf->lev_cc);
   swe_ctx_destroy(pf->ctx_cc);
@@ -234,7 +235,7 @@ extern "C" int pfasst_create(pfasst **out, const pfasst_config *cfg) {
                 {&pf->fe_c, (size_t)(pf->Mc + 1) * nts * pf->sc}, {&pf->fi_c, (size_t)(pf->Mc + 1) * nts * pf->sc},
                 {&pf->th_cs, (size_t)(pf->Mc + 1) * nts * pf->sc}, {&pf->fe_cs, (size_t)(pf->Mc + 1) * nts * pf->sc},
                 {&pf->fi_cs, (size_t)(pf->Mc + 1) * nts * pf->sc}, {&pf->tau, (size_t)(pf->Mc + 1) * nts * pf->sc},
-                {&pf->sent, (size_t)nts * pf->sf},                {&pf->base_c, (size_t)nts * pf->sc},
+                {&pf->sent, (size_t)2 * nts * pf->sf},            {&pf->base_c, (size_t)nts * pf->sc},
                 {&pf->theta0, pf->sf}};
   for (auto &a : allocs) {
     if (cudaMalloc(a.p, a.n * sizeof(double)) != cudaSuccess) {
@@ -251,7 +252,8 @@ extern "C" int pfasst_create(pfasst **out, const pfasst_config *cfg) {
             cudaEventCreateWithFlags(&pf->ev_fork, cudaEventDisableTiming) == cudaSuccess;
   for (int g = 0; ok && g < pfasst::kMaxGroups; ++g)
     ok = cudaEventCreateWithFlags(&pf->ev_B[g], cudaEventDisableTiming) == cudaSuccess &&
-         cudaEventCreateWithFlags(&pf->ev_C[g], cudaEventDisableTiming) == cudaSuccess;
+         cudaEventCreateWithFlags(&pf->ev_C[g], cudaEventDisableTiming) == cudaSuccess &&
+         cudaEventCreateWithFlags(&pf->ev_R[g], cudaEventDisableTiming) == cudaSuccess;
   if (!ok) {
     cudaGetLastError();
     pf_free(pf);
@@ -339,7 +341,7 @@ extern "C" int pfasst_predict(pfasst *pf, pfsh_stream_t stream) {
 
 // Steps A and B for slices [g0, g0 + cnt): fine sweep, send, restriction,
 // coarse F at every node, saved copies, FAS correction.
-static int steps_AB(pfasst *pf, int g0, int cnt, cudaStream_t s) {
+static int steps_AB(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
   const pfasst_config &c = pf->cfg;
   const int nts = c.n_ts, Mc = pf->Mc, Mf = pf->Mf;
   const size_t sc = pf->sc, sf = pf->sf;
@@ -348,7 +350,7 @@ static int steps_AB(pfasst *pf, int g0, int cnt, cudaStream_t s) {
   if ((rc = sdc_sweep_strided(pf->lev_f, pf->th_f + g0 * sf, pf->fe_f + g0 * sf, pf->fi_f + g0 * sf, nullptr, fnode,
                               cnt, s)))
     return rc;
-  PFSH_CUDA(cudaMemcpyAsync(pf->sent + g0 * sf, pf->th_f + Mf * fnode + g0 * sf, cnt * sf * 8,
+  PFSH_CUDA(cudaMemcpyAsync(pf->sent + (par * nts + g0) * sf, pf->th_f + Mf * fnode + g0 * sf, cnt * sf * 8,
                             cudaMemcpyDeviceToDevice, s));
   {
     double R[16 * 16];
@@ -394,14 +396,15 @@ static int steps_AB(pfasst *pf, int g0, int cnt, cudaStream_t s) {
 
 // Step C for slices [g0, g0 + cnt) in slice order: receive slice n-1's coarse
 // end value (with its right-hand sides), one coarse sweep with the FAS term.
-static int step_C(pfasst *pf, int g0, int cnt, cudaStream_t s) {
+static int step_C(pfasst *pf, int g0, int cnt, cudaStream_t s, cudaEvent_t received) {
   const size_t sc = pf->sc, cnode = (size_t)pf->cfg.n_ts * sc;
-  return chain_sweeps(pf->lev_cc, pf->th_c, pf->fe_c, pf->fi_c, pf->tau, cnode, sc, g0, g0 + cnt, g0 > 0, s);
+  return chain_sweeps(pf->lev_cc, pf->th_c, pf->fe_c, pf->fi_c, pf->tau, cnode, sc, g0, g0 + cnt, g0 > 0, s,
+                      received);
 }
 
 // Step D for slices [g0, g0 + cnt): interpolate the coarse increments into
 // fine nodes >= 1, new fine initial values (slices >= 1), fine node-0 F.
-static int step_D(pfasst *pf, int g0, int cnt, cudaStream_t s) {
+static int step_D(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
   const pfasst_config &c = pf->cfg;
   const int nts = c.n_ts, Mc = pf->Mc, Mf = pf->Mf;
   const size_t sc = pf->sc, sf = pf->sf;
@@ -425,7 +428,7 @@ static int step_D(pfasst *pf, int g0, int cnt, cudaStream_t s) {
     dim3 g0d((ncoef_of(c.Tf) + 255) / 256, cnt - first);
     {
       PFSH_LAUNCH("k_node0", s);
-      k_node0<<<g0d, 256, 0, s>>>(c.Tf, c.Tc, first, (const double2 *)(pf->sent + g0 * sf),
+      k_node0<<<g0d, 256, 0, s>>>(c.Tf, c.Tc, first, (const double2 *)(pf->sent + ((size_t)par * nts + g0) * sf),
                                   (const double2 *)(pf->th_c + g0 * sc), (double2 *)(pf->th_f + g0 * sf));
     }
     PFSH_CHECK_LAUNCH("k_node0");
@@ -433,10 +436,20 @@ static int step_D(pfasst *pf, int g0, int cnt, cudaStream_t s) {
   return rhs_eval(pf->ctx_f, pf->th_f + g0 * sf, pf->fe_f + g0 * sf, pf->fi_f + g0 * sf, cnt, s);
 }
 
-static int iteration_body(pfasst *pf, int last, cudaStream_t s) {
+// `count` iterations of Algorithm 1, the last of them Step A only when
+// `last`.  Steps A/B of slice group g run on `s`, Step C of every group on
+// the chain stream, Step D of group g on `s` again.  Across iterations the
+// groups form a wavefront: Steps D/A/B of group g in iteration k+1 wait only
+// for Step C of group g in iteration k (and Step B of group g also for the
+// receive of group g+1 in iteration k, whose first launch reads group g's
+// last slice), so the fine sweeps of the early groups of iteration k+1 run
+// beside the coarse chain of the late groups of iteration k.  The values
+// sent in Step A are double-buffered by iteration parity because Step D of
+// group g+1 in iteration k reads them after Step A of group g in iteration
+// k+1 has run.
+static int block_body(pfasst *pf, int count, int last, cudaStream_t s) {
   const int nts = pf->cfg.n_ts;
-  if (last)   // the last iteration ends after the fine sweep (Step A)
-    return sdc_sweep_strided(pf->lev_f, pf->th_f, pf->fe_f, pf->fi_f, nullptr, (size_t)nts * pf->sf, nts, s);
+  const int nfull = count - (last ? 1 : 0);
   const int G = pf->groups;
   auto group = [&](int g, int *g0, int *cnt) {
     *g0 = (int)((long)nts * g / G);
@@ -445,64 +458,95 @@ static int iteration_body(pfasst *pf, int last, cudaStream_t s) {
   // with the event profiler on, everything runs on `s` so that per-launch
   // durations are not stretched by the overlap
   cudaStream_t cs = profiler_on() ? s : pf->chain_stream;
-  PFSH_CUDA(cudaEventRecord(pf->ev_fork, s));
-  PFSH_CUDA(cudaStreamWaitEvent(cs, pf->ev_fork, 0));
   int rc, g0, cnt;
-  for (int g = 0; g < G; ++g) {
-    group(g, &g0, &cnt);
-    if ((rc = steps_AB(pf, g0, cnt, s))) return rc;
-    PFSH_CUDA(cudaEventRecord(pf->ev_B[g], s));
-    PFSH_CUDA(cudaStreamWaitEvent(cs, pf->ev_B[g], 0));
-    if ((rc = step_C(pf, g0, cnt, cs))) return rc;
-    PFSH_CUDA(cudaEventRecord(pf->ev_C[g], cs));
+  if (nfull > 0) {
+    PFSH_CUDA(cudaEventRecord(pf->ev_fork, s));
+    PFSH_CUDA(cudaStreamWaitEvent(cs, pf->ev_fork, 0));
   }
-  for (int g = 0; g < G; ++g) {
+  for (int it = 0; it < nfull; ++it) {
+    for (int g = 0; g < G; ++g) {
+      group(g, &g0, &cnt);
+      if (it > 0) {
+        PFSH_CUDA(cudaStreamWaitEvent(s, pf->ev_C[g], 0));
+        if ((rc = step_D(pf, g0, cnt, (it - 1) & 1, s))) return rc;
+        if (g + 1 < G) PFSH_CUDA(cudaStreamWaitEvent(s, pf->ev_R[g + 1], 0));
+      }
+      if ((rc = steps_AB(pf, g0, cnt, it & 1, s))) return rc;
+      PFSH_CUDA(cudaEventRecord(pf->ev_B[g], s));
+      PFSH_CUDA(cudaStreamWaitEvent(cs, pf->ev_B[g], 0));
+      if ((rc = step_C(pf, g0, cnt, cs, g > 0 ? pf->ev_R[g] : nullptr))) return rc;
+      PFSH_CUDA(cudaEventRecord(pf->ev_C[g], cs));
+    }
+  }
+  for (int g = 0; nfull > 0 && g < G; ++g) {
     group(g, &g0, &cnt);
     PFSH_CUDA(cudaStreamWaitEvent(s, pf->ev_C[g], 0));
-    if ((rc = step_D(pf, g0, cnt, s))) return rc;
+    if ((rc = step_D(pf, g0, cnt, (nfull - 1) & 1, s))) return rc;
   }
+  if (last)   // the last iteration ends after the fine sweep (Step A)
+    return sdc_sweep_strided(pf->lev_f, pf->th_f, pf->fe_f, pf->fi_f, nullptr, (size_t)nts * pf->sf, nts, s);
   return PFSH_OK;
 }
 
-// The iteration is a fixed sequence of several hundred launches on fixed
-// buffers over two streams, so it is recorded once into a CUDA graph (on a
-// private capture stream, joined by the chain stream) and replayed on the
-// caller's stream; the first call of each kind runs eagerly,
-// which also sets every kernel attribute before capture.  Profiling or
+// A block of iterations is a fixed sequence of launches on fixed buffers
+// over two streams, so it is recorded once into a CUDA graph (on a private
+// capture stream, joined by the chain stream) per (count, last) and replayed
+// on the caller's stream; the first call of each kind runs eagerly, which
+// also sets every kernel attribute before capture.  Profiling or
 // PFSH_NO_GRAPH=1 keeps the eager path.
-extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
-  if (!pf) return fail(PFSH_EINVAL, "pfasst_iteration: NULL argument");
-  cudaStream_t s = (cudaStream_t)stream;
-  const int k = last ? 1 : 0;
-  if (!pf->graphs || profiler_on()) return iteration_body(pf, last, s);
-  if (pf->gexec[k]) {
-    PFSH_CUDA(cudaGraphLaunch(pf->gexec[k], s));
-    count_launches(pf->glaunches[k]);
+static int run_block(pfasst *pf, int count, int last, cudaStream_t s) {
+  if (!pf->graphs || profiler_on()) return block_body(pf, count, last, s);
+  pfasst::GraphEntry *e = nullptr;
+  for (auto &x : pf->graph_cache)
+    if (x.calls > 0 && x.count == count && x.last == last) e = &x;
+  if (!e) {
+    for (auto &x : pf->graph_cache)
+      if (x.calls == 0) {
+        e = &x;
+        break;
+      }
+    if (!e) return block_body(pf, count, last, s);   // cache full: eager
+    e->count = count;
+    e->last = last;
+  }
+  if (e->exec) {
+    PFSH_CUDA(cudaGraphLaunch(e->exec, s));
+    count_launches(e->launches);
     return PFSH_OK;
   }
-  if (pf->calls[k]++ == 0) return iteration_body(pf, last, s);
+  if (e->calls++ == 0) return block_body(pf, count, last, s);
   cudaGraph_t g = nullptr;
   PFSH_CUDA(cudaStreamBeginCapture(pf->cap_stream, cudaStreamCaptureModeThreadLocal));
   const unsigned long long n0 = launches_so_far();
-  int rc = iteration_body(pf, last, pf->cap_stream);
+  int rc = block_body(pf, count, last, pf->cap_stream);
   const unsigned long long n1 = launches_so_far();
-  cudaError_t e = cudaStreamEndCapture(pf->cap_stream, &g);
+  cudaError_t err = cudaStreamEndCapture(pf->cap_stream, &g);
   if (rc) {
     if (g) cudaGraphDestroy(g);
     return rc;
   }
-  if (e != cudaSuccess) return cuda_fail(e, "pfasst_iteration: cudaStreamEndCapture");
-  e = cudaGraphInstantiateWithFlags(&pf->gexec[k], g, cudaGraphInstantiateFlagUseNodePriority);
+  if (err != cudaSuccess) return cuda_fail(err, "pfasst: cudaStreamEndCapture");
+  err = cudaGraphInstantiateWithFlags(&e->exec, g, cudaGraphInstantiateFlagUseNodePriority);
   cudaGraphDestroy(g);
-  if (e != cudaSuccess) {
-    pf->gexec[k] = nullptr;
-    return cuda_fail(e, "pfasst_iteration: cudaGraphInstantiate");
+  if (err != cudaSuccess) {
+    e->exec = nullptr;
+    return cuda_fail(err, "pfasst: cudaGraphInstantiate");
   }
-  pf->glaunches[k] = n1 - n0;
+  e->launches = n1 - n0;
   g_launches_uncount(n1 - n0);
-  PFSH_CUDA(cudaGraphLaunch(pf->gexec[k], s));
-  count_launches(pf->glaunches[k]);
+  PFSH_CUDA(cudaGraphLaunch(e->exec, s));
+  count_launches(e->launches);
   return PFSH_OK;
+}
+
+extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
+  if (!pf) return fail(PFSH_EINVAL, "pfasst_iteration: NULL argument");
+  return run_block(pf, 1, last ? 1 : 0, (cudaStream_t)stream);
+}
+
+extern "C" int pfasst_iterations(pfasst *pf, int count, int last, pfsh_stream_t stream) {
+  if (!pf || count < 1) return fail(PFSH_EINVAL, "pfasst_iterations: NULL argument or count < 1");
+  return run_block(pf, count, last ? 1 : 0, (cudaStream_t)stream);
 }
 
 extern "C" int pfasst_get(pfasst *pf, int level, int slice, int node, double *out, pfsh_stream_t stream) {

@@ -215,7 +215,8 @@ static ChainGeo<R> chain_geo(const sht_plan *p, const swe_params &prm, const R *
 
 template <typename R>
 static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, double *fi, const double *tau,
-                       size_t node_stride, size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s) {
+                       size_t node_stride, size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s,
+                       cudaEvent_t after_first) {
   const swe_ctx *ctx = l->ctx;
   const sht_plan *p = ctx->plan;
   const int M = l->nodes - 1;
@@ -254,6 +255,7 @@ static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, doub
       }
       // the first launch of the chain follows other work of the stream
       if ((rc = chain_node_launch<R>(st, g, c, s, n > n0 || k > 1))) return rc;
+      if (after_first && n == n0 && k == 1) PFSH_CUDA(cudaEventRecord(after_first, s));
       if ((rc = grid_rhs(p, 1, ctx->prm, s, true))) return rc;
     }
   }
@@ -271,16 +273,18 @@ static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, doub
 // slice stride slice_stride, in doubles): slice n receives the last node of
 // slice n-1 (theta, F_E, F_I; for n = n0 only if recv_first) and performs one
 // sweep with its FAS term.  The level must hold one state (B = 1).
+// `after_first` (optional) is recorded after the first launch, which holds
+// the receive of slice n0: from then on slice n0-1 may be overwritten.
 int chain_sweeps(sdc_level *l, double *th, double *fe, double *fi, const double *tau, size_t node_stride,
-                 size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s) {
+                 size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s, cudaEvent_t after_first) {
   const sht_plan *p = l->ctx->plan;
   if (l->nodes - 1 > 8) return fail(PFSH_EUNSUPPORTED, "chain_sweeps: more than 9 nodes");
   const swe_params &prm = l->ctx->prm;
   if (p->prec == PFSH_FP64)
     return chain_typed<double>(l, chain_geo<double>(p, prm, p->d_P, SpecTables<double>{p->d_eps, p->d_ilap}), th,
-                               fe, fi, tau, node_stride, slice_stride, n0, n1, recv_first, s);
+                               fe, fi, tau, node_stride, slice_stride, n0, n1, recv_first, s, after_first);
   return chain_typed<float>(l, chain_geo<float>(p, prm, p->d_P32, SpecTables<float>{p->d_eps32, p->d_ilap32}), th,
-                            fe, fi, tau, node_stride, slice_stride, n0, n1, recv_first, s);
+                            fe, fi, tau, node_stride, slice_stride, n0, n1, recv_first, s, after_first);
 }
 
 }  // namespace pfsh

@@ -272,27 +272,38 @@ def test_pfasst_predict_and_iterations_match_oracle(Tf, Tc, nts, groups):
 @pytest.mark.parametrize("form", ["fp64", "bf16x3"])
 def test_pfasst_slice_groups_leave_results_unchanged(form):
     """The pipelined iteration (coarse chain of a slice group overlapping the
-    fine sweeps of the next groups) computes exactly what the one-group
-    iteration computes: same kernels, same batch paths, same order of
-    arithmetic per slice."""
+    fine sweeps of the next groups) and the wavefront block of iterations
+    (groups of iteration k+1 starting beside the chain of iteration k)
+    compute exactly what one-group single iterations compute: same kernels,
+    same batch paths, same order of arithmetic per slice.  The block is
+    checked eagerly, when captured into a graph and when replayed."""
     if form not in ps.available_precisions():
         pytest.skip(f"{form} not built")
     Tf, Tc, nts, dt = 63, 31, 12, 600.0
     gf, gc = syn.gaussian_grid_size(Tf), syn.gaussian_grid_size(Tc)
     st0 = cuda(state_of(Tf, 23)[0])
-    outs = []
-    for groups in (1, 3):
+
+    def run(groups, mode):
         pf = ps.pfasst_create(nts, 5, 3, Tf, *gf, Tc, *gc, dt, A, OM, syn.NU, PHIBAR, form, slice_groups=groups)
-        ps.pfasst_set_initial(pf, st0)
-        ps.pfasst_predict(pf)
-        for it in range(3):   # eager, graph capture, graph replay
-            ps.pfasst_iteration(pf, False)
-        ps.pfasst_iteration(pf, True)
+        rounds = 3 if mode == "block" else 1       # block: eager, capture, replay
+        for _ in range(rounds):
+            ps.pfasst_set_initial(pf, st0)
+            ps.pfasst_predict(pf)
+            if mode == "single":
+                for it in range(3):   # eager, graph capture, graph replay
+                    ps.pfasst_iteration(pf, False)
+                ps.pfasst_iteration(pf, True)
+            else:
+                ps.pfasst_iterations(pf, 4, True)
         res = torch.empty((nts, 5, 3, syn.ncoef(Tf)), dtype=torch.complex128, device=DEV)
         for n in range(nts):
             for k in range(5):
                 ps.pfasst_get(pf, 0, n, k, res[n, k])
         ps.pfsh_sync_status()
-        outs.append(res.cpu().numpy())
         pf.close()
-    assert np.array_equal(outs[0], outs[1])
+        return res.cpu().numpy()
+
+    ref = run(1, "single")
+    assert np.array_equal(ref, run(3, "single"))
+    assert np.array_equal(ref, run(3, "block"))
+    assert np.array_equal(ref, run(1, "block"))
