@@ -219,6 +219,21 @@ int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream);
  * groups.  Stream semantics as pfasst_iteration.  EINVAL if count < 1. */
 int pfasst_iterations(pfasst *pf, int count, int last, pfsh_stream_t stream);
 
+/* Ensembles of independent instances (uneven batches: members may differ in
+ * truncation, grid, nodes, slices and precision).  Every member is a full
+ * pfasst object (pfasst_ensemble_member returns it, e.g. for
+ * pfasst_set_initial and pfasst_get); predictor and iteration blocks of all
+ * members run concurrently, each member on its own stream pair, the
+ * iteration blocks captured into one CUDA graph per (count, last).  Results
+ * are those of the members run one by one.  The ensemble owns its members. */
+typedef struct pfasst_ensemble pfasst_ensemble;
+int pfasst_ensemble_create(pfasst_ensemble **out, const pfasst_config *cfgs, int n);
+int pfasst_ensemble_destroy(pfasst_ensemble *e);
+/* NULL (and pfsh_last_error set) if i is out of range. */
+pfasst *pfasst_ensemble_member(pfasst_ensemble *e, int i);
+int pfasst_ensemble_predict(pfasst_ensemble *e, pfsh_stream_t stream);
+int pfasst_ensemble_iterations(pfasst_ensemble *e, int count, int last, pfsh_stream_t stream);
+
 /* Copy one node of one slice to `out` (device, [3][ncoef][2]); level 0 =
  * fine, 1 = coarse. */
 int pfasst_get(pfasst *pf, int level, int slice, int node, double *out,

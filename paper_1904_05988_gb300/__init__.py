@@ -28,7 +28,9 @@ EXPORTED = ["sht_plan_create", "sht_plan_destroy", "sht_plan_query", "sht_invers
             "swe_ctx_create", "swe_ctx_destroy", "swe_rhs", "swe_implicit_solve",
             "sdc_level_create", "sdc_level_destroy", "sdc_spread", "sdc_sweep",
             "pfasst_create", "pfasst_destroy", "pfasst_set_initial", "pfasst_predict",
-            "pfasst_iteration", "pfasst_iterations", "pfasst_get", "pfsh_sync_status", "pfsh_last_error",
+            "pfasst_iteration", "pfasst_iterations", "pfasst_get", "pfasst_ensemble_create",
+            "pfasst_ensemble_destroy", "pfasst_ensemble_member", "pfasst_ensemble_predict",
+            "pfasst_ensemble_iterations", "pfsh_sync_status", "pfsh_last_error",
             "pfsh_kernel_launches", "pfsh_profiler_enable", "pfsh_profiler_report", "sht_inverse_noalloc"]
 
 
@@ -86,6 +88,10 @@ _sig = {
     "pfasst_predict": [c_void_p, c_void_p],
     "pfasst_iteration": [c_void_p, c_int, c_void_p],
     "pfasst_iterations": [c_void_p, c_int, c_int, c_void_p],
+    "pfasst_ensemble_create": [ctypes.POINTER(c_void_p), ctypes.POINTER(PfasstConfig), c_int],
+    "pfasst_ensemble_destroy": [c_void_p],
+    "pfasst_ensemble_predict": [c_void_p, c_void_p],
+    "pfasst_ensemble_iterations": [c_void_p, c_int, c_int, c_void_p],
     "pfasst_get": [c_void_p, c_int, c_int, c_int, c_void_p, c_void_p],
     "pfsh_sync_status": [c_void_p],
     "sht_inverse_noalloc": [c_int, c_int, c_int, c_void_p, c_void_p, c_int, c_void_p],
@@ -94,6 +100,8 @@ for _name, _args in _sig.items():
     _f = getattr(_lib, _name)
     _f.argtypes = _args
     _f.restype = c_int
+_lib.pfasst_ensemble_member.argtypes = [c_void_p, c_int]
+_lib.pfasst_ensemble_member.restype = c_void_p
 _lib.pfsh_last_error.argtypes = []
 _lib.pfsh_last_error.restype = ctypes.c_char_p
 _lib.pfsh_kernel_launches.argtypes = []
@@ -203,9 +211,33 @@ class SdcLevel(_Handle):
 class Pfasst(_Handle):
     _destroy = "pfasst_destroy"
 
-    def __init__(self, ptr: int, cfg: PfasstConfig):
+    def __init__(self, ptr: int, cfg: PfasstConfig, owner=None):
         super().__init__(ptr)
         self.cfg = cfg
+        self._owner = owner   # an ensemble member is destroyed with its ensemble
+
+    def close(self):
+        if self._owner is None:
+            super().close()
+        self.ptr = None
+
+
+class PfasstEnsemble(_Handle):
+    _destroy = "pfasst_ensemble_destroy"
+
+    def __init__(self, ptr: int, cfgs: list):
+        super().__init__(ptr)
+        self.members = []
+        for i, c in enumerate(cfgs):
+            m = _lib.pfasst_ensemble_member(ptr, i)
+            if not m:
+                raise PfshError(PFSH_EINVAL, last_error())
+            self.members.append(Pfasst(m, c, owner=self))
+
+    def close(self):
+        for m in getattr(self, "members", []):
+            m.ptr = None
+        super().close()
 
 
 # ---------------------------------------------------------------------------
@@ -281,9 +313,8 @@ def sdc_sweep(level: SdcLevel, theta: torch.Tensor, fE: torch.Tensor, fI: torch.
 def pfasst_create(n_ts: int, fine_nodes: int, coarse_nodes: int, Tf: int, nlat_f: int, nlon_f: int,
                   Tc: int, nlat_c: int, nlon_c: int, dt: float, a: float, omega: float, nu: float,
                   phibar: float, prec: int | str = PFSH_FP64, slice_groups: int = 0) -> Pfasst:
-    prec = PREC_NAMES[prec] if isinstance(prec, str) else prec
-    cfg = PfasstConfig(n_ts, fine_nodes, coarse_nodes, Tf, nlat_f, nlon_f, Tc, nlat_c, nlon_c, dt,
-                       SweParams(a, omega, nu, phibar), prec, slice_groups)
+    cfg = pfasst_config(n_ts, fine_nodes, coarse_nodes, Tf, nlat_f, nlon_f, Tc, nlat_c, nlon_c, dt, a, omega, nu,
+                        phibar, prec, slice_groups)
     h = c_void_p()
     _check(_lib.pfasst_create(ctypes.byref(h), ctypes.byref(cfg)))
     return Pfasst(h.value, cfg)
@@ -303,6 +334,36 @@ def pfasst_iteration(pf: Pfasst, last: bool = False, stream=None) -> None:
 
 def pfasst_iterations(pf: Pfasst, count: int, last: bool = False, stream=None) -> None:
     _check(_lib.pfasst_iterations(pf.ptr, count, 1 if last else 0, _stream(stream)))
+
+
+def pfasst_config(n_ts: int, fine_nodes: int, coarse_nodes: int, Tf: int, nlat_f: int, nlon_f: int,
+                  Tc: int, nlat_c: int, nlon_c: int, dt: float, a: float, omega: float, nu: float,
+                  phibar: float, prec: int | str = PFSH_FP64, slice_groups: int = 0) -> PfasstConfig:
+    prec = PREC_NAMES[prec] if isinstance(prec, str) else prec
+    return PfasstConfig(n_ts, fine_nodes, coarse_nodes, Tf, nlat_f, nlon_f, Tc, nlat_c, nlon_c, dt,
+                        SweParams(a, omega, nu, phibar), prec, slice_groups)
+
+
+def pfasst_ensemble_create(cfgs: list) -> PfasstEnsemble:
+    arr = (PfasstConfig * len(cfgs))(*cfgs)
+    h = c_void_p()
+    _check(_lib.pfasst_ensemble_create(ctypes.byref(h), arr, len(cfgs)))
+    return PfasstEnsemble(h.value, list(cfgs))
+
+
+def pfasst_ensemble_member(ens: PfasstEnsemble, i: int) -> Pfasst:
+    """Member i (owned by the ensemble), for pfasst_set_initial / pfasst_get."""
+    if not 0 <= i < len(ens.members):
+        raise PfshError(PFSH_EINVAL, "pfasst_ensemble_member: index out of range")
+    return ens.members[i]
+
+
+def pfasst_ensemble_predict(ens: PfasstEnsemble, stream=None) -> None:
+    _check(_lib.pfasst_ensemble_predict(ens.ptr, _stream(stream)))
+
+
+def pfasst_ensemble_iterations(ens: PfasstEnsemble, count: int, last: bool = False, stream=None) -> None:
+    _check(_lib.pfasst_ensemble_iterations(ens.ptr, count, 1 if last else 0, _stream(stream)))
 
 
 def pfasst_get(pf: Pfasst, level: int, slice_: int, node: int, out: torch.Tensor, stream=None) -> torch.Tensor:

@@ -225,6 +225,19 @@ struct sdc_level {
   double *d_fac = nullptr;   // [M+1][T+1][4] implicit-solve factors per node and degree
 };
 
+// CUDA graphs of iteration blocks keyed by (iterations, last): the first call
+// of a key runs eagerly, the second records and launches the graph, later
+// calls replay it (see pfasst.cu run_cached).
+struct GraphEntry {
+  int count = 0, last = 0, calls = 0;
+  cudaGraphExec_t exec = nullptr;
+  unsigned long long launches = 0;
+};
+struct GraphCache {
+  static constexpr int kMax = 8;
+  GraphEntry e[kMax];
+};
+
 struct pfasst {
   pfasst_config cfg;
   sht_plan *plan_f = nullptr, *plan_c = nullptr;
@@ -241,13 +254,7 @@ struct pfasst {
   double *theta0;             // [fine state]
   double Rt[16][16], Pt[16][16];   // time restriction / interpolation
   // CUDA graphs of iteration blocks, keyed by (iterations, last)
-  struct GraphEntry {
-    int count = 0, last = 0, calls = 0;
-    cudaGraphExec_t exec = nullptr;
-    unsigned long long launches = 0;
-  };
-  static constexpr int kMaxGraphs = 8;
-  GraphEntry graph_cache[kMaxGraphs];
+  GraphCache graphs_;
   cudaStream_t cap_stream = nullptr;
   bool graphs = true;
   // Step C runs on its own stream with its own coarse plan/context/level so
@@ -259,6 +266,19 @@ struct pfasst {
   swe_ctx *ctx_cc = nullptr;
   sdc_level *lev_cc = nullptr;
   cudaEvent_t ev_fork = nullptr, ev_B[kMaxGroups] = {}, ev_C[kMaxGroups] = {}, ev_R[kMaxGroups] = {};
+};
+
+// Independent PFASST instances advanced together (pfasst.cu): each member on
+// its own stream (plus its own chain stream), one graph per block.
+struct pfasst_ensemble {
+  int n = 0;
+  pfasst **members = nullptr;
+  cudaStream_t *streams = nullptr;
+  cudaEvent_t *ev_join = nullptr;
+  cudaEvent_t ev_fork = nullptr;
+  cudaStream_t cap_stream = nullptr;
+  GraphCache graphs_;
+  bool graphs = true;
 };
 
 namespace pfsh {

@@ -172,7 +172,7 @@ static void pf_free(pfasst *pf) {
                     pf->fe_cs, pf->fi_cs, pf->tau, pf->sent, pf->base_c, pf->theta0};
   for (double *b : bufs)
     if (b) cudaFree(b);
-  for (auto &e : pf->graph_cache)
+  for (auto &e : pf->graphs_.e)
     if (e.exec) cudaGraphExecDestroy(e.exec);
   if (pf->cap_stream) cudaStreamDestroy(pf->cap_stream);
   if (pf->chain_stream) cudaStreamDestroy(pf->chain_stream);
@@ -489,23 +489,25 @@ static int block_body(pfasst *pf, int count, int last, cudaStream_t s) {
 }
 
 // A block of iterations is a fixed sequence of launches on fixed buffers
-// over two streams, so it is recorded once into a CUDA graph (on a private
-// capture stream, joined by the chain stream) per (count, last) and replayed
-// on the caller's stream; the first call of each kind runs eagerly, which
-// also sets every kernel attribute before capture.  Profiling or
+// over several streams, so it is recorded once into a CUDA graph (on a
+// private capture stream that the other streams join) per (count, last) and
+// replayed on the caller's stream; the first call of each key runs eagerly,
+// which also sets every kernel attribute before capture.  Profiling or
 // PFSH_NO_GRAPH=1 keeps the eager path.
-static int run_block(pfasst *pf, int count, int last, cudaStream_t s) {
-  if (!pf->graphs || profiler_on()) return block_body(pf, count, last, s);
-  pfasst::GraphEntry *e = nullptr;
-  for (auto &x : pf->graph_cache)
+template <typename Body>
+static int run_cached(GraphCache &cache, bool graphs, cudaStream_t cap, int count, int last, cudaStream_t s,
+                      Body body) {
+  if (!graphs || profiler_on()) return body(s);
+  GraphEntry *e = nullptr;
+  for (auto &x : cache.e)
     if (x.calls > 0 && x.count == count && x.last == last) e = &x;
   if (!e) {
-    for (auto &x : pf->graph_cache)
+    for (auto &x : cache.e)
       if (x.calls == 0) {
         e = &x;
         break;
       }
-    if (!e) return block_body(pf, count, last, s);   // cache full: eager
+    if (!e) return body(s);   // cache full: eager
     e->count = count;
     e->last = last;
   }
@@ -514,13 +516,13 @@ static int run_block(pfasst *pf, int count, int last, cudaStream_t s) {
     count_launches(e->launches);
     return PFSH_OK;
   }
-  if (e->calls++ == 0) return block_body(pf, count, last, s);
+  if (e->calls++ == 0) return body(s);
   cudaGraph_t g = nullptr;
-  PFSH_CUDA(cudaStreamBeginCapture(pf->cap_stream, cudaStreamCaptureModeThreadLocal));
+  PFSH_CUDA(cudaStreamBeginCapture(cap, cudaStreamCaptureModeThreadLocal));
   const unsigned long long n0 = launches_so_far();
-  int rc = block_body(pf, count, last, pf->cap_stream);
+  int rc = body(cap);
   const unsigned long long n1 = launches_so_far();
-  cudaError_t err = cudaStreamEndCapture(pf->cap_stream, &g);
+  cudaError_t err = cudaStreamEndCapture(cap, &g);
   if (rc) {
     if (g) cudaGraphDestroy(g);
     return rc;
@@ -539,6 +541,11 @@ static int run_block(pfasst *pf, int count, int last, cudaStream_t s) {
   return PFSH_OK;
 }
 
+static int run_block(pfasst *pf, int count, int last, cudaStream_t s) {
+  return run_cached(pf->graphs_, pf->graphs, pf->cap_stream, count, last, s,
+                    [&](cudaStream_t st) { return block_body(pf, count, last, st); });
+}
+
 extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
   if (!pf) return fail(PFSH_EINVAL, "pfasst_iteration: NULL argument");
   return run_block(pf, 1, last ? 1 : 0, (cudaStream_t)stream);
@@ -547,6 +554,107 @@ extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
 extern "C" int pfasst_iterations(pfasst *pf, int count, int last, pfsh_stream_t stream) {
   if (!pf || count < 1) return fail(PFSH_EINVAL, "pfasst_iterations: NULL argument or count < 1");
   return run_block(pf, count, last ? 1 : 0, (cudaStream_t)stream);
+}
+
+// ---------------------------------------------------------------------------
+// ensembles of independent instances
+// ---------------------------------------------------------------------------
+static void ens_free(pfasst_ensemble *e) {
+  if (!e) return;
+  for (auto &x : e->graphs_.e)
+    if (x.exec) cudaGraphExecDestroy(x.exec);
+  for (int i = 0; i < e->n; ++i) {
+    if (e->members && e->members[i]) pfasst_destroy(e->members[i]);
+    if (e->streams && e->streams[i]) cudaStreamDestroy(e->streams[i]);
+    if (e->ev_join && e->ev_join[i]) cudaEventDestroy(e->ev_join[i]);
+  }
+  if (e->ev_fork) cudaEventDestroy(e->ev_fork);
+  if (e->cap_stream) cudaStreamDestroy(e->cap_stream);
+  delete[] e->members;
+  delete[] e->streams;
+  delete[] e->ev_join;
+  delete e;
+}
+
+extern "C" int pfasst_ensemble_create(pfasst_ensemble **out, const pfasst_config *cfgs, int n) {
+  if (!out || !cfgs || n < 1) return fail(PFSH_EINVAL, "pfasst_ensemble_create: NULL argument or n < 1");
+  *out = nullptr;
+  pfasst_ensemble *e = new (std::nothrow) pfasst_ensemble();
+  if (!e) return fail(PFSH_ENOMEM, "pfasst_ensemble_create");
+  e->members = new (std::nothrow) pfasst *[n]();
+  e->streams = new (std::nothrow) cudaStream_t[n]();
+  e->ev_join = new (std::nothrow) cudaEvent_t[n]();
+  if (!e->members || !e->streams || !e->ev_join) {
+    ens_free(e);
+    return fail(PFSH_ENOMEM, "pfasst_ensemble_create");
+  }
+  e->n = n;
+  for (int i = 0; i < n; ++i) {
+    int rc = pfasst_create(&e->members[i], &cfgs[i]);
+    if (rc) {
+      ens_free(e);
+      return rc;
+    }
+    if (cudaStreamCreateWithFlags(&e->streams[i], cudaStreamNonBlocking) != cudaSuccess ||
+        cudaEventCreateWithFlags(&e->ev_join[i], cudaEventDisableTiming) != cudaSuccess) {
+      cudaGetLastError();
+      ens_free(e);
+      return fail(PFSH_ECUDA, "pfasst_ensemble_create: streams/events");
+    }
+  }
+  if (cudaEventCreateWithFlags(&e->ev_fork, cudaEventDisableTiming) != cudaSuccess ||
+      cudaStreamCreateWithFlags(&e->cap_stream, cudaStreamNonBlocking) != cudaSuccess) {
+    cudaGetLastError();
+    ens_free(e);
+    return fail(PFSH_ECUDA, "pfasst_ensemble_create: streams/events");
+  }
+  const char *env = getenv("PFSH_NO_GRAPH");
+  e->graphs = !(env && env[0] && env[0] != '0');
+  *out = e;
+  return PFSH_OK;
+}
+
+extern "C" int pfasst_ensemble_destroy(pfasst_ensemble *e) {
+  if (!e) return PFSH_OK;
+  cudaDeviceSynchronize();
+  ens_free(e);
+  return PFSH_OK;
+}
+
+extern "C" pfasst *pfasst_ensemble_member(pfasst_ensemble *e, int i) {
+  if (!e || i < 0 || i >= e->n) {
+    fail(PFSH_EINVAL, "pfasst_ensemble_member: index out of range");
+    return nullptr;
+  }
+  return e->members[i];
+}
+
+// fork every member onto its own stream, run `body(member, stream)`, join
+template <typename Body>
+static int ens_fanout(pfasst_ensemble *e, cudaStream_t s, Body body) {
+  PFSH_CUDA(cudaEventRecord(e->ev_fork, s));
+  for (int i = 0; i < e->n; ++i) {
+    PFSH_CUDA(cudaStreamWaitEvent(e->streams[i], e->ev_fork, 0));
+    int rc = body(e->members[i], e->streams[i]);
+    if (rc) return rc;
+    PFSH_CUDA(cudaEventRecord(e->ev_join[i], e->streams[i]));
+    PFSH_CUDA(cudaStreamWaitEvent(s, e->ev_join[i], 0));
+  }
+  return PFSH_OK;
+}
+
+extern "C" int pfasst_ensemble_predict(pfasst_ensemble *e, pfsh_stream_t stream) {
+  if (!e) return fail(PFSH_EINVAL, "pfasst_ensemble_predict: NULL argument");
+  return ens_fanout(e, (cudaStream_t)stream,
+                    [](pfasst *pf, cudaStream_t st) { return pfasst_predict(pf, (pfsh_stream_t)st); });
+}
+
+extern "C" int pfasst_ensemble_iterations(pfasst_ensemble *e, int count, int last, pfsh_stream_t stream) {
+  if (!e || count < 1) return fail(PFSH_EINVAL, "pfasst_ensemble_iterations: NULL argument or count < 1");
+  const int lst = last ? 1 : 0;
+  return run_cached(e->graphs_, e->graphs, e->cap_stream, count, lst, (cudaStream_t)stream, [&](cudaStream_t st) {
+    return ens_fanout(e, st, [&](pfasst *pf, cudaStream_t ms) { return block_body(pf, count, lst, ms); });
+  });
 }
 
 extern "C" int pfasst_get(pfasst *pf, int level, int slice, int node, double *out, pfsh_stream_t stream) {
