@@ -387,9 +387,16 @@ def kernel_work_per_iteration(name: str, prec: str):
         return (nfs * (5 * ncf1 * 2 * elem + 3 * st_f) + ncb * (5 * ncc1 * 2 * elem + 3 * st_c), "byte",
                 ("hbm", None), None)
     if name == "k_sdc_old":
-        # fine: theta_0, F_E and F_I at every node in, M "old" arrays out;
-        # coarse: the same plus M FAS arrays in
-        return NTS * ((1 + 2 * NF + (NF - 1)) * st_f + (1 + 2 * NC + 2 * (NC - 1)) * st_c), "byte", ("hbm", None), None
+        # fine sweeps of every slice: per complex coefficient 2 M (M+1) complex
+        # FMAs of real coefficients (F_E and F_I at every node into M old
+        # parts) = 8 M (M+1) real flops; FP64-pipe bound (measured 83% busy)
+        mf = NF - 1
+        return NTS * 3 * ncf * 8 * mf * (mf + 1), "flop", ("alu", "FP64 pipe"), None
+    if name == "k_chain_node":
+        # every launch but the first of a group analyses one node (5 columns)
+        # and synthesises the next (4 columns) of one T127 slice
+        n = NTS * (NC - 1)
+        return n * (legendre_flops(TC, nlat_c, 5) + legendre_flops(TC, nlat_c, 4)), "flop", simt_bound, None
     if name == "k_sdc_node":
         mf, mc = NF - 1, NC - 1
         return NTS * (mf * (mf + 1) * st_f + mc * (mc + 1) * st_c), "byte", ("hbm", None), None

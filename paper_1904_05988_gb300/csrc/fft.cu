@@ -105,11 +105,11 @@ __global__ void __launch_bounds__(256) k_grid_rhs(FftArgs f, int T, int nlat, in
                                                   const typename cpx<Rl>::t *__restrict__ F,
                                                   const Rl *__restrict__ rowf,
                                                   const typename cpx<Rl>::t *__restrict__ tw,
-                                                  typename cpx<Rl>::t *__restrict__ H) {
+                                                  typename cpx<Rl>::t *__restrict__ H, bool center) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_wait();
   grid_rhs_body<Rl, Shape>(f, T, nlat, B, blockIdx.x, blockIdx.y, F, rowf, tw, H,
-                           reinterpret_cast<typename cpx<Rl>::t *>(smem_raw));
+                           reinterpret_cast<typename cpx<Rl>::t *>(smem_raw), center);
 }
 
 template <typename Rl, typename Shape>
@@ -117,11 +117,11 @@ __global__ void __launch_bounds__(256) k_grid_rhs_long(FftArgs f, int T, int nla
                                                        const typename cpx<Rl>::t *__restrict__ F,
                                                        const Rl *__restrict__ rowf,
                                                        const typename cpx<Rl>::t *__restrict__ tw,
-                                                       typename cpx<Rl>::t *__restrict__ H) {
+                                                       typename cpx<Rl>::t *__restrict__ H, bool center) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_wait();
   grid_rhs_body_long<Rl, Shape>(f, T, nlat, B, blockIdx.x, blockIdx.y, F, rowf, tw, H,
-                                reinterpret_cast<typename cpx<Rl>::t *>(smem_raw));
+                                reinterpret_cast<typename cpx<Rl>::t *>(smem_raw), center);
 }
 
 // ---------------------------------------------------------------------------
@@ -202,6 +202,9 @@ static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typenam
   const bool longrows = sm10 > kGridSmemLimit;
   if (longrows && sm6 > kGridSmemLimit) return fail(PFSH_EUNSUPPORTED, "grid stage: nlon too long for this precision");
   const size_t sm = longrows ? sm6 : sm10;
+  // centre the product rows when the last pass's leak (multiples of
+  // nlon / last radix) falls inside the retained band
+  const bool center = f.N / f.radix[f.npass - 1] <= p->T;
   return with_shape(f.N, [&]<typename Shape>() -> int {
     auto kern = longrows ? k_grid_rhs_long<Rl, Shape> : k_grid_rhs<Rl, Shape>;
     int rc = set_smem((const void *)kern, sm);
@@ -210,10 +213,10 @@ static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typenam
       PFSH_LAUNCH(longrows ? "k_grid_rhs_long" : "k_grid_rhs", s);
       if (pdl) {
         cudaError_t e = launch_pdl(kern, dim3(p->nh, B), dim3(256), sm, s, f, p->T, p->nlat, B, (const C *)p->F,
-                                   rowf, tw, (C *)p->H);
+                                   rowf, tw, (C *)p->H, center);
         if (e != cudaSuccess) return cuda_fail(e, "k_grid_rhs");
       } else {
-        kern<<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw, (C *)p->H);
+        kern<<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw, (C *)p->H, center);
       }
     }
     PFSH_CHECK_LAUNCH("k_grid_rhs");

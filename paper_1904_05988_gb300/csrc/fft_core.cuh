@@ -253,31 +253,13 @@ typedef ShapeCT<1536, 16, 16, 2, 3> Shape1536;
 typedef ShapeCT<1920, 16, 8, 3, 5> Shape1920;
 typedef ShapeCT<3840, 16, 16, 3, 5> Shape3840;
 
-// Row means of NF padded transforms in `o` (elements sidx(k), k < N):
-// subtracted in place, and stashed in the last slot (NP - 1) of each
-// transform of both `o` and `g`, which the passes never touch, so that the
-// unpack of the forward transform can add N * mean back to wavenumber 0
-// whichever buffer the result lands in.  `g` is free on entry (the first
-// nwarps * NF elements serve as reduction scratch).  Removing the mean keeps
-// the rounding of a large zonal mean out of the other wavenumbers: the last
-// Stockham pass of radix R mixes wavenumbers j + q N/R, and with R = 5
-// (nlon = 1920, 3840) those land inside the retained band, where the
-// derivatives of the assembly amplify them.
+// Block-wide means of NF complex row sums (each thread passes its partial
+// sums); `scratch` holds at least nwarps * NF elements and is free until the
+// closing barrier.  Called by every thread of a block.
 template <typename C, int NF>
-__device__ __forceinline__ void subtract_row_means(C *o, C *g, int N, int NP) {
-  typedef decltype(o[0].x) R;
-  R sx[NF], sy[NF];
-#pragma unroll
-  for (int f = 0; f < NF; ++f) sx[f] = sy[f] = (R)0;
-  for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    const int e = sidx(k);
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      const C v = o[f * NP + e];
-      sx[f] += v.x;
-      sy[f] += v.y;
-    }
-  }
+__device__ __forceinline__ void block_means(decltype(C().x) (&sx)[NF], decltype(C().x) (&sy)[NF], int N,
+                                            C *scratch, C (&mean)[NF]) {
+  typedef decltype(C().x) R;
 #pragma unroll
   for (int f = 0; f < NF; ++f)
 #pragma unroll
@@ -288,32 +270,42 @@ __device__ __forceinline__ void subtract_row_means(C *o, C *g, int N, int NP) {
   const int warp = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
   if (lane == 0)
 #pragma unroll
-    for (int f = 0; f < NF; ++f) g[warp * NF + f] = mk<C>(sx[f], sy[f]);
+    for (int f = 0; f < NF; ++f) scratch[warp * NF + f] = mk<C>(sx[f], sy[f]);
   __syncthreads();
-  C mean[NF];
 #pragma unroll
   for (int f = 0; f < NF; ++f) {
     R ax = (R)0, ay = (R)0;
     for (int w = 0; w < nw; ++w) {
-      ax += g[w * NF + f].x;
-      ay += g[w * NF + f].y;
+      ax += scratch[w * NF + f].x;
+      ay += scratch[w * NF + f].y;
     }
     mean[f] = mk<C>(ax / (R)N, ay / (R)N);
   }
   __syncthreads();
-  for (int k = threadIdx.x; k < N; k += blockDim.x) {
-    const int e = sidx(k);
-#pragma unroll
-    for (int f = 0; f < NF; ++f) o[f * NP + e] = o[f * NP + e] - mean[f];
-  }
-  if (threadIdx.x == 0)
-#pragma unroll
-    for (int f = 0; f < NF; ++f) {
-      o[f * NP + NP - 1] = mean[f];
-      g[f * NP + NP - 1] = mean[f];
-    }
-  __syncthreads();
 }
+
+// The five products of the grid stage at one point (packed north/south rows).
+template <typename C, typename Rl>
+__device__ __forceinline__ void grid_products(const C &eta, const C &php, const C &U, const C &V, Rl inv, Rl h,
+                                              C (&o)[5]) {
+  const Rl Ui = U.x * inv, Us = U.y * inv, Vi = V.x * inv, Vs = V.y * inv;
+  o[0] = mk<C>(eta.x * Ui, eta.y * Us);
+  o[1] = mk<C>(eta.x * Vi, eta.y * Vs);
+  o[2] = mk<C>(php.x * Ui, php.y * Us);
+  o[3] = mk<C>(php.x * Vi, php.y * Vs);
+  o[4] = mk<C>((U.x * U.x + V.x * V.x) * h, (U.y * U.y + V.y * V.y) * h);
+}
+
+// Row means are taken out of the products before the forward transform and
+// put back at wavenumber 0 in the unpack (kept in the last slot, NP - 1, of
+// each transform of both ping-pong buffers, which the passes never touch):
+// the last Stockham pass of radix R mixes wavenumbers j + q N/R, and with
+// R = 5 (nlon = 1920, 3840) the rounding of a large zonal mean would land
+// inside the retained band, where the derivatives of the assembly amplify
+// it.  The products are formed twice (sums, then centred values) rather
+// than re-reading and rewriting the five product rows.  Only when the leak
+// would land inside the band (nlon / last radix <= T: `center`); otherwise
+// the products are formed once.
 
 // RHS grid stage for one latitude pair (j, nlat-1-j) of state b: 4 spectra
 // (eta, Phi', U, V) -> inverse FFTs -> products
@@ -326,7 +318,8 @@ template <typename Rl, typename Shape>
 __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat, int B, int j, int b,
                                               const typename cpx<Rl>::t *__restrict__ F, const Rl *__restrict__ rowf,
                                               const typename cpx<Rl>::t *__restrict__ tw,
-                                              typename cpx<Rl>::t *__restrict__ H, typename cpx<Rl>::t *smem) {
+                                              typename cpx<Rl>::t *__restrict__ H, typename cpx<Rl>::t *smem,
+                                              bool center) {
   typedef typename cpx<Rl>::t C;
   const int N = Shape::n(f), NP = padded(N);
   C *A = smem;            // 5 padded transforms
@@ -352,18 +345,39 @@ __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat,
   C *o = (g == A) ? Bf : A;
   const Rl inv = rowf[2 * j];                // 1/(1 - mu_j^2)
   const Rl h = (Rl)0.5 * inv;
+  C mean[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) mean[q] = mk<C>(0.0, 0.0);
+  if (center) {
+    Rl sx[5], sy[5];
+#pragma unroll
+    for (int q = 0; q < 5; ++q) sx[q] = sy[q] = (Rl)0;
+    for (int k = threadIdx.x; k < N; k += blockDim.x) {
+      const int e = sidx(k);
+      C pr[5];
+      grid_products<C, Rl>(g[e], g[NP + e], g[2 * NP + e], g[3 * NP + e], inv, h, pr);
+#pragma unroll
+      for (int q = 0; q < 5; ++q) {
+        sx[q] += pr[q].x;
+        sy[q] += pr[q].y;
+      }
+    }
+    block_means<C, 5>(sx, sy, N, o, mean);
+  }
   for (int k = threadIdx.x; k < N; k += blockDim.x) {
     const int e = sidx(k);
-    const C eta = g[e], php = g[NP + e], U = g[2 * NP + e], V = g[3 * NP + e];
-    const Rl Ui = U.x * inv, Us = U.y * inv, Vi = V.x * inv, Vs = V.y * inv;
-    o[e] = mk<C>(eta.x * Ui, eta.y * Us);
-    o[NP + e] = mk<C>(eta.x * Vi, eta.y * Vs);
-    o[2 * NP + e] = mk<C>(php.x * Ui, php.y * Us);
-    o[3 * NP + e] = mk<C>(php.x * Vi, php.y * Vs);
-    o[4 * NP + e] = mk<C>((U.x * U.x + V.x * V.x) * h, (U.y * U.y + V.y * V.y) * h);
+    C pr[5];
+    grid_products<C, Rl>(g[e], g[NP + e], g[2 * NP + e], g[3 * NP + e], inv, h, pr);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) o[q * NP + e] = pr[q] - mean[q];
   }
+  if (threadIdx.x == 0)
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      o[q * NP + NP - 1] = mean[q];
+      g[q * NP + NP - 1] = mean[q];
+    }
   __syncthreads();
-  subtract_row_means<C, 5>(o, g, N, NP);
   C *Z = Shape::run(f, o, g, 5, tw, false);
   const Rl half = (Rl)0.5 / (Rl)N;
   const Rl wj = rowf[2 * j + 1];
@@ -373,7 +387,7 @@ __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat,
     const C *z = Z + fld * NP;
     C zm = z[sidx(m)];
     C zc = cconj(z[sidx(m == 0 ? 0 : N - m)]);
-    if (m == 0) {                           // the row mean taken out before the transform
+    if (center && m == 0) {                 // the row mean taken out before the transform
       const C dc = (Rl)N * z[NP - 1];
       zm = zm + dc;
       zc = zc + cconj(dc);
@@ -396,7 +410,8 @@ __device__ __forceinline__ void grid_rhs_body_long(const FftArgs &f, int T, int 
                                                    const typename cpx<Rl>::t *__restrict__ F,
                                                    const Rl *__restrict__ rowf,
                                                    const typename cpx<Rl>::t *__restrict__ tw,
-                                                   typename cpx<Rl>::t *__restrict__ H, typename cpx<Rl>::t *smem) {
+                                                   typename cpx<Rl>::t *__restrict__ H, typename cpx<Rl>::t *smem,
+                                                   bool center) {
   typedef typename cpx<Rl>::t C;
   const int N = Shape::n(f), NP = padded(N);
   C *G = smem;             // 4 padded transforms
@@ -430,27 +445,34 @@ __device__ __forceinline__ void grid_rhs_body_long(const FftArgs &f, int T, int 
   const Rl wj = rowf[2 * j + 1];
   const int nh = nlat / 2;
   for (int fld = 0; fld < 5; ++fld) {
+    C mean[1] = {mk<C>(0.0, 0.0)};
+    if (center) {
+      Rl sx[1] = {(Rl)0}, sy[1] = {(Rl)0};
+      for (int k = threadIdx.x; k < N; k += blockDim.x) {
+        const int e = sidx(k);
+        C pr[5];
+        grid_products<C, Rl>(G[e], G[NP + e], G[2 * NP + e], G[3 * NP + e], inv, h, pr);
+        sx[0] += pr[fld].x;
+        sy[0] += pr[fld].y;
+      }
+      block_means<C, 1>(sx, sy, N, W0, mean);
+    }
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
       const int e = sidx(k);
-      const C eta = G[e], php = G[NP + e], U = G[2 * NP + e], V = G[3 * NP + e];
-      const Rl Ui = U.x * inv, Us = U.y * inv, Vi = V.x * inv, Vs = V.y * inv;
-      C o;
-      switch (fld) {
-        case 0: o = mk<C>(eta.x * Ui, eta.y * Us); break;
-        case 1: o = mk<C>(eta.x * Vi, eta.y * Vs); break;
-        case 2: o = mk<C>(php.x * Ui, php.y * Us); break;
-        case 3: o = mk<C>(php.x * Vi, php.y * Vs); break;
-        default: o = mk<C>((U.x * U.x + V.x * V.x) * h, (U.y * U.y + V.y * V.y) * h); break;
-      }
-      W0[e] = o;
+      C pr[5];
+      grid_products<C, Rl>(G[e], G[NP + e], G[2 * NP + e], G[3 * NP + e], inv, h, pr);
+      W0[e] = pr[fld] - mean[0];
+    }
+    if (threadIdx.x == 0) {
+      W0[NP - 1] = mean[0];
+      W1[NP - 1] = mean[0];
     }
     __syncthreads();
-    subtract_row_means<C, 1>(W0, W1, N, NP);
     const C *Z = Shape::run(f, W0, W1, 1, tw, false);
     for (int m = threadIdx.x; m <= T; m += blockDim.x) {
       C zm = Z[sidx(m)];
       C zc = cconj(Z[sidx(m == 0 ? 0 : N - m)]);
-      if (m == 0) {
+      if (center && m == 0) {
         const C dc = (Rl)N * Z[NP - 1];
         zm = zm + dc;
         zc = zc + cconj(dc);
