@@ -1,0 +1,83 @@
+"""PFASST at the benchmark's full size against the oracle: T255 on 384 x 768
+(5 Gauss-Lobatto nodes) / T127 on 192 x 384 (3 nodes), dt = 120 s, the
+balanced jet plus the 120 m Gaussian height bump, predictor and one
+iteration of Algorithm 1.  Four slices (instead of the benchmark's 32) keep
+the oracle to under a minute while the fine sweeps still take the batched
+path of the benchmark (tensor-core Legendre GEMMs for 3xBF16, batches of 4
+states); the coarse chain takes the fused single-slice launches.
+
+The oracle builds the initial state (its own projection of the bump) and the
+GPU receives that same state.  Bounds (measured on GB300 in brackets).
+"""
+import math
+
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle.pfasst import PFASST
+from oracle.sdc import SDCLevel
+from oracle.sht import SHT, pack, unpack
+from oracle.swe import SWEParams
+from _lib import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+ensure_built()
+import paper_1904_05988_gb300 as ps  # noqa: E402
+
+DEV = torch.device("cuda:0")
+TF, TC, NTS, NF, NC, DT = 255, 127, 4, 5, 3, 120.0
+BOUNDS = {  # end values, their change from the initial value
+    "fp64": (1e-12, 1e-8),       # (1.2e-14, 3.3e-10)
+    "bf16x3": (5e-8, 1e-3),      # (7.0e-9, 2.0e-4)
+}
+
+
+def rel(a, b):
+    return float(np.linalg.norm(np.asarray(a) - np.asarray(b)) / np.linalg.norm(np.asarray(b)))
+
+
+@pytest.fixture(scope="module")
+def reference():
+    gf, gc = syn.gaussian_grid_size(TF), syn.gaussian_grid_size(TC)
+    sht = SHT(TF, *gf, L=TF + 1)
+    lam = 2.0 * math.pi * np.arange(gf[1]) / gf[1]
+    lam_c, phi_c = syn.bump_center(2)
+    bump = syn.GRAVITY * syn.gaussian_bump(sht.mu, lam, amplitude=120.0, width=1.0 / 15.0, lam_c=lam_c, phi_c=phi_c)
+    st = unpack(syn.zonal_jet(TF), TF)
+    st[0] += sht.analysis(bump, TF + 1)
+    phibar = st[0, 0, 0].real / math.sqrt(2.0)
+    p = SWEParams(a=syn.EARTH_RADIUS, omega=syn.OMEGA, g=syn.GRAVITY, nu=syn.NU, phibar=phibar)
+    o = PFASST(SDCLevel(TF, *gf, NF, DT, p), SDCLevel(TC, *gc, NC, DT, p), NTS)
+    o.predict(st)
+    o.iteration(False)
+    ends = np.stack([pack(o.th_f[n, NF - 1], TF) for n in range(NTS)])
+    return pack(st, TF), phibar, ends
+
+
+@pytest.mark.parametrize("form", ["fp64", "bf16x3"])
+def test_pfasst_full_size_grids_match_oracle(form, reference):
+    if form not in ps.available_precisions():
+        pytest.skip(f"{form} not built")
+    st0, phibar, ends = reference
+    gf, gc = syn.gaussian_grid_size(TF), syn.gaussian_grid_size(TC)
+    pf = ps.pfasst_create(NTS, NF, NC, TF, *gf, TC, *gc, DT, syn.EARTH_RADIUS, syn.OMEGA, syn.NU, phibar, form)
+    ps.pfasst_set_initial(pf, torch.tensor(st0, dtype=torch.complex128, device=DEV))
+    ps.pfasst_predict(pf)
+    ps.pfasst_iteration(pf, False)
+    out = torch.empty((3, syn.ncoef(TF)), dtype=torch.complex128, device=DEV)
+    errs = []
+    for n in range(NTS):
+        ps.pfasst_get(pf, 0, n, NF - 1, out)
+        ps.pfsh_sync_status()
+        errs.append(rel(out.cpu().numpy(), ends[n]))
+    # the change from the initial value (bump and jet evolution) is matched too
+    ps.pfasst_get(pf, 0, NTS - 1, NF - 1, out)
+    ps.pfsh_sync_status()
+    e_change = rel(out.cpu().numpy() - st0, ends[-1] - st0)
+    print(f"\nT255/T127 x {NTS} slices, {form}: end values {max(errs):.3e}, change {e_change:.3e}")
+    assert max(errs) < BOUNDS[form][0], errs
+    assert e_change < BOUNDS[form][1], e_change
+    pf.close()
