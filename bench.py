@@ -369,12 +369,28 @@ def kernel_work_per_iteration(name: str, prec: str):
     tc = prec in ("bf16", "fp16", "bf16x3")
     simt_bound = ("alu", "FP64 pipe") if prec == "fp64" else ("alu", "FP32 pipe")
     if name.startswith("k_synth") or name.startswith("k_anal"):
-        cols = 4 if name.startswith("k_synth") else 5
+        synth = name.startswith("k_synth")
+        cols = 4 if synth else 5
         w = nfs * legendre_flops(TF, nlat_f, cols) + ncb * legendre_flops(TC, nlat_c, cols)
+        # bytes: per state the activations in and the results out (complex
+        # fp32), per launch the Legendre table (bf16 hi/lo images for 3xBF16,
+        # bf16 for bf16/fp16, fp32 rows for fp32, fp64 for FP64)
+        def per_state(T, nlat):
+            spec = syn.ncoef(T + 1) * cols * 8
+            four = (T + 1) * nlat * cols * 8
+            return spec + four
+        tab = {"bf16x3": 4, "bf16": 2, "fp16": 2, "fp32": 4, "fp64": 8}[prec]
+        def table(T, nlat):
+            return (T + 2) * (T + 3) // 2 * (nlat // 2) * tab
+        groups = 1 if prec == "fp64" else 2
+        byts = (nfs * per_state(TF, nlat_f) + ncb * per_state(TC, nlat_c) +
+                groups * (NF * table(TF, nlat_f) + NC * table(TC, nlat_c)))
+        if prec == "fp64":
+            byts *= 2   # fp64 complex activations and results
         if tc:
             mult = 3 if prec == "bf16x3" else 1
-            return w, "flop", ("tensor", f"{mult} MMA products per algorithmic flop"), None
-        return w, "flop", simt_bound, None
+            return w, "flop", ("tensor", f"{mult} MMA products per algorithmic flop"), byts
+        return w, "flop", simt_bound, byts
     if name.startswith("k_small_synth") or name.startswith("k_small_anal"):
         cols = 4 if "synth" in name else 5
         return ncs * legendre_flops(TC, nlat_c, cols), "flop", simt_bound, None
@@ -417,9 +433,23 @@ def roofline_entry(name: str, n: int, tot_ms: float, prec: str, iterations: int)
     if model is None:
         out.update({"bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None})
         return out
-    work, unit, (bound, note), _ = model
+    work, unit, (bound, note), byts = model
     rate = work * iterations / (tot_ms / 1e3)
     pk, src = peaks()
+    if bound == "tensor" and byts:
+        # per-order GEMMs at this batch: below the bf16 ridge (peak flops /
+        # HBM bandwidth) the table and activation traffic bounds them
+        mult = 3 if "3 MMA" in (note or "") else 1
+        intensity = mult * work / byts
+        ridge = pk["bf16_tflops_sustained"] * 1e12 / (pk["hbm_gbs"] * 1e9)
+        if intensity < ridge:
+            brate = byts * iterations / (tot_ms / 1e3)
+            out.update({"bound": "hbm", "achieved": brate / 1e9, "peak": pk["hbm_gbs"], "unit": "GB/s",
+                        "frac": brate / 1e9 / pk["hbm_gbs"], "peak_source": f"{src} copy bandwidth",
+                        "note": f"tensor-core GEMM below the ridge: {intensity:.0f} executed flop/B vs "
+                                f"{ridge:.0f}; tensor pipe at {rate * mult / 1e12 / pk['bf16_tflops_sustained']:.3f} "
+                                f"of the bf16 peak ({note})"})
+            return out
     if bound == "tensor":
         peak = pk["bf16_tflops_sustained"]
         out.update({"bound": "tensor", "achieved": rate / 1e12, "peak": peak, "unit": "TFLOP/s",

@@ -80,10 +80,37 @@ __global__ void __launch_bounds__(NTHREADS, 1)
   const int m_len = T + 2 - m;          // degrees n = m .. T+1
   const size_t eo = (size_t)eoff(T, m);
 
-  for (int q = 0; q < wk.nchunks; ++q) {
+  // activation items of one chunk (two adjacent columns x 8 consecutive K,
+  // loaded as float2) into registers; zeros outside the tile
+  constexpr int MAXIT = (MROWS / 2) * (KC / 8) / NTHREADS;
+  auto load_chunk = [&](int q, float2 (&v)[MAXIT][8]) {
     const TcChunk ch = chunks[wk.first + q];
-    const int s = q & 1, u = q >> 1;
-    if (q >= 2) ok &= tc::mbar_wait(&done[s], (u - 1) & 1);
+    const int nit = (MROWS / 2) * (ch.klen >> 3);
+#pragma unroll
+    for (int u = 0; u < MAXIT; ++u) {
+      const int it = tid + u * NTHREADS;
+      const int rp = it & (MROWS / 2 - 1), g = it >> 6;
+      const int c = cb * MROWS + 2 * rp;
+#pragma unroll
+      for (int i = 0; i < 8; ++i) {
+        const int k = ch.kstart + g * 8 + i;
+        v[u][i] = make_float2(0.f, 0.f);
+        if (it < nit && c < cols_real) {
+          if (!ANALYSIS) {
+            const int noff = 2 * k + ch.p;      // n - m
+            if (noff < m_len) v[u][i] = *(const float2 *)(act + (eo + noff) * cols_real + c);
+          } else {
+            if (k < nh) v[u][i] = *(const float2 *)(act + (((size_t)m * 2 + ch.p) * nh + k) * cols_real + c);
+          }
+        }
+      }
+    }
+  };
+  // stage chunk q (registers v) into shared memory and issue its MMAs
+  auto produce = [&](int q, float2 (&v)[MAXIT][8]) {
+    const TcChunk ch = chunks[wk.first + q];
+    const int s = q & 1, u2 = q >> 1;
+    if (q >= 2) ok &= tc::mbar_wait(&done[s], (u2 - 1) & 1);
     const int KL = ch.klen;
     const uint32_t b_half = (uint32_t)N * KL * 2;
     if (tid == 0) {
@@ -91,32 +118,19 @@ __global__ void __launch_bounds__(NTHREADS, 1)
       tc::mbar_arrive_expect_tx(&full[s], bytes);
       tc::bulk_g2s(stB[s], img + ch.off, bytes, &full[s]);
     }
-    // produce the activation chunk: rows = 128 real columns, K = KL; one
-    // item = two adjacent columns x 8 consecutive K, loaded as float2
     uint8_t *Ahi = stA[s], *Alo = stA[s] + a_half;
-    const int groups = KL >> 3;
-    for (int it = tid; it < (MROWS / 2) * groups; it += NTHREADS) {
-      const int rp = it & (MROWS / 2 - 1), g = it >> 6;
-      const int r = 2 * rp, c = cb * MROWS + r;
-      float2 v[8];
+    const int nit = (MROWS / 2) * (KL >> 3);
 #pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        const int k = ch.kstart + g * 8 + i;
-        v[i] = make_float2(0.f, 0.f);
-        if (c < cols_real) {
-          if (!ANALYSIS) {
-            const int noff = 2 * k + ch.p;      // n - m
-            if (noff < m_len) v[i] = *(const float2 *)(act + (eo + noff) * cols_real + c);
-          } else {
-            if (k < nh) v[i] = *(const float2 *)(act + (((size_t)m * 2 + ch.p) * nh + k) * cols_real + c);
-          }
-        }
-      }
+    for (int uu = 0; uu < MAXIT; ++uu) {
+      const int it = tid + uu * NTHREADS;
+      if (it >= nit) continue;
+      const int rp = it & (MROWS / 2 - 1), g = it >> 6;
+      const int r = 2 * rp;
       uint16_t h0[8], l0[8], h1[8], l1[8];
 #pragma unroll
       for (int i = 0; i < 8; ++i) {
-        tc::split2<FP16>(v[i].x, h0[i], l0[i]);
-        tc::split2<FP16>(v[i].y, h1[i], l1[i]);
+        tc::split2<FP16>(v[uu][i].x, h0[i], l0[i]);
+        tc::split2<FP16>(v[uu][i].y, h1[i], l1[i]);
       }
       const uint32_t off0 = tc::tile_offset(r, g * 8, KL), off1 = tc::tile_offset(r + 1, g * 8, KL);
       *(uint4 *)(Ahi + off0) = make_uint4(h0[0] | (uint32_t)h0[1] << 16, h0[2] | (uint32_t)h0[3] << 16,
@@ -133,7 +147,7 @@ __global__ void __launch_bounds__(NTHREADS, 1)
     tc::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
-      ok &= tc::mbar_wait(&full[s], u & 1);
+      ok &= tc::mbar_wait(&full[s], u2 & 1);
       tc::fence_after_sync();
       const uint32_t idesc = tc::make_idesc(MROWS, N, FP16);
       const uint32_t sbo = 16u * KL;
@@ -153,6 +167,100 @@ __global__ void __launch_bounds__(NTHREADS, 1)
         }
       }
       tc::mma_commit(&done[s]);
+    }
+  };
+  if constexpr (ANALYSIS) {
+    // analysis (K = latitudes, six chunks per CTA at T255): two register
+    // sets, the loads of chunk q+1 in flight while chunk q is converted and
+    // multiplied (unrolled by two so that both sets stay in registers)
+    float2 va[MAXIT][8], vb[MAXIT][8];
+    if (wk.nchunks > 0) load_chunk(0, va);
+    for (int q = 0; q < wk.nchunks; q += 2) {
+      if (q + 1 < wk.nchunks) load_chunk(q + 1, vb);
+      produce(q, va);
+      if (q + 1 < wk.nchunks) {
+        if (q + 2 < wk.nchunks) load_chunk(q + 2, va);
+        produce(q + 1, vb);
+      }
+    }
+  } else {
+    // synthesis (K = degrees of one parity, few chunks): each thread loads,
+    // splits and stores its items of chunk q in turn (measured faster than
+    // the two-set prefetch here: 31 vs 48 us at T255 with 16 states)
+    for (int q = 0; q < wk.nchunks; ++q) {
+      const TcChunk ch = chunks[wk.first + q];
+      const int s = q & 1, u = q >> 1;
+      if (q >= 2) ok &= tc::mbar_wait(&done[s], (u - 1) & 1);
+      const int KL = ch.klen;
+      const uint32_t b_half = (uint32_t)N * KL * 2;
+      if (tid == 0) {
+        const uint32_t bytes = b_half * (X3 ? 2 : 1);
+        tc::mbar_arrive_expect_tx(&full[s], bytes);
+        tc::bulk_g2s(stB[s], img + ch.off, bytes, &full[s]);
+      }
+      // produce the activation chunk: rows = 128 real columns, K = KL; one
+      // item = two adjacent columns x 8 consecutive K, loaded as float2
+      uint8_t *Ahi = stA[s], *Alo = stA[s] + a_half;
+      const int groups = KL >> 3;
+      for (int it = tid; it < (MROWS / 2) * groups; it += NTHREADS) {
+        const int rp = it & (MROWS / 2 - 1), g = it >> 6;
+        const int r = 2 * rp, c = cb * MROWS + r;
+        float2 v[8];
+  #pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          const int k = ch.kstart + g * 8 + i;
+          v[i] = make_float2(0.f, 0.f);
+          if (c < cols_real) {
+            if (!ANALYSIS) {
+              const int noff = 2 * k + ch.p;      // n - m
+              if (noff < m_len) v[i] = *(const float2 *)(act + (eo + noff) * cols_real + c);
+            } else {
+              if (k < nh) v[i] = *(const float2 *)(act + (((size_t)m * 2 + ch.p) * nh + k) * cols_real + c);
+            }
+          }
+        }
+        uint16_t h0[8], l0[8], h1[8], l1[8];
+  #pragma unroll
+        for (int i = 0; i < 8; ++i) {
+          tc::split2<FP16>(v[i].x, h0[i], l0[i]);
+          tc::split2<FP16>(v[i].y, h1[i], l1[i]);
+        }
+        const uint32_t off0 = tc::tile_offset(r, g * 8, KL), off1 = tc::tile_offset(r + 1, g * 8, KL);
+        *(uint4 *)(Ahi + off0) = make_uint4(h0[0] | (uint32_t)h0[1] << 16, h0[2] | (uint32_t)h0[3] << 16,
+                                            h0[4] | (uint32_t)h0[5] << 16, h0[6] | (uint32_t)h0[7] << 16);
+        *(uint4 *)(Ahi + off1) = make_uint4(h1[0] | (uint32_t)h1[1] << 16, h1[2] | (uint32_t)h1[3] << 16,
+                                            h1[4] | (uint32_t)h1[5] << 16, h1[6] | (uint32_t)h1[7] << 16);
+        if (X3) {
+          *(uint4 *)(Alo + off0) = make_uint4(l0[0] | (uint32_t)l0[1] << 16, l0[2] | (uint32_t)l0[3] << 16,
+                                              l0[4] | (uint32_t)l0[5] << 16, l0[6] | (uint32_t)l0[7] << 16);
+          *(uint4 *)(Alo + off1) = make_uint4(l1[0] | (uint32_t)l1[1] << 16, l1[2] | (uint32_t)l1[3] << 16,
+                                              l1[4] | (uint32_t)l1[5] << 16, l1[6] | (uint32_t)l1[7] << 16);
+        }
+      }
+      tc::fence_proxy_async();
+      __syncthreads();
+      if (tid == 0) {
+        ok &= tc::mbar_wait(&full[s], u & 1);
+        tc::fence_after_sync();
+        const uint32_t idesc = tc::make_idesc(MROWS, N, FP16);
+        const uint32_t sbo = 16u * KL;
+        const uint32_t a0 = tc::smem_u32(Ahi), a1 = tc::smem_u32(Alo);
+        const uint32_t b0 = tc::smem_u32(stB[s]), b1 = b0 + b_half;
+        const uint32_t d = tmem + (uint32_t)(ch.p * N);
+        for (int ks = 0; ks < KL / 16; ++ks) {
+          const uint32_t acc = (ch.kstart == 0 && ks == 0) ? 0u : 1u;
+          const uint64_t ah = tc::make_desc(a0 + ks * 256, 128, sbo);
+          const uint64_t bh = tc::make_desc(b0 + ks * 256, 128, sbo);
+          tc::mma_f16(d, ah, bh, idesc, acc);
+          if (X3) {
+            const uint64_t al = tc::make_desc(a1 + ks * 256, 128, sbo);
+            const uint64_t bl = tc::make_desc(b1 + ks * 256, 128, sbo);
+            tc::mma_f16(d, ah, bl, idesc, 1u);
+            tc::mma_f16(d, al, bh, idesc, 1u);
+          }
+        }
+        tc::mma_commit(&done[s]);
+      }
     }
   }
   if (tid == 0) tc::mma_commit(fin);
