@@ -105,6 +105,24 @@ __global__ void k_interp_inc(int Tf, int Tc, int nts, int nf, int ncn, int kmin,
   }
 }
 
+// Predictor start: the restricted initial value (state 0 of base_c) and its
+// right-hand sides (state 0 of fe_c, fi_c) copied to every slice of base_c
+// and to every (node, slice) of th_c, fe_c, fi_c; grid.y = (node, slice).
+__global__ void k_broadcast(size_t n2, int nts, const double2 *__restrict__ base, const double2 *__restrict__ fe0,
+                            const double2 *__restrict__ fi0, double2 *__restrict__ th, double2 *fe, double2 *fi,
+                            double2 *base_all) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int ns = blockIdx.y, slice = ns % nts;
+  if (e >= n2) return;
+  const double2 b = base[e], ve = fe0[e], vi = fi0[e];   // state 0 is only read
+  th[(size_t)ns * n2 + e] = b;
+  if (ns > 0) {
+    fe[(size_t)ns * n2 + e] = ve;
+    fi[(size_t)ns * n2 + e] = vi;
+  }
+  if (ns < nts && slice > 0) base_all[(size_t)slice * n2 + e] = b;
+}
+
 // Predictor: x_f[k][b] = theta0 + sum_i Pt[k][i] Z(x_c[i][b] - base_c[b])
 __global__ void k_pred_interp(int Tf, int Tc, int nts, int nf, int ncn, Mat16 Pt, const double2 *__restrict__ th0,
                               const double2 *__restrict__ xc, const double2 *__restrict__ basec,
@@ -288,38 +306,40 @@ extern "C" int pfasst_set_initial(pfasst *pf, const double *theta0, pfsh_stream_
   return PFSH_OK;
 }
 
-extern "C" int pfasst_predict(pfasst *pf, pfsh_stream_t stream) {
-  if (!pf) return fail(PFSH_EINVAL, "pfasst_predict: NULL argument");
-  cudaStream_t s = (cudaStream_t)stream;
+// Predictor (Section 5.2.1): the restricted initial value is broadcast to
+// every slice and node, then in round j the slices n >= j take slice n-1's
+// round-(j-1) end value and sweep once on the coarse level (slice n sweeps
+// n+1 times in all); the received value's right-hand sides are those the
+// sender evaluated at its last node (the same state through the same
+// kernels), so they travel with it.  Finally the coarse increments are
+// interpolated to the fine nodes and the fine right-hand sides evaluated.
+static int predict_body(pfasst *pf, cudaStream_t s) {
   const int nts = pf->cfg.n_ts, Mc = pf->Mc, Mf = pf->Mf;
   const size_t sc = pf->sc, sf = pf->sf;
   const size_t cnode = (size_t)nts * sc;
   int rc;
-  // restricted broadcast value into base_c[0], then to every slice and node
+  // restricted initial value and its right-hand sides, broadcast
   double R1[16 * 16] = {0};
   R1[0] = 1.0;
   if ((rc = restrict_launch(R1, 1, 1, pf->theta0, sf, pf->base_c, sc, pf->cfg.Tf, pf->cfg.Tc, 1, s))) return rc;
-  for (int n = 1; n < nts; ++n)
-    PFSH_CUDA(cudaMemcpyAsync(pf->base_c + n * sc, pf->base_c, sc * 8, cudaMemcpyDeviceToDevice, s));
   if ((rc = rhs_eval(pf->ctx_c, pf->base_c, pf->fe_c, pf->fi_c, 1, s))) return rc;
-  for (int n = 1; n < nts; ++n) {
-    PFSH_CUDA(cudaMemcpyAsync(pf->fe_c + n * sc, pf->fe_c, sc * 8, cudaMemcpyDeviceToDevice, s));
-    PFSH_CUDA(cudaMemcpyAsync(pf->fi_c + n * sc, pf->fi_c, sc * 8, cudaMemcpyDeviceToDevice, s));
+  {
+    const size_t n2 = sc / 2;   // complex elements per state
+    PFSH_LAUNCH("k_broadcast", s);
+    dim3 g((unsigned)((n2 + 255) / 256), (unsigned)(Mc + 1) * nts);
+    k_broadcast<<<g, 256, 0, s>>>(n2, nts, (const double2 *)pf->base_c, (const double2 *)pf->fe_c,
+                                  (const double2 *)pf->fi_c, (double2 *)pf->th_c, (double2 *)pf->fe_c,
+                                  (double2 *)pf->fi_c, (double2 *)pf->base_c);
   }
-  for (int i = 0; i <= Mc; ++i) {
-    PFSH_CUDA(cudaMemcpyAsync(pf->th_c + i * cnode, pf->base_c, cnode * 8, cudaMemcpyDeviceToDevice, s));
-    if (i) {
-      PFSH_CUDA(cudaMemcpyAsync(pf->fe_c + i * cnode, pf->fe_c, cnode * 8, cudaMemcpyDeviceToDevice, s));
-      PFSH_CUDA(cudaMemcpyAsync(pf->fi_c + i * cnode, pf->fi_c, cnode * 8, cudaMemcpyDeviceToDevice, s));
-    }
-  }
+  PFSH_CHECK_LAUNCH("k_broadcast");
   // rounds: slices n >= j take slice n-1's round j-1 end value and sweep
   for (int j = 0; j < nts; ++j) {
     const int cnt = nts - j;
     if (j > 0) {
-      PFSH_CUDA(cudaMemcpyAsync(pf->th_c + j * sc, pf->th_c + Mc * cnode + (j - 1) * sc, cnt * sc * 8,
-                                cudaMemcpyDeviceToDevice, s));
-      if ((rc = rhs_eval(pf->ctx_c, pf->th_c + j * sc, pf->fe_c + j * sc, pf->fi_c + j * sc, cnt, s))) return rc;
+      const size_t from = Mc * cnode + (j - 1) * sc, to = j * sc, bytes = cnt * sc * 8;
+      PFSH_CUDA(cudaMemcpyAsync(pf->th_c + to, pf->th_c + from, bytes, cudaMemcpyDeviceToDevice, s));
+      PFSH_CUDA(cudaMemcpyAsync(pf->fe_c + to, pf->fe_c + from, bytes, cudaMemcpyDeviceToDevice, s));
+      PFSH_CUDA(cudaMemcpyAsync(pf->fi_c + to, pf->fi_c + from, bytes, cudaMemcpyDeviceToDevice, s));
     }
     if ((rc = sdc_sweep_strided(pf->lev_c, pf->th_c + j * sc, pf->fe_c + j * sc, pf->fi_c + j * sc, nullptr, cnode,
                                 cnt, s)))
@@ -544,6 +564,13 @@ static int run_cached(GraphCache &cache, bool graphs, cudaStream_t cap, int coun
 static int run_block(pfasst *pf, int count, int last, cudaStream_t s) {
   return run_cached(pf->graphs_, pf->graphs, pf->cap_stream, count, last, s,
                     [&](cudaStream_t st) { return block_body(pf, count, last, st); });
+}
+
+extern "C" int pfasst_predict(pfasst *pf, pfsh_stream_t stream) {
+  if (!pf) return fail(PFSH_EINVAL, "pfasst_predict: NULL argument");
+  // graph key (0, 2): no iteration block has count 0
+  return run_cached(pf->graphs_, pf->graphs, pf->cap_stream, 0, 2, (cudaStream_t)stream,
+                    [&](cudaStream_t st) { return predict_body(pf, st); });
 }
 
 extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
