@@ -234,6 +234,14 @@ pfasst *pfasst_ensemble_member(pfasst_ensemble *e, int i);
 int pfasst_ensemble_predict(pfasst_ensemble *e, pfsh_stream_t stream);
 int pfasst_ensemble_iterations(pfasst_ensemble *e, int count, int last, pfsh_stream_t stream);
 
+/* Residual check for a variable number of iterations: res[n] (device,
+ * n_ts doubles) = max over the coefficients of slice n of |theta_f(end) -
+ * theta_f(end) at the previous call| / max |theta_f(end)| (fine level, last
+ * node), and the current end values become the previous ones.  Call it once
+ * after the predictor, then after every iteration (or block) and stop when
+ * max_n res[n] is below a tolerance.  Stream-ordered; no host sync. */
+int pfasst_residual(pfasst *pf, double *res, pfsh_stream_t stream);
+
 /* Copy one node of one slice to `out` (device, [3][ncoef][2]); level 0 =
  * fine, 1 = coarse. */
 int pfasst_get(pfasst *pf, int level, int slice, int node, double *out,

@@ -28,7 +28,7 @@ EXPORTED = ["sht_plan_create", "sht_plan_destroy", "sht_plan_query", "sht_invers
             "swe_ctx_create", "swe_ctx_destroy", "swe_rhs", "swe_implicit_solve",
             "sdc_level_create", "sdc_level_destroy", "sdc_spread", "sdc_sweep",
             "pfasst_create", "pfasst_destroy", "pfasst_set_initial", "pfasst_predict",
-            "pfasst_iteration", "pfasst_iterations", "pfasst_get", "pfasst_ensemble_create",
+            "pfasst_iteration", "pfasst_iterations", "pfasst_residual", "pfasst_get", "pfasst_ensemble_create",
             "pfasst_ensemble_destroy", "pfasst_ensemble_member", "pfasst_ensemble_predict",
             "pfasst_ensemble_iterations", "pfsh_sync_status", "pfsh_last_error",
             "pfsh_kernel_launches", "pfsh_profiler_enable", "pfsh_profiler_report", "sht_inverse_noalloc"]
@@ -88,6 +88,7 @@ _sig = {
     "pfasst_predict": [c_void_p, c_void_p],
     "pfasst_iteration": [c_void_p, c_int, c_void_p],
     "pfasst_iterations": [c_void_p, c_int, c_int, c_void_p],
+    "pfasst_residual": [c_void_p, c_void_p, c_void_p],
     "pfasst_ensemble_create": [ctypes.POINTER(c_void_p), ctypes.POINTER(PfasstConfig), c_int],
     "pfasst_ensemble_destroy": [c_void_p],
     "pfasst_ensemble_predict": [c_void_p, c_void_p],
@@ -334,6 +335,13 @@ def pfasst_iteration(pf: Pfasst, last: bool = False, stream=None) -> None:
 
 def pfasst_iterations(pf: Pfasst, count: int, last: bool = False, stream=None) -> None:
     _check(_lib.pfasst_iterations(pf.ptr, count, 1 if last else 0, _stream(stream)))
+
+
+def pfasst_residual(pf: Pfasst, res: torch.Tensor, stream=None) -> torch.Tensor:
+    """res: float64 [n_ts] on the device; res[n] = max |change of slice n's fine
+    end value since the previous call| / max |its end value|."""
+    _check(_lib.pfasst_residual(pf.ptr, _ptr(res, torch.float64, pf.cfg.n_ts), _stream(stream)))
+    return res
 
 
 def pfasst_config(n_ts: int, fine_nodes: int, coarse_nodes: int, Tf: int, nlat_f: int, nlon_f: int,

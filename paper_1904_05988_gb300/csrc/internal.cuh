@@ -252,6 +252,7 @@ struct pfasst {
   double *sent;               // [n_ts][fine state]
   double *base_c;             // [n_ts][coarse state] restricted initial value
   double *theta0;             // [fine state]
+  double *prev_end = nullptr; // [n_ts][fine state] end values at the last residual check
   double Rt[16][16], Pt[16][16];   // time restriction / interpolation
   // CUDA graphs of iteration blocks, keyed by (iterations, last)
   GraphCache graphs_;

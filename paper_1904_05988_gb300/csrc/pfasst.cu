@@ -105,6 +105,40 @@ __global__ void k_interp_inc(int Tf, int Tc, int nts, int nf, int ncn, int kmin,
   }
 }
 
+// Residual check: per slice b, max |theta_f(end) - prev| / max |theta_f(end)|
+// over the slice's coefficients (one block per slice), then prev = current.
+__global__ void k_residual(size_t n2, const double2 *__restrict__ cur, double2 *__restrict__ prev,
+                           double *__restrict__ res) {
+  __shared__ double sd[32], sv[32];
+  const int b = blockIdx.x;
+  const double2 *c = cur + (size_t)b * n2;
+  double2 *p = prev + (size_t)b * n2;
+  double md = 0.0, mv = 0.0;
+  for (size_t e = threadIdx.x; e < n2; e += blockDim.x) {
+    const double2 x = c[e], y = p[e];
+    md = fmax(md, fmax(fabs(x.x - y.x), fabs(x.y - y.y)));
+    mv = fmax(mv, fmax(fabs(x.x), fabs(x.y)));
+    p[e] = x;
+  }
+  for (int d = 16; d > 0; d >>= 1) {
+    md = fmax(md, __shfl_xor_sync(0xffffffffu, md, d));
+    mv = fmax(mv, __shfl_xor_sync(0xffffffffu, mv, d));
+  }
+  const int w = threadIdx.x >> 5, lane = threadIdx.x & 31, nw = blockDim.x >> 5;
+  if (lane == 0) {
+    sd[w] = md;
+    sv[w] = mv;
+  }
+  __syncthreads();
+  if (threadIdx.x == 0) {
+    for (int i = 1; i < nw; ++i) {
+      md = fmax(md, sd[i]);
+      mv = fmax(mv, sv[i]);
+    }
+    res[b] = mv > 0.0 ? md / mv : md;
+  }
+}
+
 // Predictor start: the restricted initial value (state 0 of base_c) and its
 // right-hand sides (state 0 of fe_c, fi_c) copied to every slice of base_c
 // and to every (node, slice) of th_c, fe_c, fi_c; grid.y = (node, slice).
@@ -187,7 +221,7 @@ using namespace pfsh;
 static void pf_free(pfasst *pf) {
   if (!pf) return;
   double *bufs[] = {pf->th_f, pf->fe_f, pf->fi_f, pf->th_c, pf->fe_c, pf->fi_c, pf->th_cs,
-                    pf->fe_cs, pf->fi_cs, pf->tau, pf->sent, pf->base_c, pf->theta0};
+                    pf->fe_cs, pf->fi_cs, pf->tau, pf->sent, pf->base_c, pf->theta0, pf->prev_end};
   for (double *b : bufs)
     if (b) cudaFree(b);
   for (auto &e : pf->graphs_.e)
@@ -254,7 +288,7 @@ extern "C" int pfasst_create(pfasst **out, const pfasst_config *cfg) {
                 {&pf->th_cs, (size_t)(pf->Mc + 1) * nts * pf->sc}, {&pf->fe_cs, (size_t)(pf->Mc + 1) * nts * pf->sc},
                 {&pf->fi_cs, (size_t)(pf->Mc + 1) * nts * pf->sc}, {&pf->tau, (size_t)(pf->Mc + 1) * nts * pf->sc},
                 {&pf->sent, (size_t)2 * nts * pf->sf},            {&pf->base_c, (size_t)nts * pf->sc},
-                {&pf->theta0, pf->sf}};
+                {&pf->theta0, pf->sf},                            {&pf->prev_end, (size_t)nts * pf->sf}};
   for (auto &a : allocs) {
     if (cudaMalloc(a.p, a.n * sizeof(double)) != cudaSuccess) {
       cudaGetLastError();
@@ -571,6 +605,19 @@ extern "C" int pfasst_predict(pfasst *pf, pfsh_stream_t stream) {
   // graph key (0, 2): no iteration block has count 0
   return run_cached(pf->graphs_, pf->graphs, pf->cap_stream, 0, 2, (cudaStream_t)stream,
                     [&](cudaStream_t st) { return predict_body(pf, st); });
+}
+
+extern "C" int pfasst_residual(pfasst *pf, double *res, pfsh_stream_t stream) {
+  if (!pf || !res) return fail(PFSH_EINVAL, "pfasst_residual: NULL argument");
+  const int nts = pf->cfg.n_ts;
+  cudaStream_t s = (cudaStream_t)stream;
+  {
+    PFSH_LAUNCH("k_residual", s);
+    k_residual<<<nts, 256, 0, s>>>(pf->sf / 2, (const double2 *)(pf->th_f + (size_t)pf->Mf * nts * pf->sf),
+                                   (double2 *)pf->prev_end, res);
+  }
+  PFSH_CHECK_LAUNCH("k_residual");
+  return PFSH_OK;
 }
 
 extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
