@@ -17,6 +17,18 @@ State: dense ``[..., 3, L, L]`` complex128 holding [Phi, zeta, delta]
   spectrally (n = 0 mode of psi, chi set to 0).
 * IMEX split (Section 4): F_I = L, F_E = N.
 * Implicit system of Section 5.4: x - h F_I(x) = b, solved per (n, m).
+* Alternative split with the Coriolis force implicit (the paper keeps it
+  explicit, Section 4; ``SWEParams.coriolis_implicit``): the linear Coriolis
+  tendency C(U) = [0, -div(f V), curl(f V)] moves from N to the implicit
+  part, F_I = L + C and F_E = N evaluated with eta = zeta.  From
+  V = k x grad psi + grad chi and grad f = (2 Omega cos(phi)/a) e_north:
+      -div(f V) = -f delta - (2 Omega/a) V,   curl(f V) = f zeta - (2 Omega/a) U
+  (U = u cos(phi), V = v cos(phi)), where zeta, delta are the Laplacians of
+  psi, chi (their n = 0 coefficients do not enter).  Multiplication by
+  mu = sin(phi) couples degree n to n +- 1 within an order:
+      (mu X)_n = eps_n X_{n-1} + eps_{n+1} X_{n+1},
+  so the implicit system of one order m is banded in n; it is solved here by
+  dense linear algebra per order.
 
 Spectral-transform evaluation of N (the standard vorticity-divergence
 formulation the paper adopts from Bourke 1972 / Hack 1992): with U = u cos(phi),
@@ -54,6 +66,7 @@ class SWEParams:
     g: float           # gravity (only used to define Phibar by callers)
     nu: float          # diffusion coefficient [m^2/s]
     phibar: float      # mean geopotential Phibar = g hbar
+    coriolis_implicit: bool = False   # Coriolis tendency in F_I instead of F_E
 
 
 def kappa(L: int, a: float) -> np.ndarray:
@@ -148,19 +161,50 @@ def div_curl(Ahat: np.ndarray, Bhat: np.ndarray, a: float, T: int
     return np.where(valid, div, 0.0), np.where(valid, curl, 0.0)
 
 
+def mu_times(c: np.ndarray) -> np.ndarray:
+    """Coefficients (degree < L) of mu times the series c (dense [..., L, L]):
+    (mu X)_n = eps_n X_{n-1} + eps_{n+1} X_{n+1} (the degree-L term is cut)."""
+    from .sht import epsilon
+    L = c.shape[-1]
+    eps = epsilon(L + 1)
+    out = np.zeros_like(c)
+    out[..., :, 1:] += eps[:L, 1:L] * c[..., :, :L - 1]
+    out[..., :, :L - 1] += eps[:L, 1:L] * c[..., :, 1:]
+    return out
+
+
+def coriolis_linear(state: np.ndarray, p: SWEParams) -> np.ndarray:
+    """C(state) = [0, -div(f V), curl(f V)], degree <= T, dense [..., 3, L, L]:
+    -f delta - 2 Omega V / a and f zeta - 2 Omega U / a with f = 2 Omega mu."""
+    L = state.shape[-1]
+    zeta, delta = state[..., 1, :, :], state[..., 2, :, :]
+    U, V = velocity_coefficients(zeta, delta, p.a)
+    zeta_l, delta_l = zeta.copy(), delta.copy()     # lap psi, lap chi
+    zeta_l[..., 0, 0] = 0.0
+    delta_l[..., 0, 0] = 0.0
+    out = np.zeros_like(state)
+    out[..., 1, :, :] = -2.0 * p.omega * (mu_times(delta_l) + V[..., :L, :L] / p.a)
+    out[..., 2, :, :] = 2.0 * p.omega * (mu_times(zeta_l) - U[..., :L, :L] / p.a)
+    return out
+
+
 def linear_part(state: np.ndarray, p: SWEParams) -> np.ndarray:
-    """F_I = L(state), dense [..., 3, L, L]."""
+    """F_I = L(state) (+ C(state) when the Coriolis term is implicit), dense
+    [..., 3, L, L]."""
     k = kappa(state.shape[-1], p.a)
     Phi, zeta, delta = state[..., 0, :, :], state[..., 1, :, :], state[..., 2, :, :]
     out = np.empty_like(state)
     out[..., 0, :, :] = -p.phibar * delta - p.nu * k * Phi
     out[..., 1, :, :] = -p.nu * k * zeta
     out[..., 2, :, :] = k * Phi - p.nu * k * delta
+    if p.coriolis_implicit:
+        out += coriolis_linear(state, p)
     return out
 
 
 def nonlinear_part(state: np.ndarray, sht: SHT, p: SWEParams) -> np.ndarray:
-    """F_E = N(state) by the spectral transform method (grid products)."""
+    """F_E = N(state) by the spectral transform method (grid products); with
+    the Coriolis term implicit, eta = zeta (f moves to F_I)."""
     T = state.shape[-1] - 1
     Phi, zeta, delta = state[..., 0, :, :], state[..., 1, :, :], state[..., 2, :, :]
     U, V = velocity_coefficients(zeta, delta, p.a)
@@ -168,7 +212,8 @@ def nonlinear_part(state: np.ndarray, sht: SHT, p: SWEParams) -> np.ndarray:
     one_m_mu2 = (1.0 - mu) * (1.0 + mu)
     Ug = sht.synthesis(U)
     Vg = sht.synthesis(V)
-    eta = sht.synthesis(zeta) + 2.0 * p.omega * mu          # zeta + f
+    f = 0.0 if p.coriolis_implicit else 2.0 * p.omega * mu
+    eta = sht.synthesis(zeta) + f                            # zeta + f
     phip = sht.synthesis(Phi) - p.phibar                     # Phi'
     L2 = T + 2
     A1 = sht.analysis(eta * Ug / one_m_mu2, L2)
@@ -199,6 +244,8 @@ def implicit_solve(b: np.ndarray, h: float, p: SWEParams) -> np.ndarray:
       [ s        h Phibar ] [Phi  ]   [b_Phi  ]
       [ -h k     s        ] [delta] = [b_delta]
     """
+    if p.coriolis_implicit:
+        return _implicit_solve_orders(b, h, p)
     k = kappa(b.shape[-1], p.a)
     s = 1.0 + h * p.nu * k
     det = s * s + h * h * p.phibar * k
@@ -207,4 +254,44 @@ def implicit_solve(b: np.ndarray, h: float, p: SWEParams) -> np.ndarray:
     x[..., 0, :, :] = (s * bP - h * p.phibar * bd) / det
     x[..., 1, :, :] = bz / s
     x[..., 2, :, :] = (s * bd + h * k * bP) / det
+    return x
+
+
+_order_inverses: dict = {}
+
+
+def _implicit_solve_orders(b: np.ndarray, h: float, p: SWEParams) -> np.ndarray:
+    """x - h (L + C)(x) = b with the Coriolis term implicit: orders m do not
+    couple, so each order's 3(T+1-m) unknowns solve a dense system whose
+    matrix I - h J_m is read off the operator itself (J_m column (f, n) =
+    F_I of the unit coefficient (f, m, n); one application per (f, j = n - m)
+    fills that column for every order at once)."""
+    L = b.shape[-1]
+    key = (L, h, p.a, p.omega, p.nu, p.phibar)
+    if key not in _order_inverses:
+        cols = np.zeros((3, L, 3, L, L), dtype=np.complex128)   # [f, j][out f, m, n]
+        for f in range(3):
+            for j in range(L):
+                e = np.zeros((3, L, L), dtype=np.complex128)
+                for m in range(L - j):
+                    e[f, m, m + j] = 1.0
+                cols[f, j] = linear_part(e, p)
+        inv = []
+        for m in range(L):
+            K = L - m
+            A = np.empty((3 * K, 3 * K), dtype=np.complex128)
+            for f in range(3):
+                for j in range(K):
+                    A[:, f * K + j] = -h * cols[f, j][:, m, m:].reshape(-1)
+            A += np.eye(3 * K)
+            inv.append(np.linalg.inv(A))
+        if len(_order_inverses) > 16:
+            _order_inverses.clear()
+        _order_inverses[key] = inv
+    inv = _order_inverses[key]
+    x = np.zeros_like(b)
+    for m in range(L):
+        K = L - m
+        rhs_m = b[..., :, m, m:].reshape(b.shape[:-3] + (3 * K,))
+        x[..., :, m, m:] = (rhs_m @ inv[m].T).reshape(b.shape[:-3] + (3, K))
     return x

@@ -12,7 +12,7 @@ from scipy.special import lpmv
 
 from oracle.sht import SHT, unpack, gauss_legendre
 from oracle.swe import (SWEParams, rhs, velocity_coefficients, div_curl, implicit_solve,
-                        linear_part, nonlinear_part, kappa)
+                        linear_part, nonlinear_part, kappa, coriolis_linear)
 import synthetic as syn
 
 A = syn.EARTH_RADIUS
@@ -209,3 +209,111 @@ def test_implicit_solve_against_dense_linear_algebra():
             Mx[:, f] = (e - h * linear_part(e, p))[:, m, n].real
         ref = np.linalg.solve(Mx, b[:, m, n])
         assert np.max(np.abs(ref - x[:, m, n])) <= 1e-13 * np.max(np.abs(ref))
+
+
+# ---------------------------------------------------------------------------
+# Coriolis term in the implicit part (F_I = L + C, F_E = N with eta = zeta)
+# ---------------------------------------------------------------------------
+def cparams(nu=0.0, omega=syn.OMEGA):
+    return SWEParams(a=A, omega=omega, g=syn.GRAVITY, nu=nu, phibar=syn.GRAVITY * syn.MEAN_DEPTH,
+                     coriolis_implicit=True)
+
+
+def _state(T, seed, nmin=0):
+    return unpack(syn.random_spectrum(T, (3,), seed=seed, rms=1e-5, nmin=nmin), T) * np.array(
+        [1e4, 1, 1])[:, None, None]
+
+
+@pytest.mark.parametrize("T", [10, 21])
+def test_coriolis_operator_is_the_transform_difference_of_f(T):
+    """C from mu-multiplication and the recovered U, V against the
+    transform-method route: N with eta = zeta + f minus N with eta = zeta
+    (grid products f U, f V, analysed and differentiated).  Random states
+    include the n = 0 coefficients, which must not enter."""
+    s = level(T)
+    st = _state(T, 31 + T)
+    C = coriolis_linear(st, params())
+    diff = nonlinear_part(st, s, params()) - nonlinear_part(st, s, params(omega=0.0))
+    assert np.max(np.abs(C[0])) == 0.0
+    for f in (1, 2):
+        assert np.max(np.abs(C[f] - diff[f])) < 1e-11 * np.max(np.abs(diff[f])), f
+
+
+def test_coriolis_operator_conserves_kinetic_energy():
+    """The Coriolis force does no work: with KE = sum a^2 (|zeta_n|^2 +
+    |delta_n|^2) / (n(n+1)) per order, Re sum (conj(zeta) C_zeta +
+    conj(delta) C_delta) / (n(n+1)) = 0 for every order m separately."""
+    T = 21
+    st = _state(T, 5)
+    C = coriolis_linear(st, params())
+    n = np.arange(T + 1, dtype=float)
+    w = np.zeros(T + 1)
+    w[1:] = 1.0 / (n[1:] * (n[1:] + 1.0))
+    terms = w * (np.conj(st[1]) * C[1] + np.conj(st[2]) * C[2])
+    per_m = terms.sum(axis=-1).real
+    scale = (w * (np.abs(st[1]) * np.abs(C[1]) + np.abs(st[2]) * np.abs(C[2]))).sum(axis=-1)
+    assert np.all(np.abs(per_m) <= 1e-13 * scale.max())
+    assert scale.max() > 0.0
+
+
+@pytest.mark.parametrize("m,n", [(1, 1), (3, 5), (7, 12)])
+def test_coriolis_operator_gives_the_rossby_haurwitz_frequency(m, n):
+    """A single vorticity harmonic zeta_n^m: the vorticity tendency of C is
+    i 2 Omega m / (n(n+1)) zeta_n^m and nothing else (the beta term; the
+    classical Rossby-Haurwitz dispersion relation), while the divergence
+    tendency lives on degrees n - 1 and n + 1 only."""
+    T = 15
+    st = np.zeros((3, T + 1, T + 1), complex)
+    st[1, m, n] = 0.3 - 0.7j
+    C = coriolis_linear(st, params())
+    expect = np.zeros((T + 1, T + 1), complex)
+    expect[m, n] = 1j * 2.0 * syn.OMEGA * m / (n * (n + 1.0)) * st[1, m, n]
+    assert np.max(np.abs(C[1] - expect)) <= 1e-15 * np.abs(expect[m, n])
+    mask = np.zeros((T + 1, T + 1), bool)
+    mask[m, [d for d in (n - 1, n + 1) if m <= d <= T]] = True
+    assert np.max(np.abs(C[2][~mask])) == 0.0
+    assert np.max(np.abs(C[2][mask])) > 0.0
+
+
+@pytest.mark.parametrize("T", [15, 63])
+def test_balanced_jet_is_steady_with_implicit_coriolis(T):
+    """The sum F_E + F_I does not depend on the split.  F_I = L + C nearly
+    cancels itself for this geostrophically balanced flow, so the scale is
+    the gravity-wave term L alone."""
+    s = level(T)
+    st = unpack(syn.zonal_jet(T), T)
+    FE, FI = rhs(st, s, cparams())
+    scale = np.max(np.abs(linear_part(st, params())))
+    assert np.max(np.abs(FE + FI)) < 1e-11 * scale
+    assert np.max(np.abs(FI)) < 0.1 * scale     # the gradient-wind remainder (Rossby number ~ 0.03)
+
+
+def test_implicit_solve_with_coriolis():
+    """x - h (L + C)(x) = b by the per-order dense solve: residual through the
+    operator, and Omega = 0 reduces to the per-coefficient solve."""
+    T = 12
+    h = 37.5
+    b = _state(T, 6)
+    p = cparams(nu=1e5)
+    x = implicit_solve(b, h, p)
+    hFx = h * linear_part(x, p)
+    scale = np.max(np.abs(x)) + np.max(np.abs(hFx)) + np.max(np.abs(b))
+    assert np.max(np.abs(x - hFx - b)) < 1e-14 * scale
+    # the Coriolis coupling is felt at this step size
+    assert np.max(np.abs(x - implicit_solve(b, h, params(nu=1e5)))) > 1e-6 * np.max(np.abs(x))
+    x0 = implicit_solve(b, h, cparams(nu=1e5, omega=0.0))
+    assert np.max(np.abs(x0 - implicit_solve(b, h, params(nu=1e5, omega=0.0)))) <= 1e-14 * np.max(np.abs(x0))
+
+
+def test_sdc_collocation_solution_does_not_depend_on_the_split():
+    """Iterated to convergence, IMEX-SDC solves the collocation problem of
+    dU/dt = F_E + F_I, which is the same for both splits: one step of 600 s,
+    5 Lobatto nodes, 30 sweeps."""
+    from oracle.sdc import SDCLevel, sdc_step
+    T = 10
+    nlat, nlon = syn.gaussian_grid_size(T)
+    st = unpack(syn.zonal_jet(T), T) + _state(T, 9, nmin=1)
+    a = sdc_step(SDCLevel(T, nlat, nlon, 5, 600.0, params(nu=1e5)), st, 30)
+    b = sdc_step(SDCLevel(T, nlat, nlon, 5, 600.0, cparams(nu=1e5)), st, 30)
+    change = np.linalg.norm(a - st)
+    assert np.linalg.norm(a - b) < 1e-11 * change
