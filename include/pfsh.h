@@ -125,11 +125,22 @@ int sht_forward(sht_plan *plan, const void *grid, double *spec, int batch,
 /* Shallow-water right-hand sides and implicit solve (Sections 2, 4, 5.4)   */
 /* ------------------------------------------------------------------------ */
 
+/* Where the Coriolis force goes in the IMEX split (Section 4):
+ * EXPLICIT (the paper's split): f = 2 omega mu enters N through
+ *   eta = zeta + f, and F_I = L is diagonal in (n, m).
+ * IMPLICIT: the linear Coriolis tendency C = [0, -div(f V), curl(f V)]
+ *   moves to F_I = L + C and N is evaluated with eta = zeta (F_E + F_I is
+ *   unchanged).  C couples degree n to n +- 1 within an order m, so the
+ *   implicit system of an order is banded (two tridiagonal chains). */
+#define PFSH_CORIOLIS_EXPLICIT 0
+#define PFSH_CORIOLIS_IMPLICIT 1
+
 typedef struct {
   double a;      /* sphere radius [m]                                        */
   double omega;  /* rotation rate [1/s]; f = 2 omega mu                      */
   double nu;     /* second-order diffusion coefficient [m^2/s]               */
   double phibar; /* mean geopotential Phibar = g hbar [m^2/s^2]              */
+  int coriolis;  /* PFSH_CORIOLIS_EXPLICIT (0) or PFSH_CORIOLIS_IMPLICIT     */
 } swe_params;
 
 /* The context keeps a reference to `plan` (which must outlive it) and owns
@@ -139,13 +150,18 @@ int swe_ctx_destroy(swe_ctx *ctx);
 
 /* F_E = N(Theta) (Eq. nonlinear_operators, evaluated by the spectral
  * transform method) and F_I = L(Theta) (Eq. linear_wave_motion_induced_by_
- * gravitational_forces) for B states [B][3][ncoef][2].  fE is required,
- * fI may be NULL.  Outputs must not overlap `state`. */
+ * gravitational_forces) for B states [B][3][ncoef][2]; with
+ * PFSH_CORIOLIS_IMPLICIT, F_E = N with eta = zeta and F_I = L + C.  fE is
+ * required, fI may be NULL.  Outputs must not overlap `state`. */
 int swe_rhs(swe_ctx *ctx, const double *state, double *fE, double *fI, int B,
             pfsh_stream_t stream);
 
-/* Solve x - h L(x) = b (Eq. implicit_systems) coefficient by coefficient:
- * b, x [B][3][ncoef][2]; x may alias b. */
+/* Solve x - h F_I(x) = b (Eq. implicit_systems): coefficient by coefficient
+ * for PFSH_CORIOLIS_EXPLICIT; with PFSH_CORIOLIS_IMPLICIT, one banded solve
+ * per order m (FP64 elimination along n, no pivoting: stable because the
+ * Coriolis coupling is skew-Hermitian in the energy weights).  b, x
+ * [B][3][ncoef][2]; x may alias b.  Calls on one context must not run
+ * concurrently on different streams (they share a factor table). */
 int swe_implicit_solve(swe_ctx *ctx, const double *b, double *x, double h,
                        int B, pfsh_stream_t stream);
 

@@ -1,0 +1,116 @@
+// The split with the Coriolis term implicit (F_I = L + C, F_E = N evaluated
+// with eta = zeta; Section 4 keeps the Coriolis term explicit, in N).
+//
+// Linear Coriolis tendency C = [0, -div(f V), curl(f V)], f = 2 Omega mu.
+// With V = k x grad psi + grad chi, -div(f V) = -f delta - 2 Omega V/a and
+// curl(f V) = f zeta - 2 Omega U/a (U = u cos(phi), V = v cos(phi)), where
+// only the Laplacians of psi and chi enter (no n = 0 coefficient).  The
+// multiplication by mu couples degree n to n +- 1 within an order m:
+//   C_zeta,n  = 2 Omega [ i m/(n(n+1)) zeta_n - alpha_n delta_{n-1} - beta_n delta_{n+1} ]
+//   C_delta,n = 2 Omega [ i m/(n(n+1)) delta_n + alpha_n zeta_{n-1} + beta_n zeta_{n+1} ]
+//   alpha_n = eps_n (n+1)/n for n >= 2 (0 for n <= 1),  beta_n = eps_{n+1} n/(n+1) (0 at n = T).
+//
+// Implicit system x - h (L + C)(x) = b of one order m (Eq. implicit_systems
+// with the Coriolis coupling): with k_n = n(n+1)/a^2, s_n = 1 + h nu k_n and
+// th = 2 Omega h, eliminating Phi_n = (b_Phi,n - h Phibar delta_n) / s_n gives
+//   zeta row:  (s_n - i th m/(n(n+1))) zeta_n + th alpha_n delta_{n-1} + th beta_n delta_{n+1} = b_zeta,n
+//   delta row: (d_n - i th m/(n(n+1))) delta_n - th alpha_n zeta_{n-1} - th beta_n zeta_{n+1}
+//              = b_delta,n + (h k_n / s_n) b_Phi,n,            d_n = s_n + h^2 Phibar k_n / s_n,
+// two independent tridiagonal chains, (zeta_m, delta_{m+1}, zeta_{m+2}, ...)
+// and (delta_m, zeta_{m+1}, ...).  Scaled by the kinetic-energy weights
+// 1/(n(n+1)) the Coriolis coupling is skew-Hermitian and the diagonal has a
+// positive real part, so elimination without pivoting is stable for any h.
+// Chain c, position j: degree n = m + j, field (j + c) & 1 (0 zeta, 1 delta).
+// Forward elimination with w_j = D_j - a_j c'_{j-1}, c'_j = c_j / w_j,
+// y_j = (r_j - a_j y_{j-1}) / w_j, then x_j = y_j - c'_j x_{j+1}.
+// The factors {c'_j, 1/w_j} depend on h only: one table per SDC node.
+#pragma once
+
+#include "internal.cuh"
+
+namespace pfsh {
+
+// per-coefficient coupling table of the context: {alpha_n, beta_n, m/(n(n+1)), 0}
+__host__ __device__ inline double band_eps(int n, int m) {
+  return (n > 0 && n >= m) ? sqrt((double)(n - m) * (double)(n + m) / (4.0 * n * n - 1.0)) : 0.0;
+}
+
+// C of coefficient (m, n) (packed index idx) of one state [3][nc]
+__device__ __forceinline__ void coriolis_point(int m, int n, int T, const double2 *__restrict__ st, int nc,
+                                               size_t idx, CorArgs cor, double2 *cz, double2 *cd) {
+  const double4_32a q = cor.ab[idx];
+  auto at = [&](int f, int nn, int off) {
+    if (nn < m || nn > T) return make_double2(0.0, 0.0);
+    double2 v = st[(size_t)f * nc + idx + off];
+    if (m == 0) v.y = 0.0;
+    return v;
+  };
+  const double2 z = at(1, n, 0), d = at(2, n, 0);
+  const double2 zm = at(1, n - 1, -1), dm = at(2, n - 1, -1), zp = at(1, n + 1, 1), dp = at(2, n + 1, 1);
+  const double tw = cor.tw;
+  *cz = make_double2(tw * (-q.z * z.y - q.x * dm.x - q.y * dp.x), tw * (q.z * z.x - q.x * dm.y - q.y * dp.y));
+  *cd = make_double2(tw * (-q.z * d.y + q.x * zm.x + q.y * zp.x), tw * (q.z * d.x + q.x * zm.y + q.y * zp.y));
+}
+
+// shared-memory scratch of one order's banded solve besides its right-hand
+// sides (K = T+1 at most): factors [2][K] and alpha [K], plus alignment slack
+__host__ __device__ inline size_t band_scratch_bytes(int T) {
+  return (size_t)(T + 1) * (2 * sizeof(double4_32a) + sizeof(double)) + 32;
+}
+
+// Solve the order-m system in place.  sr[3][K] (Phi, zeta, delta rows of
+// order m, K = T+1-m) holds b on entry and x on return; tab = the node's
+// factor table [2][nc] (zeta rows, delta rows); scratch = band_scratch_bytes(T)
+// of shared memory (any 16-byte alignment).  Called by every thread of the
+// block; ends with a barrier.
+__device__ __forceinline__ void band_order_solve(int m, int T, double h, double inva2, double nu, double phibar,
+                                                 CorArgs cor, const double4_32a *__restrict__ tab, double2 *sr,
+                                                 void *scratch) {
+  const int K = T + 1 - m, p0 = poff(T, m), nc = ncoef_of(T);
+  double4_32a *stab = reinterpret_cast<double4_32a *>((reinterpret_cast<uintptr_t>(scratch) + 31) & ~uintptr_t(31));
+  double *sal = reinterpret_cast<double *>(stab + 2 * K);          // [K]
+  const double th = cor.tw * h;
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    const int n = m + j;
+    const double k = (double)n * (n + 1) * inva2, s = 1.0 + h * nu * k, g = h * k / s;
+    const double2 bP = sr[j];
+    sr[2 * K + j].x = fma(g, bP.x, sr[2 * K + j].x);
+    sr[2 * K + j].y = fma(g, bP.y, sr[2 * K + j].y);
+    stab[j] = tab[p0 + j];
+    stab[K + j] = tab[(size_t)nc + p0 + j];
+    sal[j] = th * cor.ab[p0 + j].x;
+  }
+  __syncthreads();
+  if (threadIdx.x < 2) {
+    const int c = threadIdx.x;
+    double2 y = make_double2(0.0, 0.0);
+    for (int j = 0; j < K; ++j) {
+      const int f = (j + c) & 1;
+      const double a = f ? -sal[j] : sal[j];
+      const double4_32a q = stab[f * K + j];
+      double2 *x = sr + (1 + f) * K + j;
+      const double rx = fma(-a, y.x, x->x), ry = fma(-a, y.y, x->y);
+      y = make_double2(fma(rx, q.z, -ry * q.w), fma(rx, q.w, ry * q.z));
+      *x = y;
+    }
+    double2 xn = make_double2(0.0, 0.0);
+    for (int j = K - 1; j >= 0; --j) {
+      const int f = (j + c) & 1;
+      const double4_32a q = stab[f * K + j];
+      double2 *x = sr + (1 + f) * K + j;
+      const double2 v = *x;
+      xn = make_double2(v.x - fma(q.x, xn.x, -q.y * xn.y), v.y - fma(q.x, xn.y, q.y * xn.x));
+      *x = xn;
+    }
+  }
+  __syncthreads();
+  for (int j = threadIdx.x; j < K; j += blockDim.x) {
+    const int n = m + j;
+    const double k = (double)n * (n + 1) * inva2, is = 1.0 / (1.0 + h * nu * k), hp = h * phibar;
+    const double2 bP = sr[j], d = sr[2 * K + j];
+    sr[j] = make_double2((bP.x - hp * d.x) * is, (bP.y - hp * d.y) * is);
+  }
+  __syncthreads();
+}
+
+}  // namespace pfsh

@@ -170,6 +170,13 @@ struct TcChunk {          // one K chunk of one (m, row tile, parity)
 struct TcWork {           // one CTA row tile of order m
   int first, nchunks, N, row0, nrows;
 };
+// Coriolis term of the implicit part (banded.cuh): coupling table of the
+// context and 2 Omega, or {nullptr, 0} when the Coriolis term is explicit
+struct CorArgs {
+  const double4_32a *ab;   // [ncoef] {alpha_n, beta_n, m/(n(n+1)), 0}
+  double tw;               // 2 Omega
+};
+
 struct TcDir {
   uint8_t *img = nullptr;
   TcChunk *chunks = nullptr;
@@ -212,6 +219,11 @@ struct swe_ctx {
   sht_plan *plan;
   swe_params prm;
   int max_states;     // states per RHS pass (plan->max_batch / 5)
+  // Coriolis term implicit: coupling table [ncoef] and the factor table of
+  // swe_implicit_solve [2][ncoef] (banded.cu)
+  double4_32a *d_cor = nullptr;
+  double4_32a *d_band_scr = nullptr;
+  ~swe_ctx();
 };
 
 struct sdc_level {
@@ -223,6 +235,7 @@ struct sdc_level {
   double Q[16][16], QE[16][16], QI[16][16];
   double *d_old = nullptr;   // [M][max_batch][3][ncoef] c128: node-update constants
   double *d_fac = nullptr;   // [M+1][T+1][4] implicit-solve factors per node and degree
+  double4_32a *d_band = nullptr;   // Coriolis implicit: [M+1][2][ncoef] banded-solve factors per node
 };
 
 // CUDA graphs of iteration blocks keyed by (iterations, last): the first call
@@ -296,6 +309,13 @@ struct SdcCoef {
 };
 SdcCoef sdc_coef(const sdc_level *l);
 
+inline bool coriolis_implicit(const swe_params &p) { return p.coriolis == PFSH_CORIOLIS_IMPLICIT; }
+// the rotation rate seen by the explicit part (eta = zeta + f, or zeta)
+inline double omega_explicit(const swe_params &p) { return coriolis_implicit(p) ? 0.0 : p.omega; }
+inline CorArgs cor_args(const swe_ctx *c) {
+  return coriolis_implicit(c->prm) ? CorArgs{c->d_cor, 2.0 * c->prm.omega} : CorArgs{nullptr, 0.0};
+}
+
 // ---------------------------------------------------------------------------
 // kernels / launchers (defined in the .cu files)
 // ---------------------------------------------------------------------------
@@ -318,7 +338,7 @@ int analysis_small(const sht_plan *p, int cols, cudaStream_t s);
 bool small_synth(int cols);
 bool small_rhs(int B);
 int rhs_small(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
-              cudaStream_t s);
+              CorArgs cor, cudaStream_t s);
 bool small_analysis(int cols);
 // launch bookkeeping: kernels replayed by a CUDA graph
 void count_launches(unsigned long long n);
@@ -343,7 +363,14 @@ int spec_to_X(const sht_plan *p, const double *spec, int batch, cudaStream_t s);
 int Y_to_spec(const sht_plan *p, double *spec, int batch, cudaStream_t s);
 int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &prm, cudaStream_t s);
 int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI, int B,
-                 const swe_params &prm, cudaStream_t s);
+                 const swe_params &prm, CorArgs cor, cudaStream_t s);
+
+// banded implicit solve of the split with the Coriolis term implicit (banded.cu)
+int band_ctx_init(swe_ctx *c);
+int band_factor_launch(const swe_ctx *c, double h, double4_32a *tab, cudaStream_t s);
+int band_solve_launch(const swe_ctx *c, const double *b, double *x, double h, int B, cudaStream_t s);
+int band_sdc_node_launch(const sdc_level *l, int i, size_t node_stride, const SdcCoef &coef, const double *O,
+                         const double *fE, const double *fI, double *theta, int B, cudaStream_t s);
 int implicit_solve_launch(int T, const double *b, double *x, double h, int B,
                           const swe_params &prm, cudaStream_t s);
 

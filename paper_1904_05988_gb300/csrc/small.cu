@@ -52,20 +52,20 @@ __global__ void __launch_bounds__(kSynthThreads) k_small_synth(int T, int nlat, 
 
 template <typename R, int NB>
 __global__ void __launch_bounds__(kAnalThreads) k_small_anal(int T, int nlat, int B, int rows, R inva, R inva2,
-                                                             double dinva2, double nu, double phibar,
+                                                             double dinva2, double nu, double phibar, CorArgs cor,
                                                              const R *__restrict__ eps, const R *__restrict__ P,
                                                              const typename cpx<R>::t *__restrict__ H,
                                                              const double2 *__restrict__ state,
                                                              double2 *__restrict__ fE, double2 *__restrict__ fI) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   R *Pst = reinterpret_cast<R *>(smem_raw);
-  small_anal_body<R, NB>(blockIdx.x, T, nlat, B, rows, Pst, false, inva, inva2, dinva2, nu, phibar, eps, P, H,
+  small_anal_body<R, NB>(blockIdx.x, T, nlat, B, rows, Pst, false, inva, inva2, dinva2, nu, phibar, cor, eps, P, H,
                          state, fE, fI, smem_raw + small_stage_bytes<R>(nlat, rows));
 }
 
 template <typename R, int NB>
 static int small_launch(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
-                        const R *P, SpecTables<R> tb, cudaStream_t s) {
+                        CorArgs cor, const R *P, SpecTables<R> tb, cudaStream_t s) {
   typedef typename cpx<R>::t C;
   const int T = p->T, nlat = p->nlat;
   const size_t w1 = small_synth_work<R>(T, nlat, B, kSynthThreads);
@@ -76,8 +76,8 @@ static int small_launch(const sht_plan *p, const double *state, double *fE, doub
   {
     PFSH_LAUNCH("k_small_synth", s);
     k_small_synth<R, NB><<<T + 1, kSynthThreads, sm1, s>>>(T, nlat, B, r1, (R)(-prm.a * prm.a), (R)(1.0 / prm.a),
-                                                           prm.omega, prm.phibar, tb, P, (const double2 *)state,
-                                                           (C *)p->F);
+                                                           omega_explicit(prm), prm.phibar, tb, P,
+                                                           (const double2 *)state, (C *)p->F);
   }
   PFSH_CHECK_LAUNCH("k_small_synth");
   if ((rc = grid_rhs(p, B, prm, s))) return rc;
@@ -89,7 +89,7 @@ static int small_launch(const sht_plan *p, const double *state, double *fE, doub
   {
     PFSH_LAUNCH("k_small_anal", s);
     k_small_anal<R, NB><<<T + 1, kAnalThreads, sm3, s>>>(T, nlat, B, r3, (R)(1.0 / prm.a), (R)inva2, inva2,
-                                                         prm.nu, prm.phibar, tb.eps, P, (const C *)p->H,
+                                                         prm.nu, prm.phibar, cor, tb.eps, P, (const C *)p->H,
                                                          (const double2 *)state, (double2 *)fE, (double2 *)fI);
   }
   PFSH_CHECK_LAUNCH("k_small_anal");
@@ -99,14 +99,14 @@ static int small_launch(const sht_plan *p, const double *state, double *fE, doub
 bool small_rhs(int B) { return B <= kSmallMaxStates; }
 
 int rhs_small(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
-              cudaStream_t s) {
+              CorArgs cor, cudaStream_t s) {
   const SpecTables<double> t64{p->d_eps, p->d_ilap};
   const SpecTables<float> t32{p->d_eps32, p->d_ilap32};
   if (p->prec == PFSH_FP64)
-    return B == 1 ? small_launch<double, 1>(p, state, fE, fI, B, prm, p->d_P, t64, s)
-                  : small_launch<double, 2>(p, state, fE, fI, B, prm, p->d_P, t64, s);
-  return B == 1 ? small_launch<float, 1>(p, state, fE, fI, B, prm, p->d_P32, t32, s)
-                : small_launch<float, 2>(p, state, fE, fI, B, prm, p->d_P32, t32, s);
+    return B == 1 ? small_launch<double, 1>(p, state, fE, fI, B, prm, cor, p->d_P, t64, s)
+                  : small_launch<double, 2>(p, state, fE, fI, B, prm, cor, p->d_P, t64, s);
+  return B == 1 ? small_launch<float, 1>(p, state, fE, fI, B, prm, cor, p->d_P32, t32, s)
+                : small_launch<float, 2>(p, state, fE, fI, B, prm, cor, p->d_P32, t32, s);
 }
 
 // ---------------------------------------------------------------------------
@@ -126,6 +126,8 @@ struct ChainStep {
   int k, M;                   // node to update (0: none) and last node
   double hphibar;             // dt QI[k][k] Phibar
   const double4_32a *fac;     // solve factors of node k [T+1]
+  double h;                   // dt QI[k][k]
+  const double4_32a *band;    // Coriolis implicit: banded-solve factors of node k [2][nc]
 };
 
 template <typename R>
@@ -134,6 +136,7 @@ struct ChainGeo {
   size_t work;                // bytes of the body work region
   R ma2, inva, inva2;
   double dinva2, omega, nu, phibar;
+  CorArgs cor;
   SpecTables<R> tb;
   const R *P;
   typename cpx<R>::t *F;
@@ -153,7 +156,8 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_node(ChainStep st, Chai
   stage_rows_async(Pst, g.P + (size_t)eoff(T, m) * (g.nlat / 2), min(K, g.rows), g.nlat / 2);
   pdl_wait();
   if (anal)
-    small_anal_body<R, 1>(m, T, g.nlat, 1, g.rows, Pst, true, g.inva, g.inva2, g.dinva2, g.nu, g.phibar, g.tb.eps,
+    small_anal_body<R, 1>(m, T, g.nlat, 1, g.rows, Pst, true, g.inva, g.inva2, g.dinva2, g.nu, g.phibar, g.cor,
+                          g.tb.eps,
                           g.P, g.H, st.a_th, st.a_fe, st.a_fi, work);
   if (st.k == 0) {
     if (!anal) stage_wait();
@@ -174,8 +178,12 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_node(ChainStep st, Chai
     order_old_part<8>(m, T, st.M, st.ns, c, st.th, st.fe, st.fi, st.tau, st.O);
     __syncthreads();
   }
-  order_node_update(m, T, st.k, st.ns, c, st.hphibar, st.fac, st.O + (size_t)(st.k - 1) * 3 * nc, st.fe, st.fi,
-                    st.th, thk);
+  if (g.cor.tw != 0.0)   // the analysis is done: its work region holds the banded solve's scratch
+    order_node_update_band(m, T, st.k, st.ns, c, st.h, g.dinva2, g.nu, g.phibar, g.cor, st.band,
+                           st.O + (size_t)(st.k - 1) * 3 * nc, st.fe, st.fi, st.th, thk, work);
+  else
+    order_node_update(m, T, st.k, st.ns, c, st.hphibar, st.fac, st.O + (size_t)(st.k - 1) * 3 * nc, st.fe, st.fi,
+                      st.th, thk);
   __syncthreads();
   // rows issued in the prologue: complete after the analysis, else in flight
   const int pmode = anal ? (K <= g.rows ? STAGE_DONE : STAGE_SELF) : STAGE_ISSUED;
@@ -187,6 +195,7 @@ template <typename R>
 static int chain_node_launch(const ChainStep &st, ChainGeo<R> g, const SdcCoef &c, cudaStream_t s, bool pdl) {
   g.work = std::max(small_synth_work<R>(g.T, g.nlat, 1, kChainThreads),
                     small_anal_work<R>(g.T, g.nlat, 1, kChainThreads));
+  if (g.cor.tw != 0.0) g.work = std::max(g.work, align16(band_scratch_bytes(g.T)));
   const size_t thk = align16((size_t)3 * (g.T + 1) * sizeof(double2));
   g.rows = small_stage_rows<R>(g.work + thk, g.T, g.nlat, kChainBudget);
   const size_t smem = g.work + thk + small_stage_bytes<R>(g.nlat, g.rows);
@@ -206,11 +215,13 @@ static int chain_node_launch(const ChainStep &st, ChainGeo<R> g, const SdcCoef &
 }
 
 template <typename R>
-static ChainGeo<R> chain_geo(const sht_plan *p, const swe_params &prm, const R *P, SpecTables<R> tb) {
+static ChainGeo<R> chain_geo(const swe_ctx *ctx, const R *P, SpecTables<R> tb) {
   typedef typename cpx<R>::t C;
+  const sht_plan *p = ctx->plan;
+  const swe_params &prm = ctx->prm;
   const double inva2 = 1.0 / (prm.a * prm.a);
-  return ChainGeo<R>{p->T, p->nlat, 0, 0, (R)(-prm.a * prm.a), (R)(1.0 / prm.a), (R)inva2, inva2, prm.omega, prm.nu,
-                     prm.phibar, tb, P, (C *)p->F, (const C *)p->H};
+  return ChainGeo<R>{p->T, p->nlat, 0, 0, (R)(-prm.a * prm.a), (R)(1.0 / prm.a), (R)inva2, inva2, omega_explicit(prm),
+                     prm.nu, prm.phibar, cor_args(ctx), tb, P, (C *)p->F, (const C *)p->H};
 }
 
 template <typename R>
@@ -238,6 +249,8 @@ static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, doub
       st.M = M;
       st.hphibar = c.h[k] * ctx->prm.phibar;
       st.fac = (const double4_32a *)l->d_fac + (size_t)k * (p->T + 1);
+      st.h = c.h[k];
+      st.band = l->d_band ? l->d_band + (size_t)k * 2 * p->ncoef : nullptr;
       const bool recv = k == 1 && (n > n0 || recv_first);
       if (k > 1) {                                   // analysis of node k-1 of this slice
         st.a_th = st.th + (k - 1) * ns;
@@ -279,11 +292,11 @@ int chain_sweeps(sdc_level *l, double *th, double *fe, double *fi, const double 
                  size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s, cudaEvent_t after_first) {
   const sht_plan *p = l->ctx->plan;
   if (l->nodes - 1 > 8) return fail(PFSH_EUNSUPPORTED, "chain_sweeps: more than 9 nodes");
-  const swe_params &prm = l->ctx->prm;
+  if (coriolis_implicit(l->ctx->prm) && !l->d_band) return fail(PFSH_EINVAL, "chain_sweeps: no banded factors");
   if (p->prec == PFSH_FP64)
-    return chain_typed<double>(l, chain_geo<double>(p, prm, p->d_P, SpecTables<double>{p->d_eps, p->d_ilap}), th,
+    return chain_typed<double>(l, chain_geo<double>(l->ctx, p->d_P, SpecTables<double>{p->d_eps, p->d_ilap}), th,
                                fe, fi, tau, node_stride, slice_stride, n0, n1, recv_first, s, after_first);
-  return chain_typed<float>(l, chain_geo<float>(p, prm, p->d_P32, SpecTables<float>{p->d_eps32, p->d_ilap32}), th,
+  return chain_typed<float>(l, chain_geo<float>(l->ctx, p->d_P32, SpecTables<float>{p->d_eps32, p->d_ilap32}), th,
                             fe, fi, tau, node_stride, slice_stride, n0, n1, recv_first, s, after_first);
 }
 

@@ -214,7 +214,8 @@ __device__ __forceinline__ void small_synth_body(int m, int T, int nlat, int B, 
 template <typename R, int NB>
 __device__ __forceinline__ void small_anal_body(int m, int T, int nlat, int B, int rows, R *Pst, bool p_issued,
                                                 R inva, R inva2,
-                                                double dinva2, double nu, double phibar, const R *__restrict__ eps,
+                                                double dinva2, double nu, double phibar, CorArgs cor,
+                                                const R *__restrict__ eps,
                                                 const R *__restrict__ P, const typename cpx<R>::t *__restrict__ H,
                                                 const double2 *__restrict__ state, double2 *__restrict__ fE,
                                                 double2 *__restrict__ fI, void *work) {
@@ -293,7 +294,8 @@ __device__ __forceinline__ void small_anal_body(int m, int T, int nlat, int B, i
     oE[idx] = fe[0];
     oE[nc + idx] = fe[1];
     oE[2 * nc + idx] = fe[2];
-    if (fI) linear_point(m, n, state + (size_t)b * 3 * nc, nc, idx, dinva2, nu, phibar, fI + (size_t)b * 3 * nc);
+    if (fI)
+      linear_point(m, n, T, state + (size_t)b * 3 * nc, nc, idx, dinva2, nu, phibar, cor, fI + (size_t)b * 3 * nc);
   }
   __syncthreads();
 }
@@ -370,6 +372,36 @@ __device__ __forceinline__ void order_node_update(int m, int T, int i, size_t ns
       sm_th[len + t] = x1;
       sm_th[2 * len + t] = x2;
     }
+  }
+}
+
+// The same node update with the Coriolis term implicit: the right-hand sides
+// of order m are gathered in sm_th [3][T+1-m] and solved there by the banded
+// solve of banded.cuh (scratch: band_scratch_bytes(T) of shared memory).
+__device__ __forceinline__ void order_node_update_band(int m, int T, int i, size_t ns, const SdcCoef &c, double h,
+                                                       double inva2, double nu, double phibar, CorArgs cor,
+                                                       const double4_32a *__restrict__ band,
+                                                       const double2 *__restrict__ O, const double2 *__restrict__ fe,
+                                                       const double2 *__restrict__ fi, double2 *__restrict__ th,
+                                                       double2 *sm_th, void *scratch) {
+  const int nc = ncoef_of(T), p0 = poff(T, m), len = T + 1 - m;
+  for (int t = threadIdx.x; t < 3 * len; t += blockDim.x) {
+    const int f = t / len;
+    const size_t e = (size_t)f * nc + p0 + (t - f * len);
+    double2 v = O[e];
+    for (int j = 1; j < i; ++j) {
+      const double2 a = fe[(size_t)j * ns + e], g = fi[(size_t)j * ns + e];
+      v.x = fma(c.nI[i][j], g.x, fma(c.nE[i][j], a.x, v.x));
+      v.y = fma(c.nI[i][j], g.y, fma(c.nE[i][j], a.y, v.y));
+    }
+    sm_th[t] = v;
+  }
+  __syncthreads();
+  band_order_solve(m, T, h, inva2, nu, phibar, cor, band, sm_th, scratch);
+  double2 *out = th + (size_t)i * ns;
+  for (int t = threadIdx.x; t < 3 * len; t += blockDim.x) {
+    const int f = t / len;
+    out[(size_t)f * nc + p0 + (t - f * len)] = sm_th[t];
   }
 }
 

@@ -15,13 +15,13 @@ namespace pfsh {
 // grid products, forward FFT -> analysis of 5 fields -> assembly.
 static int rhs_pass(swe_ctx *c, const double *state, double *fE, double *fI, int B, cudaStream_t s) {
   const sht_plan *p = c->plan;
-  if (small_rhs(B)) return rhs_small(p, state, fE, fI, B, c->prm, s);
+  if (small_rhs(B)) return rhs_small(p, state, fE, fI, B, c->prm, cor_args(c), s);
   int rc;
   if ((rc = rhs_prep(p, state, B, c->prm, s))) return rc;
   if ((rc = legendre_synth(p, 4 * B, s))) return rc;
   if ((rc = grid_rhs(p, B, c->prm, s))) return rc;
   if ((rc = legendre_analysis(p, 5 * B, s))) return rc;
-  return rhs_assemble(p, state, fE, fI, B, c->prm, s);
+  return rhs_assemble(p, state, fE, fI, B, c->prm, cor_args(c), s);
 }
 
 int rhs_eval(swe_ctx *c, const double *state, double *fE, double *fI, int B, cudaStream_t s) {
@@ -145,6 +145,8 @@ using namespace pfsh;
 extern "C" int swe_ctx_create(swe_ctx **out, sht_plan *plan, const swe_params *prm) {
   if (!out || !plan || !prm) return fail(PFSH_EINVAL, "swe_ctx_create: NULL argument");
   if (!(prm->a > 0) || !(prm->nu >= 0)) return fail(PFSH_EINVAL, "swe_ctx_create: need a > 0, nu >= 0");
+  if (prm->coriolis != PFSH_CORIOLIS_EXPLICIT && prm->coriolis != PFSH_CORIOLIS_IMPLICIT)
+    return fail(PFSH_EINVAL, "swe_ctx_create: coriolis must be PFSH_CORIOLIS_EXPLICIT or PFSH_CORIOLIS_IMPLICIT");
   if (plan->max_batch < 5) return fail(PFSH_EINVAL, "swe_ctx_create: plan max_batch must be >= 5");
   if (plan->prec == PFSH_FP16)
     return fail(PFSH_EUNSUPPORTED, "swe_ctx_create: the FP16 form serves transforms only (the flux products "
@@ -154,6 +156,10 @@ extern "C" int swe_ctx_create(swe_ctx **out, sht_plan *plan, const swe_params *p
   c->plan = plan;
   c->prm = *prm;
   c->max_states = plan->max_batch / 5;
+  if (coriolis_implicit(c->prm)) {
+    int rc = band_ctx_init(c);
+    if (rc) { delete c; return rc; }
+  }
   *out = c;
   return PFSH_OK;
 }
@@ -172,6 +178,7 @@ extern "C" int swe_rhs(swe_ctx *c, const double *state, double *fE, double *fI, 
 extern "C" int swe_implicit_solve(swe_ctx *c, const double *b, double *x, double h, int B, pfsh_stream_t stream) {
   if (!c || B < 0 || (B > 0 && (!b || !x)) || !(h >= 0)) return fail(PFSH_EINVAL, "swe_implicit_solve: invalid argument");
   if (B == 0) return PFSH_OK;
+  if (coriolis_implicit(c->prm)) return band_solve_launch(c, b, x, h, B, (cudaStream_t)stream);
   return implicit_solve_launch(c->plan->T, b, x, h, B, c->prm, (cudaStream_t)stream);
 }
 
@@ -221,6 +228,25 @@ extern "C" int sdc_level_create(sdc_level **out, swe_ctx *ctx, int nodes, double
       return fail(PFSH_ECUDA, "sdc_level_create: factors");
     }
   }
+  if (coriolis_implicit(ctx->prm)) {
+    // banded-solve factors of nodes 1..M (h = dt QI[i][i]), computed on the device
+    const size_t per = (size_t)2 * ctx->plan->ncoef;
+    int rc2 = PFSH_OK;
+    if (cudaMalloc(&l->d_band, (size_t)nodes * per * sizeof(double4_32a)) != cudaSuccess) {
+      cudaGetLastError();
+      rc2 = fail(PFSH_ENOMEM, "sdc_level_create: banded factors");
+    }
+    for (int i = 1; i < nodes && rc2 == PFSH_OK; ++i)
+      rc2 = band_factor_launch(ctx, dt * l->QI[i][i], l->d_band + (size_t)i * per, 0);
+    if (rc2 == PFSH_OK && cudaDeviceSynchronize() != cudaSuccess) rc2 = fail(PFSH_ECUDA, "sdc_level_create: factors");
+    if (rc2) {
+      cudaFree(l->d_old);
+      cudaFree(l->d_fac);
+      if (l->d_band) cudaFree(l->d_band);
+      delete l;
+      return rc2;
+    }
+  }
   *out = l;
   return PFSH_OK;
 }
@@ -230,6 +256,7 @@ extern "C" int sdc_level_destroy(sdc_level *l) {
   cudaDeviceSynchronize();
   if (l->d_old) cudaFree(l->d_old);
   if (l->d_fac) cudaFree(l->d_fac);
+  if (l->d_band) cudaFree(l->d_band);
   delete l;
   return PFSH_OK;
 }

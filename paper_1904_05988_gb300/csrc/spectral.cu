@@ -113,12 +113,13 @@ int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &pr
   {
     PFSH_LAUNCH("k_rhs_prep", s);
     if (p->prec == PFSH_FP64)
-      k_rhs_prep<double><<<g, 256, 0, s>>>(p->T, p->ne, B, -prm.a * prm.a, 1.0 / prm.a, prm.omega, prm.phibar,
+      k_rhs_prep<double><<<g, 256, 0, s>>>(p->T, p->ne, B, -prm.a * prm.a, 1.0 / prm.a, omega_explicit(prm),
+                                           prm.phibar,
                                            SpecTables<double>{p->d_eps, p->d_ilap}, (const double2 *)state,
                                            (double2 *)p->X);
     else
-      k_rhs_prep<float><<<g, 256, 0, s>>>(p->T, p->ne, B, (float)(-prm.a * prm.a), (float)(1.0 / prm.a), prm.omega,
-                                          prm.phibar, SpecTables<float>{p->d_eps32, p->d_ilap32},
+      k_rhs_prep<float><<<g, 256, 0, s>>>(p->T, p->ne, B, (float)(-prm.a * prm.a), (float)(1.0 / prm.a),
+                                          omega_explicit(prm), prm.phibar, SpecTables<float>{p->d_eps32, p->d_ilap32},
                                           (const double2 *)state, (float2 *)p->X);
   }
   PFSH_CHECK_LAUNCH("k_rhs_prep");
@@ -135,7 +136,7 @@ int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &pr
 // ---------------------------------------------------------------------------
 template <typename M>
 __global__ void k_rhs_assemble(int T, int B, M inva, M inva2, double dinva2, double nu, double phibar,
-                               const M *__restrict__ eps, const typename cpx<M>::t *__restrict__ Y,
+                               CorArgs cor, const M *__restrict__ eps, const typename cpx<M>::t *__restrict__ Y,
                                const double2 *__restrict__ state, double2 *__restrict__ fE,
                                double2 *__restrict__ fI) {
   typedef typename cpx<M>::t C;
@@ -160,22 +161,23 @@ __global__ void k_rhs_assemble(int T, int B, M inva, M inva2, double dinva2, dou
   oE[idx] = fe[0];
   oE[nc + idx] = fe[1];
   oE[2 * nc + idx] = fe[2];
-  if (fI) linear_point(m, n, state + (size_t)b * 3 * nc, nc, idx, dinva2, nu, phibar, fI + (size_t)b * 3 * nc);
+  if (fI)
+    linear_point(m, n, T, state + (size_t)b * 3 * nc, nc, idx, dinva2, nu, phibar, cor, fI + (size_t)b * 3 * nc);
 }
 
 int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
-                 cudaStream_t s) {
+                 CorArgs cor, cudaStream_t s) {
   dim3 g((p->ncoef + 255) / 256, B);
   const double inva = 1.0 / prm.a, inva2 = 1.0 / (prm.a * prm.a);
   {
     PFSH_LAUNCH("k_rhs_assemble", s);
     if (p->prec == PFSH_FP64)
-      k_rhs_assemble<double><<<g, 256, 0, s>>>(p->T, B, inva, inva2, inva2, prm.nu, prm.phibar, p->d_eps,
+      k_rhs_assemble<double><<<g, 256, 0, s>>>(p->T, B, inva, inva2, inva2, prm.nu, prm.phibar, cor, p->d_eps,
                                                (const double2 *)p->Y, (const double2 *)state, (double2 *)fE,
                                                (double2 *)fI);
     else
       k_rhs_assemble<float><<<g, 256, 0, s>>>(p->T, B, (float)inva, (float)inva2, inva2, prm.nu, prm.phibar,
-                                              p->d_eps32, (const float2 *)p->Y, (const double2 *)state,
+                                              cor, p->d_eps32, (const float2 *)p->Y, (const double2 *)state,
                                               (double2 *)fE, (double2 *)fI);
   }
   PFSH_CHECK_LAUNCH("k_rhs_assemble");
@@ -349,14 +351,18 @@ int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const
   PFSH_CHECK_LAUNCH("k_sdc_old");
   for (int i = 1; i <= M; ++i) {
     dim3 g((nc + 127) / 128, B);
-    {
+    if (coriolis_implicit(ctx->prm)) {
+      int rc = band_sdc_node_launch(l, i, node_stride, c, l->d_old + (size_t)(i - 1) * nc3 * B * 2, fE, fI, theta, B,
+                                    s);
+      if (rc) return rc;
+    } else {
       PFSH_LAUNCH("k_sdc_node", s);
       k_sdc_node<<<g, 128, 0, s>>>(T, B, i, ns, c, c.h[i] * ctx->prm.phibar,
                                    (const double4_32a *)l->d_fac + (size_t)i * (T + 1),
                                    (const double2 *)l->d_old + (size_t)(i - 1) * nc3 * B, (const double2 *)fE,
                                    (const double2 *)fI, (double2 *)theta);
+      PFSH_CHECK_LAUNCH("k_sdc_node");
     }
-    PFSH_CHECK_LAUNCH("k_sdc_node");
     int rc = rhs_eval(l->ctx, theta + (size_t)i * node_stride, fE + (size_t)i * node_stride,
                       fI + (size_t)i * node_stride, B, s);
     if (rc) return rc;

@@ -9,6 +9,7 @@
 //             curl_n = [i m B_n - n eps_{n+1} A_{n+1} + (n+1) eps_n A_{n-1}] / a
 //             F_E = [-div(A2,B2), -div(A1,B1), curl(A1,B1) + n(n+1)/a^2 E]
 //             F_I = [-Phibar delta - nu k Phi, -nu k zeta, k Phi - nu k delta]
+//             (+ the Coriolis tendency C when it is implicit, banded.cuh)
 //
 // The arithmetic type M is the plan's transform type: double for FP64 plans;
 // float for the mixed plans, whose transforms consume and produce float data
@@ -17,6 +18,7 @@
 #pragma once
 
 #include "internal.cuh"
+#include "banded.cuh"
 
 namespace pfsh {
 
@@ -106,15 +108,24 @@ __device__ __forceinline__ void assemble_point(int m, int n, const C cur[5], con
   if (m == 0) { fe[0].y = 0.0; fe[1].y = 0.0; fe[2].y = 0.0; }
 }
 
-// F_I = L(state) at packed index idx (always double)
-__device__ __forceinline__ void linear_point(int m, int n, const double2 *__restrict__ st, int nc, size_t idx,
-                                             double inva2, double nu, double phibar, double2 *__restrict__ oI) {
+// F_I = L(state) (+ C(state) when cor.tw != 0) at packed index idx (always double)
+__device__ __forceinline__ void linear_point(int m, int n, int T, const double2 *__restrict__ st, int nc, size_t idx,
+                                             double inva2, double nu, double phibar, CorArgs cor,
+                                             double2 *__restrict__ oI) {
   double2 Phi = st[idx], zeta = st[nc + idx], delta = st[2 * nc + idx];
   if (m == 0) { Phi.y = 0.0; zeta.y = 0.0; delta.y = 0.0; }
   const double k = (double)n * (n + 1) * inva2, nk = nu * k;
+  double2 oz = make_double2(-nk * zeta.x, -nk * zeta.y);
+  double2 od = make_double2(k * Phi.x - nk * delta.x, k * Phi.y - nk * delta.y);
+  if (cor.tw != 0.0) {
+    double2 cz, cd;
+    coriolis_point(m, n, T, st, nc, idx, cor, &cz, &cd);
+    oz.x += cz.x; oz.y += cz.y;
+    od.x += cd.x; od.y += cd.y;
+  }
   oI[idx] = make_double2(-phibar * delta.x - nk * Phi.x, -phibar * delta.y - nk * Phi.y);
-  oI[nc + idx] = make_double2(-nk * zeta.x, -nk * zeta.y);
-  oI[2 * nc + idx] = make_double2(k * Phi.x - nk * delta.x, k * Phi.y - nk * delta.y);
+  oI[nc + idx] = oz;
+  oI[2 * nc + idx] = od;
 }
 
 }  // namespace pfsh

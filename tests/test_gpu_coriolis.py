@@ -1,0 +1,177 @@
+"""The split with the Coriolis term implicit (F_I = L + C, F_E = N with
+eta = zeta; PFSH_CORIOLIS_IMPLICIT) against the oracle: right-hand sides of
+both RHS paths (batched, and the small-batch path of the coarse chain), the
+banded implicit solve, SDC sweeps (batched node update), and PFASST, whose
+coarse chain solves each order's banded system inside the fused chain step.
+
+Bounds: FP64 as for the paper's split (RHS_TOL for one RHS; 1e-13 for F_I and
+the solve; 1e-12 / 1e-11 for sweeps and PFASST); 3xBF16 as for the paper's
+split (its F_E bound; F_I and the solve stay FP64).
+"""
+import numpy as np
+import pytest
+
+import synthetic as syn
+from oracle.sht import SHT, pack, unpack
+from oracle.swe import SWEParams, rhs, implicit_solve
+from oracle.sdc import SDCLevel
+from oracle.pfasst import PFASST
+from _lib import ensure_built
+
+pytestmark = pytest.mark.gpu
+
+torch = pytest.importorskip("torch")
+ensure_built()
+import paper_1904_05988_gb300 as ps  # noqa: E402
+
+DEV = torch.device("cuda:0")
+A, OM, G = syn.EARTH_RADIUS, syn.OMEGA, syn.GRAVITY
+PHIBAR = G * syn.MEAN_DEPTH
+RHS_TOL = {"fp64": 5e-11, "bf16x3": 2e-2}
+PF_TOL = {"fp64": 1e-11, "bf16x3": 5e-7}
+FORMS = [f for f in ("fp64", "bf16x3") if f in ps.available_precisions()]
+
+
+def rel(a, b):
+    return np.linalg.norm(np.asarray(a) - np.asarray(b)) / max(np.linalg.norm(np.asarray(b)), 1e-300)
+
+
+def cuda(x):
+    return torch.tensor(np.ascontiguousarray(x), dtype=torch.complex128, device=DEV)
+
+
+def state_of(T, seed, batch=1):
+    s = syn.random_spectrum(T, (batch, 3), seed=seed, rms=1e-5)
+    s[:, 0] *= 1e3
+    return s + syn.zonal_jet(T)[None]
+
+
+def oparams(nu=syn.NU):
+    return SWEParams(a=A, omega=OM, g=G, nu=nu, phibar=PHIBAR, coriolis_implicit=True)
+
+
+@pytest.mark.parametrize("form", FORMS)
+@pytest.mark.parametrize("T,B", [(63, 3), (31, 1), (127, 2)])
+def test_coriolis_implicit_rhs_matches_oracle(form, T, B):
+    nlat, nlon = syn.gaussian_grid_size(T)
+    plan = ps.sht_plan_create(T, nlat, nlon, 5 * B, form)
+    ctx = ps.swe_ctx_create(plan, A, OM, syn.NU, PHIBAR, coriolis_implicit=True)
+    st = state_of(T, 300 + T, B)
+    fE = torch.empty((B, 3, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    fI = torch.empty_like(fE)
+    ps.swe_rhs(ctx, cuda(st), fE, fI)
+    ps.pfsh_sync_status()
+    s = SHT(T, nlat, nlon)
+    for b in range(B):
+        FE, FI = rhs(unpack(st[b], T), s, oparams())
+        e_E = rel(fE.cpu().numpy()[b], pack(FE, T))
+        e_I = rel(fI.cpu().numpy()[b], pack(FI, T))
+        assert e_E < RHS_TOL[form], (b, e_E)
+        assert e_I < 1e-13, (b, e_I)
+    print(f"\n[{form} T{T} B{B}] Coriolis implicit: F_E {e_E:.2e}, F_I {e_I:.2e}")
+
+
+@pytest.mark.parametrize("h", [45.0, 3600.0])
+def test_coriolis_banded_solve_matches_oracle_and_aliases(h):
+    """h = 3600 s: 2 Omega h ~ 0.5, far from diagonal dominance."""
+    T = 42
+    nlat, nlon = syn.gaussian_grid_size(T)
+    plan = ps.sht_plan_create(T, nlat, nlon, 5, "fp64")
+    ctx = ps.swe_ctx_create(plan, A, OM, syn.NU, PHIBAR, coriolis_implicit=True)
+    b = state_of(T, 7, 3)
+    x = torch.empty((3, 3, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    ps.swe_implicit_solve(ctx, cuda(b), x, h)
+    bb = cuda(b)
+    ps.swe_implicit_solve(ctx, bb, bb, h)      # in place
+    ps.pfsh_sync_status()
+    ref = pack(implicit_solve(unpack(b, T), h, oparams()), T)
+    assert rel(x.cpu().numpy(), ref) < 1e-13
+    assert torch.equal(x, bb)
+    # the coupling matters at this h: the per-coefficient solve differs
+    diag = pack(implicit_solve(unpack(b, T), h, SWEParams(a=A, omega=OM, g=G, nu=syn.NU, phibar=PHIBAR)), T)
+    assert rel(diag, ref) > 1e-9
+
+
+@pytest.mark.parametrize("B", [3, 1])
+def test_coriolis_sdc_sweeps_with_tau_match_oracle(B):
+    T, nodes, dt = 31, 5, 600.0
+    nlat, nlon = syn.gaussian_grid_size(T)
+    plan = ps.sht_plan_create(T, nlat, nlon, 10, "fp64")
+    ctx = ps.swe_ctx_create(plan, A, OM, syn.NU, PHIBAR, coriolis_implicit=True)
+    lvl = ps.sdc_level_create(ctx, nodes, dt, B)
+    st = state_of(T, 13, B)
+    tau = syn.random_spectrum(T, (nodes, B, 3), seed=14, rms=1e-9)
+    tau[0] = 0
+    th = torch.empty((nodes, B, 3, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    fE, fI = torch.empty_like(th), torch.empty_like(th)
+    ps.sdc_spread(lvl, cuda(st), th, fE, fI)
+    ps.sdc_sweep(lvl, th, fE, fI, cuda(tau))
+    ps.sdc_sweep(lvl, th, fE, fI, cuda(tau))
+    ps.pfsh_sync_status()
+    lv = SDCLevel(T, nlat, nlon, nodes, dt, oparams())
+    for b in range(B):
+        t_, e_, i_ = lv.spread(unpack(st[b], T))
+        for _ in range(2):
+            t_, e_, i_ = lv.sweep(t_, e_, i_, unpack(tau[:, b], T))
+        assert rel(th.cpu().numpy()[:, b], pack(t_, T)) < 1e-12
+        assert rel(fI.cpu().numpy()[:, b], pack(i_, T)) < 1e-12
+        assert rel(fE.cpu().numpy()[:, b], pack(e_, T)) < 1e-11
+
+
+@pytest.mark.parametrize("Tf,Tc,nts,groups", [(21, 10, 4, 0), (21, 10, 9, 2)])
+def test_coriolis_pfasst_matches_oracle(Tf, Tc, nts, groups):
+    dt, nf, nc, iters = 600.0, 5, 3, 3
+    gf, gc = syn.gaussian_grid_size(Tf), syn.gaussian_grid_size(Tc)
+    st0 = state_of(Tf, 22)[0]
+    pf = ps.pfasst_create(nts, nf, nc, Tf, *gf, Tc, *gc, dt, A, OM, syn.NU, PHIBAR, "fp64", slice_groups=groups,
+                          coriolis_implicit=True)
+    ps.pfasst_set_initial(pf, cuda(st0))
+    ps.pfasst_predict(pf)
+    o = PFASST(SDCLevel(Tf, *gf, nf, dt, oparams()), SDCLevel(Tc, *gc, nc, dt, oparams()), nts)
+    o.predict(unpack(st0, Tf))
+    out = torch.empty((3, syn.ncoef(Tf)), dtype=torch.complex128, device=DEV)
+    outc = torch.empty((3, syn.ncoef(Tc)), dtype=torch.complex128, device=DEV)
+
+    def compare(tol):
+        for n in range(nts):
+            for k in range(nf):
+                ps.pfasst_get(pf, 0, n, k, out)
+                assert rel(out.cpu().numpy(), pack(o.th_f[n, k], Tf)) < tol, (n, k)
+            ps.pfasst_get(pf, 1, n, nc - 1, outc)
+            assert rel(outc.cpu().numpy(), pack(o.th_c[n, nc - 1], Tc)) < tol, n
+
+    compare(1e-12)
+    for it in range(iters):
+        last = it == iters - 1
+        ps.pfasst_iteration(pf, last)
+        o.iteration(last)
+        ps.pfsh_sync_status()
+        compare(PF_TOL["fp64"])
+    pf.close()
+
+
+@pytest.mark.parametrize("form", FORMS)
+def test_coriolis_pfasst_two_iterations_mixed(form):
+    """T63/T31, 4 slices: end values and their change from the initial value,
+    through the graph-captured block of iterations."""
+    Tf, Tc, nts, dt = 63, 31, 4, 600.0
+    gf, gc = syn.gaussian_grid_size(Tf), syn.gaussian_grid_size(Tc)
+    st0 = state_of(Tf, 43)[0]
+    pf = ps.pfasst_create(nts, 5, 3, Tf, *gf, Tc, *gc, dt, A, OM, syn.NU, PHIBAR, form, coriolis_implicit=True)
+    for _ in range(3):     # eager, capture, replay
+        ps.pfasst_set_initial(pf, cuda(st0))
+        ps.pfasst_predict(pf)
+        ps.pfasst_iterations(pf, 2, True)
+    ps.pfsh_sync_status()
+    o = PFASST(SDCLevel(Tf, *gf, 5, dt, oparams()), SDCLevel(Tc, *gc, 3, dt, oparams()), nts)
+    ref = o.run(unpack(st0, Tf), 2)
+    out = torch.empty((3, syn.ncoef(Tf)), dtype=torch.complex128, device=DEV)
+    errs = []
+    for n in range(nts):
+        ps.pfasst_get(pf, 0, n, 4, out)
+        errs.append(rel(out.cpu().numpy(), pack(ref[n], Tf)))
+    e_inc = rel(out.cpu().numpy() - st0, pack(ref[nts - 1], Tf) - st0)
+    print(f"\n[{form}] Coriolis implicit PFASST end values {max(errs):.2e}, increment {e_inc:.2e}")
+    assert max(errs) < PF_TOL[form]
+    assert e_inc < 1e3 * PF_TOL[form]
+    pf.close()
