@@ -194,9 +194,9 @@ def run_ours(args, rank, world, local_rank):
 
     st0, phibar = initial_state(ps, torch, dev, seed=2 + rank)
 
-    def make(prec):
+    def make(prec, **kw):
         return ps.pfasst_create(NTS, NF, NC, TF, *GRID_F, TC, *GRID_C, DT, syn.EARTH_RADIUS, syn.OMEGA, syn.NU,
-                                phibar, prec)
+                                phibar, prec, **kw)
 
     pf = make(args.prec)
     d_st0 = torch.tensor(st0, dtype=torch.complex128, device=dev)
@@ -301,6 +301,27 @@ def run_ours(args, rank, world, local_rank):
                 "what": f"end value of slice {NTS - 1} after predictor + {NPF} iterations: relative L2 difference of "
                         "the state, and of its change from the initial value (bump + jet evolution)"}
 
+    # ---- the same workload with the Coriolis term implicit / the two-substep node solve ----
+    variants = None
+    if not args.no_variants:
+        variants = {}
+        for name, kw in (("coriolis_implicit", {"coriolis_implicit": True}), ("implicit_split", {"implicit_split": True}),
+                         ("coriolis_implicit+implicit_split", {"coriolis_implicit": True, "implicit_split": True})):
+            pv = make(args.prec, **kw)
+            ps.pfasst_set_initial(pv, d_st0)
+            ps.pfasst_predict(pv)
+            kv = max(2, min(10, args.steps))
+            prepare_block(ps, pv, kv, 1)
+            msv = time_iterations(ps, torch, pv, stream, kv) / kv
+            block_solve(ps, torch, pv, h_in, h_out, d_in, d_out)
+            torch.cuda.synchronize()
+            alt = h_out.numpy()
+            pv.close()
+            variants[name] = {
+                "value": world * 1e3 / msv, "unit": "PFASST iterations/s", "ms_per_step": msv, "steps": kv,
+                "end_state_change_rel_l2_vs_headline": float(np.linalg.norm((alt - st0) - (end_state - st0))
+                                                             / np.linalg.norm(end_state - st0))}
+
     cpu = cpu_baseline_sample() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
         dtype = "f64" if args.prec == "fp64" else \
@@ -318,6 +339,7 @@ def run_ours(args, rank, world, local_rank):
                                 "slice groups in a wavefront across iterations)"},
             "swe_rhs_evals_per_s": rhs_per_s,
             "fp64_gpu_path": fp64,
+            "variants": variants,
             "e2e": {"value": e2e_val, "unit": "PFASST iterations/s", "h2d_bytes_per_step": state_bytes,
                     "d2h_bytes_per_step": state_bytes,
                     "what": f"per block: H2D initial value, predictor, {NPF} iterations, D2H last slice end value"},
@@ -545,6 +567,8 @@ def main():
     ap.add_argument("--warmup", type=int, default=3)
     ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "fp16", "bf16x3"])
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the FP64 GPU path")
+    ap.add_argument("--no-variants", action="store_true",
+                    help="skip timing the Coriolis-implicit and two-substep variants of the workload")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()

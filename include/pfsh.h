@@ -141,6 +141,15 @@ typedef struct {
   double nu;     /* second-order diffusion coefficient [m^2/s]               */
   double phibar; /* mean geopotential Phibar = g hbar [m^2/s^2]              */
   int coriolis;  /* PFSH_CORIOLIS_EXPLICIT (0) or PFSH_CORIOLIS_IMPLICIT     */
+  int implicit_split; /* SDC node solve (Section 5.1.1): 0 = one solve of
+                 * x - h F_I(x) = b; 1 = two substeps, the physical linear
+                 * terms (gravity waves, plus Coriolis when implicit) with the
+                 * diffusion of the previous iterate, then the diffusion:
+                 *   x* - h L0(x*) = b + h D(old),  x - h D(x) = x* - h D(old)
+                 * (D = the diffusion part of F_I; each substep carries its
+                 * own correction term, so converged sweeps reach the same
+                 * collocation solution).  swe_implicit_solve always solves
+                 * x - h F_I(x) = b in one step.                              */
 } swe_params;
 
 /* The context keeps a reference to `plan` (which must outlive it) and owns

@@ -39,7 +39,7 @@ from numpy.polynomial import Polynomial
 from numpy.polynomial import legendre as npleg
 
 from .sht import SHT
-from .swe import SWEParams, implicit_solve, rhs
+from .swe import SWEParams, implicit_solve, implicit_solve_split, rhs
 
 
 def lobatto_nodes(num_nodes: int) -> np.ndarray:
@@ -144,7 +144,10 @@ class SDCLevel:
                 b += dt * Q[i, j] * (FE[j] + FI[j])
             if tau is not None:
                 b += tau[i]
-            th_new[i] = implicit_solve(b, dt * QI[i, i], self.p)
+            if self.p.implicit_split:
+                th_new[i] = implicit_solve_split(b, dt * QI[i, i], theta[i], self.p)
+            else:
+                th_new[i] = implicit_solve(b, dt * QI[i, i], self.p)
             FE_new[i], FI_new[i] = self.eval_f(th_new[i])
         return th_new, FE_new, FI_new
 

@@ -67,6 +67,7 @@ class SWEParams:
     nu: float          # diffusion coefficient [m^2/s]
     phibar: float      # mean geopotential Phibar = g hbar
     coriolis_implicit: bool = False   # Coriolis tendency in F_I instead of F_E
+    implicit_split: bool = False      # SDC node solve in two substeps (see sdc.py)
 
 
 def kappa(L: int, a: float) -> np.ndarray:
@@ -236,6 +237,11 @@ def rhs(state: np.ndarray, sht: SHT, p: SWEParams) -> tuple[np.ndarray, np.ndarr
     return nonlinear_part(state, sht, p), linear_part(state, p)
 
 
+def diffusion_part(state: np.ndarray, p: SWEParams) -> np.ndarray:
+    """The diffusion terms of F_I, nu lap [Phi', zeta, delta] = -nu k state."""
+    return -p.nu * kappa(state.shape[-1], p.a) * state
+
+
 def implicit_solve(b: np.ndarray, h: float, p: SWEParams) -> np.ndarray:
     """x with x - h L(x) = b (Section 5.4, Eq. "implicit_systems").
 
@@ -258,6 +264,21 @@ def implicit_solve(b: np.ndarray, h: float, p: SWEParams) -> np.ndarray:
 
 
 _order_inverses: dict = {}
+
+
+def implicit_solve_split(b: np.ndarray, h: float, old: np.ndarray, p: SWEParams) -> np.ndarray:
+    """The node solve of an SDC sweep in two substeps, physical linear terms
+    first, then diffusion (Section 5.1.1; reading: each substep carries its
+    own correction term, as in multi-implicit SDC, so that the fixed point of
+    the sweep is unchanged).  With D = the diffusion part of F_I, F_I = L0 + D
+    (L0: gravity waves, plus Coriolis when it is implicit) and `old` the
+    previous iterate of the node, whose right-hand side b already contains
+    -h F_I(old):
+        x* - h L0(x*) = b + h D(old),      x - h D(x) = x* - h D(old)."""
+    from dataclasses import replace
+    xs = implicit_solve(b + h * diffusion_part(old, p), h, replace(p, nu=0.0))
+    s = 1.0 + h * p.nu * kappa(b.shape[-1], p.a)
+    return (xs - h * diffusion_part(old, p)) / s
 
 
 def _implicit_solve_orders(b: np.ndarray, h: float, p: SWEParams) -> np.ndarray:

@@ -55,7 +55,8 @@ PFSH_CORIOLIS_EXPLICIT, PFSH_CORIOLIS_IMPLICIT = 0, 1
 
 
 class SweParams(ctypes.Structure):
-    _fields_ = [("a", c_double), ("omega", c_double), ("nu", c_double), ("phibar", c_double), ("coriolis", c_int)]
+    _fields_ = [("a", c_double), ("omega", c_double), ("nu", c_double), ("phibar", c_double), ("coriolis", c_int),
+                ("implicit_split", c_int)]
 
 
 class ShtInfo(ctypes.Structure):
@@ -269,8 +270,9 @@ def sht_forward(plan: ShtPlan, grid: torch.Tensor, spec: torch.Tensor, stream=No
 
 
 def swe_ctx_create(plan: ShtPlan, a: float, omega: float, nu: float, phibar: float,
-                   coriolis_implicit: bool = False) -> SweCtx:
-    p = SweParams(a, omega, nu, phibar, PFSH_CORIOLIS_IMPLICIT if coriolis_implicit else PFSH_CORIOLIS_EXPLICIT)
+                   coriolis_implicit: bool = False, implicit_split: bool = False) -> SweCtx:
+    p = SweParams(a, omega, nu, phibar, PFSH_CORIOLIS_IMPLICIT if coriolis_implicit else PFSH_CORIOLIS_EXPLICIT,
+                  int(implicit_split))
     h = c_void_p()
     _check(_lib.swe_ctx_create(ctypes.byref(h), plan.ptr, ctypes.byref(p)))
     return SweCtx(h.value, plan, p)
@@ -318,9 +320,9 @@ def sdc_sweep(level: SdcLevel, theta: torch.Tensor, fE: torch.Tensor, fI: torch.
 def pfasst_create(n_ts: int, fine_nodes: int, coarse_nodes: int, Tf: int, nlat_f: int, nlon_f: int,
                   Tc: int, nlat_c: int, nlon_c: int, dt: float, a: float, omega: float, nu: float,
                   phibar: float, prec: int | str = PFSH_FP64, slice_groups: int = 0,
-                  coriolis_implicit: bool = False) -> Pfasst:
+                  coriolis_implicit: bool = False, implicit_split: bool = False) -> Pfasst:
     cfg = pfasst_config(n_ts, fine_nodes, coarse_nodes, Tf, nlat_f, nlon_f, Tc, nlat_c, nlon_c, dt, a, omega, nu,
-                        phibar, prec, slice_groups, coriolis_implicit)
+                        phibar, prec, slice_groups, coriolis_implicit, implicit_split)
     h = c_void_p()
     _check(_lib.pfasst_create(ctypes.byref(h), ctypes.byref(cfg)))
     return Pfasst(h.value, cfg)
@@ -352,11 +354,11 @@ def pfasst_residual(pf: Pfasst, res: torch.Tensor, stream=None) -> torch.Tensor:
 def pfasst_config(n_ts: int, fine_nodes: int, coarse_nodes: int, Tf: int, nlat_f: int, nlon_f: int,
                   Tc: int, nlat_c: int, nlon_c: int, dt: float, a: float, omega: float, nu: float,
                   phibar: float, prec: int | str = PFSH_FP64, slice_groups: int = 0,
-                  coriolis_implicit: bool = False) -> PfasstConfig:
+                  coriolis_implicit: bool = False, implicit_split: bool = False) -> PfasstConfig:
     prec = PREC_NAMES[prec] if isinstance(prec, str) else prec
     cor = PFSH_CORIOLIS_IMPLICIT if coriolis_implicit else PFSH_CORIOLIS_EXPLICIT
     return PfasstConfig(n_ts, fine_nodes, coarse_nodes, Tf, nlat_f, nlon_f, Tc, nlat_c, nlon_c, dt,
-                        SweParams(a, omega, nu, phibar, cor), prec, slice_groups)
+                        SweParams(a, omega, nu, phibar, cor, int(implicit_split)), prec, slice_groups)
 
 
 def pfasst_ensemble_create(cfgs: list) -> PfasstEnsemble:

@@ -37,14 +37,19 @@ __global__ void k_band_factor(int T, double h, double inva2, double nu, double p
   }
 }
 
-__host__ __device__ inline size_t band_rhs_bytes(int T) { return ((size_t)3 * (T + 1) * sizeof(double2) + 31) & ~size_t(31); }
+// right-hand sides [3][T+1] of one order, rounded up to 32 bytes
+__host__ __device__ inline size_t band_rhs_bytes(int T) {
+  return ((size_t)3 * (T + 1) * sizeof(double2) + 31) & ~size_t(31);
+}
 
 // One block per (order m, state b).  SDC = false: x = solve(b) (in may alias
 // out: the block reads its whole column before writing).  SDC = true: the
 // right-hand side of node i is O_i + sum_{1<=j<i} nE[i][j] F_E,j + nI[i][j]
 // F_I,j (in = O of node i [B][3nc], fe/fi node-major with stride ns) and the
-// result goes to out = theta of node i.
-template <bool SDC>
+// result goes to out = theta of node i.  SPLIT (with SDC): two substeps,
+// x* = the nu = 0 solve of r - h nu k old (tab built with nu = 0), then
+// x = (x* + h nu k old) / (1 + h nu k), old = theta of node i on entry.
+template <bool SDC, bool SPLIT>
 __global__ void __launch_bounds__(128) k_band_node(int T, int i, size_t ns, SdcCoef coef, double h, double inva2,
                                                    double nu, double phibar, CorArgs cor,
                                                    const double4_32a *__restrict__ tab, const double2 *in,
@@ -65,13 +70,28 @@ __global__ void __launch_bounds__(128) k_band_node(int T, int i, size_t ns, SdcC
         v.y = fma(coef.nI[i][j], g.y, fma(coef.nE[i][j], a.y, v.y));
       }
     }
+    if (SPLIT) {
+      const int n = m + (t - f * K);
+      const double hnk = h * nu * ((double)n * (n + 1) * inva2);
+      const double2 o = out[e];
+      v.x = fma(-hnk, o.x, v.x);
+      v.y = fma(-hnk, o.y, v.y);
+    }
     sr[t] = v;
   }
   __syncthreads();
-  band_order_solve(m, T, h, inva2, nu, phibar, cor, tab, sr, smem_raw + band_rhs_bytes(T));
+  band_order_solve(m, T, h, inva2, SPLIT ? 0.0 : nu, phibar, cor, tab, sr, smem_raw + band_rhs_bytes(T));
   for (int t = threadIdx.x; t < 3 * K; t += blockDim.x) {
     const int f = t / K;
-    out[base + (size_t)f * nc + (t - f * K)] = sr[t];
+    const size_t e = base + (size_t)f * nc + (t - f * K);
+    double2 x = sr[t];
+    if (SPLIT) {
+      const int n = m + (t - f * K);
+      const double hnk = h * nu * ((double)n * (n + 1) * inva2), is = 1.0 / (1.0 + hnk);
+      const double2 o = out[e];
+      x = make_double2(fma(hnk, o.x, x.x) * is, fma(hnk, o.y, x.y) * is);
+    }
+    out[e] = x;
   }
 }
 
@@ -97,29 +117,29 @@ int band_ctx_init(swe_ctx *c) {
   return PFSH_OK;
 }
 
-int band_factor_launch(const swe_ctx *c, double h, double4_32a *tab, cudaStream_t s) {
+int band_factor_launch(const swe_ctx *c, double h, double nu, double4_32a *tab, cudaStream_t s) {
   const int T = c->plan->T;
   const swe_params &p = c->prm;
   {
     PFSH_LAUNCH("k_band_factor", s);
-    k_band_factor<<<(2 * (T + 1) + 63) / 64, 64, 0, s>>>(T, h, 1.0 / (p.a * p.a), p.nu, p.phibar, cor_args(c), tab);
+    k_band_factor<<<(2 * (T + 1) + 63) / 64, 64, 0, s>>>(T, h, 1.0 / (p.a * p.a), nu, p.phibar, cor_args(c), tab);
   }
   PFSH_CHECK_LAUNCH("k_band_factor");
   return PFSH_OK;
 }
 
-template <bool SDC>
+template <bool SDC, bool SPLIT>
 static int band_node_launch(const swe_ctx *c, int i, size_t ns, const SdcCoef &coef, double h,
                             const double4_32a *tab, const double *in, const double *fe, const double *fi, double *out,
                             int B, cudaStream_t s) {
   const int T = c->plan->T;
   const swe_params &p = c->prm;
   const size_t smem = band_rhs_bytes(T) + band_scratch_bytes(T);
-  int rc = ensure_smem((const void *)k_band_node<SDC>, smem);
+  int rc = ensure_smem((const void *)k_band_node<SDC, SPLIT>, smem);
   if (rc) return rc;
   {
     PFSH_LAUNCH("k_band_node", s);
-    k_band_node<SDC><<<dim3(T + 1, B), 128, smem, s>>>(T, i, ns, coef, h, 1.0 / (p.a * p.a), p.nu, p.phibar,
+    k_band_node<SDC, SPLIT><<<dim3(T + 1, B), 128, smem, s>>>(T, i, ns, coef, h, 1.0 / (p.a * p.a), p.nu, p.phibar,
                                                        cor_args(c), tab, (const double2 *)in, (const double2 *)fe,
                                                        (const double2 *)fi, (double2 *)out);
   }
@@ -128,18 +148,18 @@ static int band_node_launch(const swe_ctx *c, int i, size_t ns, const SdcCoef &c
 }
 
 int band_solve_launch(const swe_ctx *c, const double *b, double *x, double h, int B, cudaStream_t s) {
-  int rc = band_factor_launch(c, h, c->d_band_scr, s);
+  int rc = band_factor_launch(c, h, c->prm.nu, c->d_band_scr, s);
   if (rc) return rc;
   SdcCoef none = {};
-  return band_node_launch<false>(c, 0, 0, none, h, c->d_band_scr, b, nullptr, nullptr, x, B, s);
+  return band_node_launch<false, false>(c, 0, 0, none, h, c->d_band_scr, b, nullptr, nullptr, x, B, s);
 }
 
 int band_sdc_node_launch(const sdc_level *l, int i, size_t node_stride, const SdcCoef &coef, const double *O,
                          const double *fE, const double *fI, double *theta, int B, cudaStream_t s) {
   const swe_ctx *c = l->ctx;
-  return band_node_launch<true>(c, i, node_stride / 2, coef, coef.h[i],
-                                l->d_band + (size_t)i * 2 * c->plan->ncoef, O, fE, fI,
-                                theta + (size_t)i * node_stride, B, s);
+  auto launch = c->prm.implicit_split ? band_node_launch<true, true> : band_node_launch<true, false>;
+  return launch(c, i, node_stride / 2, coef, coef.h[i], l->d_band + (size_t)i * 2 * c->plan->ncoef, O, fE, fI,
+                theta + (size_t)i * node_stride, B, s);
 }
 
 }  // namespace pfsh

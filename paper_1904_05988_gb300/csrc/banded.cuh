@@ -23,7 +23,8 @@
 // Chain c, position j: degree n = m + j, field (j + c) & 1 (0 zeta, 1 delta).
 // Forward elimination with w_j = D_j - a_j c'_{j-1}, c'_j = c_j / w_j,
 // y_j = (r_j - a_j y_{j-1}) / w_j, then x_j = y_j - c'_j x_{j+1}.
-// The factors {c'_j, 1/w_j} depend on h only: one table per SDC node.
+// The factors {c'_j, 1/w_j} depend on h only: one table per SDC node; the
+// two substitution passes run as warp scans (band_chain_scan).
 #pragma once
 
 #include "internal.cuh"
@@ -58,11 +59,97 @@ __host__ __device__ inline size_t band_scratch_bytes(int T) {
   return (size_t)(T + 1) * (2 * sizeof(double4_32a) + sizeof(double)) + 32;
 }
 
+// complex FP64 helpers of the chain scans
+__device__ __forceinline__ double2 zmul(double2 a, double2 b) {
+  return make_double2(fma(a.x, b.x, -a.y * b.y), fma(a.x, b.y, a.y * b.x));
+}
+__device__ __forceinline__ double2 zfma(double2 a, double2 b, double2 c) {   // a b + c
+  return make_double2(fma(a.x, b.x, fma(-a.y, b.y, c.x)), fma(a.x, b.y, fma(a.y, b.x, c.y)));
+}
+__device__ __forceinline__ double2 zshfl_up(double2 v, int d) {
+  return make_double2(__shfl_up_sync(0xffffffffu, v.x, d), __shfl_up_sync(0xffffffffu, v.y, d));
+}
+__device__ __forceinline__ double2 zshfl_down(double2 v, int d) {
+  return make_double2(__shfl_down_sync(0xffffffffu, v.x, d), __shfl_down_sync(0xffffffffu, v.y, d));
+}
+
+// One chain (c) of an order, solved by one warp.  Both elimination passes
+// are first-order affine recurrences,
+//   forward  y_j = al_j y_{j-1} + be_j,  al_j = -a_j / w_j, be_j = r_j / w_j,  y_{-1} = 0
+//   backward x_j = ga_j x_{j+1} + y_j,   ga_j = -c'_j,                        x_K = 0,
+// evaluated as scans: lane l takes the segment [l S, (l+1) S) (S = ceil(K/32)),
+// composes its affine maps, the lanes combine the composites in log2(32)
+// shuffle steps, and each lane re-runs its segment from its incoming value.
+// A sequential elimination would chain K dependent FP64 steps; this chains
+// about 2 S + 5.  sr[1 + field][j] holds r on entry, x on return.
+__device__ __forceinline__ void band_chain_scan(int c, int lane, int K, const double4_32a *stab, const double *sal,
+                                                double2 *sr) {
+  const int S = (K + 31) >> 5, j0 = min(K, lane * S), j1 = min(K, j0 + S);
+  auto coefs = [&](int j, double2 *al, double2 *be) {
+    const int f = (j + c) & 1;
+    const double4_32a q = stab[f * K + j];
+    const double a = f ? -sal[j] : sal[j];
+    const double2 iw = make_double2(q.z, q.w), r = sr[(1 + f) * K + j];
+    *al = make_double2(-a * iw.x, -a * iw.y);
+    *be = zmul(r, iw);
+  };
+  // forward: composite of the lane's maps, inclusive scan, re-run
+  double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
+  for (int j = j0; j < j1; ++j) {
+    double2 al, be;
+    coefs(j, &al, &be);
+    A = zmul(al, A);
+    B = zfma(al, B, be);
+  }
+  for (int d = 1; d < 32; d <<= 1) {
+    const double2 Ap = zshfl_up(A, d), Bp = zshfl_up(B, d);
+    if (lane >= d) {
+      B = zfma(A, Bp, B);
+      A = zmul(A, Ap);
+    }
+  }
+  double2 y = zshfl_up(B, 1);
+  if (lane == 0) y = make_double2(0.0, 0.0);
+  for (int j = j0; j < j1; ++j) {
+    double2 al, be;
+    coefs(j, &al, &be);
+    y = zfma(al, y, be);
+    sr[(1 + ((j + c) & 1)) * K + j] = y;
+  }
+  // backward: maps x_{j+1} -> x_j composed from the right, suffix scan, re-run
+  A = make_double2(1.0, 0.0);
+  B = make_double2(0.0, 0.0);
+  for (int j = j1 - 1; j >= j0; --j) {
+    const int f = (j + c) & 1;
+    const double4_32a q = stab[f * K + j];
+    const double2 ga = make_double2(-q.x, -q.y);
+    A = zmul(ga, A);
+    B = zfma(ga, B, sr[(1 + f) * K + j]);
+  }
+  for (int d = 1; d < 32; d <<= 1) {
+    const double2 An = zshfl_down(A, d), Bn = zshfl_down(B, d);
+    if (lane + d < 32) {
+      B = zfma(A, Bn, B);
+      A = zmul(A, An);
+    }
+  }
+  double2 x = zshfl_down(B, 1);
+  if (lane == 31) x = make_double2(0.0, 0.0);
+  for (int j = j1 - 1; j >= j0; --j) {
+    const int f = (j + c) & 1;
+    const double4_32a q = stab[f * K + j];
+    double2 *p = sr + (1 + f) * K + j;
+    x = zfma(make_double2(-q.x, -q.y), x, *p);
+    *p = x;
+  }
+}
+
 // Solve the order-m system in place.  sr[3][K] (Phi, zeta, delta rows of
 // order m, K = T+1-m) holds b on entry and x on return; tab = the node's
 // factor table [2][nc] (zeta rows, delta rows); scratch = band_scratch_bytes(T)
-// of shared memory (any 16-byte alignment).  Called by every thread of the
-// block; ends with a barrier.
+// of shared memory (any 16-byte alignment).  Called by every thread of a
+// block of at least 64 threads (warps 0 and 1 solve the two chains); ends
+// with a barrier.
 __device__ __forceinline__ void band_order_solve(int m, int T, double h, double inva2, double nu, double phibar,
                                                  CorArgs cor, const double4_32a *__restrict__ tab, double2 *sr,
                                                  void *scratch) {
@@ -81,28 +168,7 @@ __device__ __forceinline__ void band_order_solve(int m, int T, double h, double 
     sal[j] = th * cor.ab[p0 + j].x;
   }
   __syncthreads();
-  if (threadIdx.x < 2) {
-    const int c = threadIdx.x;
-    double2 y = make_double2(0.0, 0.0);
-    for (int j = 0; j < K; ++j) {
-      const int f = (j + c) & 1;
-      const double a = f ? -sal[j] : sal[j];
-      const double4_32a q = stab[f * K + j];
-      double2 *x = sr + (1 + f) * K + j;
-      const double rx = fma(-a, y.x, x->x), ry = fma(-a, y.y, x->y);
-      y = make_double2(fma(rx, q.z, -ry * q.w), fma(rx, q.w, ry * q.z));
-      *x = y;
-    }
-    double2 xn = make_double2(0.0, 0.0);
-    for (int j = K - 1; j >= 0; --j) {
-      const int f = (j + c) & 1;
-      const double4_32a q = stab[f * K + j];
-      double2 *x = sr + (1 + f) * K + j;
-      const double2 v = *x;
-      xn = make_double2(v.x - fma(q.x, xn.x, -q.y * xn.y), v.y - fma(q.x, xn.y, q.y * xn.x));
-      *x = xn;
-    }
-  }
+  if (threadIdx.x < 64) band_chain_scan(threadIdx.x >> 5, threadIdx.x & 31, K, stab, sal, sr);
   __syncthreads();
   for (int j = threadIdx.x; j < K; j += blockDim.x) {
     const int n = m + j;

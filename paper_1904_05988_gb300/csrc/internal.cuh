@@ -234,7 +234,7 @@ struct sdc_level {
   double tau_nodes[16];
   double Q[16][16], QE[16][16], QI[16][16];
   double *d_old = nullptr;   // [M][max_batch][3][ncoef] c128: node-update constants
-  double *d_fac = nullptr;   // [M+1][T+1][4] implicit-solve factors per node and degree
+  double *d_fac = nullptr;   // [M+1][T+1][4] implicit-solve factors per node and degree (solver.cu)
   double4_32a *d_band = nullptr;   // Coriolis implicit: [M+1][2][ncoef] banded-solve factors per node
 };
 
@@ -367,7 +367,7 @@ int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI,
 
 // banded implicit solve of the split with the Coriolis term implicit (banded.cu)
 int band_ctx_init(swe_ctx *c);
-int band_factor_launch(const swe_ctx *c, double h, double4_32a *tab, cudaStream_t s);
+int band_factor_launch(const swe_ctx *c, double h, double nu, double4_32a *tab, cudaStream_t s);
 int band_solve_launch(const swe_ctx *c, const double *b, double *x, double h, int B, cudaStream_t s);
 int band_sdc_node_launch(const sdc_level *l, int i, size_t node_stride, const SdcCoef &coef, const double *O,
                          const double *fE, const double *fI, double *theta, int B, cudaStream_t s);

@@ -136,6 +136,7 @@ struct ChainGeo {
   size_t work;                // bytes of the body work region
   R ma2, inva, inva2;
   double dinva2, omega, nu, phibar;
+  bool split;                 // two-substep node solve
   CorArgs cor;
   SpecTables<R> tb;
   const R *P;
@@ -179,11 +180,11 @@ __global__ void __launch_bounds__(kChainThreads) k_chain_node(ChainStep st, Chai
     __syncthreads();
   }
   if (g.cor.tw != 0.0)   // the analysis is done: its work region holds the banded solve's scratch
-    order_node_update_band(m, T, st.k, st.ns, c, st.h, g.dinva2, g.nu, g.phibar, g.cor, st.band,
+    order_node_update_band(m, T, st.k, st.ns, c, st.h, g.dinva2, g.nu, g.phibar, g.split, g.cor, st.band,
                            st.O + (size_t)(st.k - 1) * 3 * nc, st.fe, st.fi, st.th, thk, work);
   else
-    order_node_update(m, T, st.k, st.ns, c, st.hphibar, st.fac, st.O + (size_t)(st.k - 1) * 3 * nc, st.fe, st.fi,
-                      st.th, thk);
+    order_node_update(m, T, st.k, st.ns, c, st.hphibar, g.split, st.fac, st.O + (size_t)(st.k - 1) * 3 * nc, st.fe,
+                      st.fi, st.th, thk);
   __syncthreads();
   // rows issued in the prologue: complete after the analysis, else in flight
   const int pmode = anal ? (K <= g.rows ? STAGE_DONE : STAGE_SELF) : STAGE_ISSUED;
@@ -221,7 +222,7 @@ static ChainGeo<R> chain_geo(const swe_ctx *ctx, const R *P, SpecTables<R> tb) {
   const swe_params &prm = ctx->prm;
   const double inva2 = 1.0 / (prm.a * prm.a);
   return ChainGeo<R>{p->T, p->nlat, 0, 0, (R)(-prm.a * prm.a), (R)(1.0 / prm.a), (R)inva2, inva2, omega_explicit(prm),
-                     prm.nu, prm.phibar, cor_args(ctx), tb, P, (C *)p->F, (const C *)p->H};
+                     prm.nu, prm.phibar, prm.implicit_split != 0, cor_args(ctx), tb, P, (C *)p->F, (const C *)p->H};
 }
 
 template <typename R>

@@ -338,12 +338,14 @@ __device__ __forceinline__ void order_old_part(int m, int T, int M, size_t ns, c
 }
 
 // theta_i = solve(O_i + sum_{1<=j<i} nE[i][j] F_E,j + nI[i][j] F_I,j, h_i)
-// with fac[n] = {s = 1 + h nu k, 1/s, 1/(s^2 + h^2 Phibar k), h k} of node i
-// (also written to sm_th[field][n - m] when given)
+// with the factors fac[n] of node i (the element-wise kernel k_sdc_node
+// documents both layouts: one solve, or two substeps when `split`), also
+// written to sm_th[field][n - m] when given
 __device__ __forceinline__ void order_node_update(int m, int T, int i, size_t ns, const SdcCoef &c, double hphibar,
-                                                  const double4_32a *__restrict__ fac, const double2 *__restrict__ O,
-                                                  const double2 *__restrict__ fe, const double2 *__restrict__ fi,
-                                                  double2 *__restrict__ th, double2 *sm_th) {
+                                                  bool split, const double4_32a *__restrict__ fac,
+                                                  const double2 *__restrict__ O, const double2 *__restrict__ fe,
+                                                  const double2 *__restrict__ fi, double2 *__restrict__ th,
+                                                  double2 *sm_th) {
   const int nc = ncoef_of(T), p0 = poff(T, m), len = T + 1 - m;
   double2 *out = th + (size_t)i * ns;
   for (int t = threadIdx.x; t < len; t += blockDim.x) {
@@ -361,9 +363,24 @@ __device__ __forceinline__ void order_node_update(int m, int T, int i, size_t ns
       r[f] = v;
     }
     const double4_32a q = fac[n];
-    const double2 x0 = make_double2((q.x * r[0].x - hphibar * r[2].x) * q.z, (q.x * r[0].y - hphibar * r[2].y) * q.z);
-    const double2 x1 = make_double2(r[1].x * q.y, r[1].y * q.y);
-    const double2 x2 = make_double2((q.x * r[2].x + q.w * r[0].x) * q.z, (q.x * r[2].y + q.w * r[0].y) * q.z);
+    double2 x0, x1, x2;
+    if (split) {
+      double2 old[3];
+      for (int f = 0; f < 3; ++f) {
+        old[f] = out[(size_t)f * nc + idx];
+        r[f].x = fma(-q.z, old[f].x, r[f].x);
+        r[f].y = fma(-q.z, old[f].y, r[f].y);
+      }
+      const double2 y0 = make_double2((r[0].x - hphibar * r[2].x) * q.x, (r[0].y - hphibar * r[2].y) * q.x);
+      const double2 y2 = make_double2((r[2].x + q.y * r[0].x) * q.x, (r[2].y + q.y * r[0].y) * q.x);
+      x0 = make_double2(fma(q.z, old[0].x, y0.x) * q.w, fma(q.z, old[0].y, y0.y) * q.w);
+      x1 = make_double2(fma(q.z, old[1].x, r[1].x) * q.w, fma(q.z, old[1].y, r[1].y) * q.w);
+      x2 = make_double2(fma(q.z, old[2].x, y2.x) * q.w, fma(q.z, old[2].y, y2.y) * q.w);
+    } else {
+      x0 = make_double2((q.x * r[0].x - hphibar * r[2].x) * q.z, (q.x * r[0].y - hphibar * r[2].y) * q.z);
+      x1 = make_double2(r[1].x * q.y, r[1].y * q.y);
+      x2 = make_double2((q.x * r[2].x + q.w * r[0].x) * q.z, (q.x * r[2].y + q.w * r[0].y) * q.z);
+    }
     out[idx] = x0;
     out[nc + idx] = x1;
     out[2 * nc + idx] = x2;
@@ -377,14 +394,17 @@ __device__ __forceinline__ void order_node_update(int m, int T, int i, size_t ns
 
 // The same node update with the Coriolis term implicit: the right-hand sides
 // of order m are gathered in sm_th [3][T+1-m] and solved there by the banded
-// solve of banded.cuh (scratch: band_scratch_bytes(T) of shared memory).
+// solve of banded.cuh (scratch: band_scratch_bytes(T) of shared memory; the
+// factor table `band` is built with nu = 0 when `split`, and the diffusion
+// substep follows as in order_node_update).
 __device__ __forceinline__ void order_node_update_band(int m, int T, int i, size_t ns, const SdcCoef &c, double h,
-                                                       double inva2, double nu, double phibar, CorArgs cor,
-                                                       const double4_32a *__restrict__ band,
+                                                       double inva2, double nu, double phibar, bool split,
+                                                       CorArgs cor, const double4_32a *__restrict__ band,
                                                        const double2 *__restrict__ O, const double2 *__restrict__ fe,
                                                        const double2 *__restrict__ fi, double2 *__restrict__ th,
                                                        double2 *sm_th, void *scratch) {
   const int nc = ncoef_of(T), p0 = poff(T, m), len = T + 1 - m;
+  double2 *out = th + (size_t)i * ns;
   for (int t = threadIdx.x; t < 3 * len; t += blockDim.x) {
     const int f = t / len;
     const size_t e = (size_t)f * nc + p0 + (t - f * len);
@@ -394,14 +414,29 @@ __device__ __forceinline__ void order_node_update_band(int m, int T, int i, size
       v.x = fma(c.nI[i][j], g.x, fma(c.nE[i][j], a.x, v.x));
       v.y = fma(c.nI[i][j], g.y, fma(c.nE[i][j], a.y, v.y));
     }
+    if (split) {   // r - h nu k old
+      const int n = m + (t - f * len);
+      const double hnk = h * nu * ((double)n * (n + 1) * inva2);
+      const double2 o = out[e];
+      v.x = fma(-hnk, o.x, v.x);
+      v.y = fma(-hnk, o.y, v.y);
+    }
     sm_th[t] = v;
   }
   __syncthreads();
-  band_order_solve(m, T, h, inva2, nu, phibar, cor, band, sm_th, scratch);
-  double2 *out = th + (size_t)i * ns;
+  band_order_solve(m, T, h, inva2, split ? 0.0 : nu, phibar, cor, band, sm_th, scratch);
   for (int t = threadIdx.x; t < 3 * len; t += blockDim.x) {
     const int f = t / len;
-    out[(size_t)f * nc + p0 + (t - f * len)] = sm_th[t];
+    const size_t e = (size_t)f * nc + p0 + (t - f * len);
+    double2 x = sm_th[t];
+    if (split) {   // (x* + h nu k old) / s
+      const int n = m + (t - f * len);
+      const double hnk = h * nu * ((double)n * (n + 1) * inva2), is = 1.0 / (1.0 + hnk);
+      const double2 o = out[e];
+      x = make_double2(fma(hnk, o.x, x.x) * is, fma(hnk, o.y, x.y) * is);
+      sm_th[t] = x;
+    }
+    out[e] = x;
   }
 }
 

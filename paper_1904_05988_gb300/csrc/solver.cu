@@ -147,6 +147,8 @@ extern "C" int swe_ctx_create(swe_ctx **out, sht_plan *plan, const swe_params *p
   if (!(prm->a > 0) || !(prm->nu >= 0)) return fail(PFSH_EINVAL, "swe_ctx_create: need a > 0, nu >= 0");
   if (prm->coriolis != PFSH_CORIOLIS_EXPLICIT && prm->coriolis != PFSH_CORIOLIS_IMPLICIT)
     return fail(PFSH_EINVAL, "swe_ctx_create: coriolis must be PFSH_CORIOLIS_EXPLICIT or PFSH_CORIOLIS_IMPLICIT");
+  if (prm->implicit_split != 0 && prm->implicit_split != 1)
+    return fail(PFSH_EINVAL, "swe_ctx_create: implicit_split must be 0 or 1");
   if (plan->max_batch < 5) return fail(PFSH_EINVAL, "swe_ctx_create: plan max_batch must be >= 5");
   if (plan->prec == PFSH_FP16)
     return fail(PFSH_EUNSUPPORTED, "swe_ctx_create: the FP16 form serves transforms only (the flux products "
@@ -205,7 +207,9 @@ extern "C" int sdc_level_create(sdc_level **out, swe_ctx *ctx, int nodes, double
   }
   {
     // implicit solve of node i (h = dt QI[i][i]) per degree n, k = n(n+1)/a^2:
-    // s = 1 + h nu k, 1/s, 1/(s^2 + h^2 Phibar k), h k
+    // one solve:  s = 1 + h nu k, 1/s, 1/(s^2 + h^2 Phibar k), h k
+    // two substeps (swe_params.implicit_split): 1/(1 + h^2 Phibar k), h k,
+    //             h nu k, 1/s
     std::vector<double> fac((size_t)nodes * (T + 1) * 4, 0.0);
     const swe_params &pr = ctx->prm;
     for (int i = 0; i < nodes; ++i) {
@@ -214,10 +218,17 @@ extern "C" int sdc_level_create(sdc_level **out, swe_ctx *ctx, int nodes, double
         const double k = (double)n * (n + 1) / (pr.a * pr.a);
         const double sv = 1.0 + h * pr.nu * k;
         double *f = &fac[((size_t)i * (T + 1) + n) * 4];
-        f[0] = sv;
-        f[1] = 1.0 / sv;
-        f[2] = 1.0 / (sv * sv + h * h * pr.phibar * k);
-        f[3] = h * k;
+        if (pr.implicit_split) {
+          f[0] = 1.0 / (1.0 + h * h * pr.phibar * k);
+          f[1] = h * k;
+          f[2] = h * pr.nu * k;
+          f[3] = 1.0 / sv;
+        } else {
+          f[0] = sv;
+          f[1] = 1.0 / sv;
+          f[2] = 1.0 / (sv * sv + h * h * pr.phibar * k);
+          f[3] = h * k;
+        }
       }
     }
     if (cudaMemcpy(l->d_fac, fac.data(), fac.size() * sizeof(double), cudaMemcpyHostToDevice) != cudaSuccess) {
@@ -237,7 +248,8 @@ extern "C" int sdc_level_create(sdc_level **out, swe_ctx *ctx, int nodes, double
       rc2 = fail(PFSH_ENOMEM, "sdc_level_create: banded factors");
     }
     for (int i = 1; i < nodes && rc2 == PFSH_OK; ++i)
-      rc2 = band_factor_launch(ctx, dt * l->QI[i][i], l->d_band + (size_t)i * per, 0);
+      rc2 = band_factor_launch(ctx, dt * l->QI[i][i], ctx->prm.implicit_split ? 0.0 : ctx->prm.nu,
+                               l->d_band + (size_t)i * per, 0);
     if (rc2 == PFSH_OK && cudaDeviceSynchronize() != cudaSuccess) rc2 = fail(PFSH_ECUDA, "sdc_level_create: factors");
     if (rc2) {
       cudaFree(l->d_old);

@@ -270,7 +270,12 @@ static void sdc_old_launch(int nc3, int B, size_t ns, const SdcCoef &c, const do
 
 // theta_i = solve(O_i + sum_{1<=j<i} nE[i][j] FE_j^new + nI[i][j] FI_j^new, h_i)
 // with the per-degree solve factors of node i precomputed in FP64:
-// fac[n] = {s = 1 + h nu k, 1/s, 1/(s^2 + h^2 Phibar k), h k}
+// fac[n] = {s = 1 + h nu k, 1/s, 1/(s^2 + h^2 Phibar k), h k} for one solve;
+// SPLIT (two substeps, swe_params.implicit_split): fac[n] = {1/(1 + h^2
+// Phibar k), h k, h nu k, 1/s}, and with r' = r - h nu k old (old = theta_i
+// of the previous iterate): x* = the nu = 0 solve of r', x = (x* + h nu k
+// old) / s
+template <bool SPLIT>
 __global__ void __launch_bounds__(128) k_sdc_node(int T, int B, int i, size_t nstride, SdcCoef c, double hphibar,
                                                   const double4_32a *__restrict__ fac, const double2 *__restrict__ O,
                                                   const double2 *__restrict__ fe, const double2 *__restrict__ fi,
@@ -292,8 +297,22 @@ __global__ void __launch_bounds__(128) k_sdc_node(int T, int B, int i, size_t ns
     }
     r[f] = v;
   }
-  const double4_32a q = fac[n];   // s, 1/s, 1/det, h k
+  const double4_32a q = fac[n];
   double2 *out = th + (size_t)i * nstride + (size_t)b * 3 * nc;
+  if (SPLIT) {
+    double2 old[3];
+    for (int f = 0; f < 3; ++f) {
+      old[f] = out[f * nc + idx];
+      r[f].x = fma(-q.z, old[f].x, r[f].x);
+      r[f].y = fma(-q.z, old[f].y, r[f].y);
+    }
+    const double2 x0 = make_double2((r[0].x - hphibar * r[2].x) * q.x, (r[0].y - hphibar * r[2].y) * q.x);
+    const double2 x2 = make_double2((r[2].x + q.y * r[0].x) * q.x, (r[2].y + q.y * r[0].y) * q.x);
+    out[idx] = make_double2(fma(q.z, old[0].x, x0.x) * q.w, fma(q.z, old[0].y, x0.y) * q.w);
+    out[nc + idx] = make_double2(fma(q.z, old[1].x, r[1].x) * q.w, fma(q.z, old[1].y, r[1].y) * q.w);
+    out[2 * nc + idx] = make_double2(fma(q.z, old[2].x, x2.x) * q.w, fma(q.z, old[2].y, x2.y) * q.w);
+    return;
+  }
   out[idx] = make_double2((q.x * r[0].x - hphibar * r[2].x) * q.z, (q.x * r[0].y - hphibar * r[2].y) * q.z);
   out[nc + idx] = make_double2(r[1].x * q.y, r[1].y * q.y);
   out[2 * nc + idx] = make_double2((q.x * r[2].x + q.w * r[0].x) * q.z, (q.x * r[2].y + q.w * r[0].y) * q.z);
@@ -357,10 +376,11 @@ int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const
       if (rc) return rc;
     } else {
       PFSH_LAUNCH("k_sdc_node", s);
-      k_sdc_node<<<g, 128, 0, s>>>(T, B, i, ns, c, c.h[i] * ctx->prm.phibar,
-                                   (const double4_32a *)l->d_fac + (size_t)i * (T + 1),
-                                   (const double2 *)l->d_old + (size_t)(i - 1) * nc3 * B, (const double2 *)fE,
-                                   (const double2 *)fI, (double2 *)theta);
+      auto kern = ctx->prm.implicit_split ? k_sdc_node<true> : k_sdc_node<false>;
+      kern<<<g, 128, 0, s>>>(T, B, i, ns, c, c.h[i] * ctx->prm.phibar,
+                             (const double4_32a *)l->d_fac + (size_t)i * (T + 1),
+                             (const double2 *)l->d_old + (size_t)(i - 1) * nc3 * B, (const double2 *)fE,
+                             (const double2 *)fI, (double2 *)theta);
       PFSH_CHECK_LAUNCH("k_sdc_node");
     }
     int rc = rhs_eval(l->ctx, theta + (size_t)i * node_stride, fE + (size_t)i * node_stride,

@@ -87,3 +87,67 @@ def test_accuracy_order_on_dt_refinement(nodes, sweeps, order):
         errs.append(np.max(np.abs(out - ref)[1]))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert all(abs(r - order) < 0.25 for r in rates), rates
+
+
+# ---------------------------------------------------------------------------
+# Node solve in two substeps (physical linear terms, then diffusion), each
+# with its own correction term
+# ---------------------------------------------------------------------------
+def _split(nu=syn.NU, coriolis=False):
+    p = _params()
+    return SWEParams(a=p.a, omega=p.omega, g=p.g, nu=nu, phibar=p.phibar, coriolis_implicit=coriolis,
+                     implicit_split=True)
+
+
+@pytest.mark.parametrize("coriolis", [False, True])
+def test_split_sweeps_converge_to_the_collocation_solution(coriolis):
+    """The substeps change every sweep but not its fixed point: iterated,
+    the split sweep solves the same collocation problem as the one-solve
+    sweep (and leaves a zero collocation residual)."""
+    T = 15
+    nlat, nlon = syn.gaussian_grid_size(T)
+    nu = 5e5     # strong diffusion: the splitting error of one sweep is large
+    comb = SDCLevel(T, nlat, nlon, 5, 600.0, SWEParams(a=syn.EARTH_RADIUS, omega=syn.OMEGA, g=syn.GRAVITY, nu=nu,
+                                                        phibar=syn.GRAVITY * syn.MEAN_DEPTH,
+                                                        coriolis_implicit=coriolis))
+    split = SDCLevel(T, nlat, nlon, 5, 600.0, _split(nu, coriolis))
+    x0 = _state(T)
+    a = comb.spread(x0)
+    b = split.spread(x0)
+    a1 = comb.sweep(*a)
+    b1 = split.sweep(*b)
+    assert np.max(np.abs(a1[0] - b1[0])) > 1e-9 * np.max(np.abs(a1[0] - x0))    # one sweep differs
+    for _ in range(40):
+        a = comb.sweep(*a)
+        b = split.sweep(*b)
+    change = np.max(np.abs(a[0][-1] - x0))
+    assert np.max(np.abs(a[0] - b[0])) < 1e-12 * change
+    res = split.collocation_residual(*b)
+    assert np.max(np.abs(res)) < 1e-14 * np.max(np.abs(b[0]))
+
+
+def test_split_sweep_without_diffusion_is_the_one_solve_sweep():
+    T = 12
+    nlat, nlon = syn.gaussian_grid_size(T)
+    p0 = _params()
+    comb = SDCLevel(T, nlat, nlon, 3, 600.0, SWEParams(a=p0.a, omega=p0.omega, g=p0.g, nu=0.0, phibar=p0.phibar))
+    split = SDCLevel(T, nlat, nlon, 3, 600.0, _split(nu=0.0))
+    x0 = _state(T, 4)
+    a = comb.sweep(*comb.spread(x0))
+    b = split.sweep(*split.spread(x0))
+    assert np.max(np.abs(a[0] - b[0])) <= 1e-15 * np.max(np.abs(a[0]))
+
+
+def test_split_sweeps_keep_the_accuracy_order():
+    """Two sweeps on 3 nodes stay second order in dt with the split solve."""
+    T = 15
+    nlat, nlon = syn.gaussian_grid_size(T)
+    th0 = _state(T)
+    t_end = 3600.0
+    ref = sdc_run(SDCLevel(T, nlat, nlon, 5, t_end / 32, _params()), th0, 32, 8)
+    errs = []
+    for n in (4, 8, 16):
+        out = sdc_run(SDCLevel(T, nlat, nlon, 3, t_end / n, _split()), th0, n, 2)
+        errs.append(np.max(np.abs(out - ref)[1]))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert all(abs(r - 2) < 0.25 for r in rates), rates
