@@ -51,7 +51,7 @@ def env_int(name, default):
 
 
 # ---------------------------------------------------------------------------
-# algorithmic work per unit
+# algorithmic work per unit (flops or bytes one launch must move)
 # ---------------------------------------------------------------------------
 def legendre_flops(T: int, nlat: int, cols_complex: int) -> float:
     """Real flops of one synthesis or analysis pass over `cols_complex` complex
