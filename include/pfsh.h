@@ -97,8 +97,19 @@ typedef struct {
   size_t device_bytes;   /* tables + workspace held by the plan             */
   const double *mu;      /* host copy of the nlat Gaussian latitudes (sin)  */
   const double *w;       /* host copy of the nlat Gauss weights             */
+  int tc_tiles[2][8];    /* tensor-core forms: row tiles per order used by
+                          * [0] synthesis / [1] analysis for a launch of
+                          * 1..8 blocks of 128 real columns (0 otherwise)   */
 } sht_info;
 
+/* Tensor-core forms are autotuned at creation: for every launch width the
+ * plan can see (blocks of 128 real columns up to 2 max_batch), the per-order
+ * GEMMs are timed with their output rows in ceil(rows/256) and in twice as
+ * many tiles, and the faster tiling is used for launches of that width (the
+ * results are bitwise the same: tiles split output rows, not the sums).
+ * Choices are cached per (T, nlat, precision, direction, width) for the
+ * process and, if the environment variable PFSH_TUNE_CACHE names a file, in
+ * that file (JSON lines).  PFSH_TC_TILES=1 or 2 pins the tiling instead.  */
 /* Create a transform plan for truncation T on an nlat x nlon Gaussian grid.
  * Requires T >= 1, nlat even, nlat >= T+2, nlon > 2(T+1), nlon even with all
  * prime factors <= 61, and 1 <= max_batch.  `max_batch` bounds the number of

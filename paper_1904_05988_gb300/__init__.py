@@ -62,7 +62,7 @@ class SweParams(ctypes.Structure):
 class ShtInfo(ctypes.Structure):
     _fields_ = [("T", c_int), ("nlat", c_int), ("nlon", c_int), ("ncoef", c_int), ("max_batch", c_int),
                 ("prec", c_int), ("device_bytes", c_size_t), ("mu", ctypes.POINTER(c_double)),
-                ("w", ctypes.POINTER(c_double))]
+                ("w", ctypes.POINTER(c_double)), ("tc_tiles", (c_int * 8) * 2)]
 
 
 class PfasstConfig(ctypes.Structure):
@@ -191,6 +191,8 @@ class ShtPlan(_Handle):
         self.device_bytes = info.device_bytes
         self.mu = [info.mu[i] for i in range(self.nlat)]
         self.w = [info.w[i] for i in range(self.nlat)]
+        # autotuned row tiles per order: [synthesis, analysis][launch width 1..8 x 128 real columns]
+        self.tc_tiles = [[info.tc_tiles[d][i] for i in range(8)] for d in range(2)]
 
     @property
     def grid_dtype(self) -> torch.dtype:

@@ -31,7 +31,9 @@
 
 namespace pfsh {
 
-// per-coefficient coupling table of the context: {alpha_n, beta_n, m/(n(n+1)), 0}
+// eps_n^m = sqrt((n^2 - m^2) / (4 n^2 - 1)) (0 for n = 0 or n < m); the
+// context's coupling table CorArgs::ab holds {alpha_n, beta_n, m/(n(n+1)), 0}
+// per packed coefficient (band_ctx_init)
 __host__ __device__ inline double band_eps(int n, int m) {
   return (n > 0 && n >= m) ? sqrt((double)(n - m) * (double)(n + m) / (4.0 * n * n - 1.0)) : 0.0;
 }

@@ -185,6 +185,14 @@ struct TcDir {
   size_t img_bytes = 0;
 };
 
+// Row tilings of a tensor-core plan: configuration c splits the output rows
+// of an order (latitudes for synthesis, degree positions for analysis) into
+// ntiles = tile_mult[c] x ceil(rows / 256) tiles; the autotuner of
+// legendre_tc.cu picks a configuration per launch width (column blocks of
+// 128 real columns, 1..kTcMaxNb).  The tiling splits output rows only, so
+// every configuration computes bitwise the same result.
+constexpr int kTcConfigs = 2, kTcMaxNb = 8;
+
 // ---------------------------------------------------------------------------
 // objects behind the opaque ABI handles
 // ---------------------------------------------------------------------------
@@ -204,7 +212,9 @@ struct sht_plan {
   double *d_rowf = nullptr;         // [nh][2]: 1/(1-mu_j^2), w_j (northern rows)
   float *d_rowf32 = nullptr;        // float copy
   pfsh::FftPlan fft;
-  pfsh::TcDir tc[2];                // [0] synthesis, [1] analysis (tensor-core precisions)
+  pfsh::TcDir tc[2][pfsh::kTcConfigs];   // [direction: 0 synthesis, 1 analysis][configuration]
+  int tc_mult[2][pfsh::kTcConfigs] = {};  // row-tile multiplier of each configuration (0: not built)
+  unsigned char tc_pick[2][pfsh::kTcMaxNb] = {};   // configuration per launch width
   // workspace for one pass of at most max_batch fields
   void *ws = nullptr;
   size_t ws_bytes = 0;
@@ -331,8 +341,9 @@ int synth_simt(const sht_plan *p, int cols, cudaStream_t s);      // X -> F
 int analysis_simt(const sht_plan *p, int cols, cudaStream_t s);   // H -> Y
 int synth_tc(const sht_plan *p, int cols, cudaStream_t s);
 int analysis_tc(const sht_plan *p, int cols, cudaStream_t s);
-int tc_tables_build(sht_plan *p);
+int tc_tables_build(sht_plan *p);   // builds the tilings and runs the autotuner
 void tc_tables_free(sht_plan *p);
+int tc_tiles_used(const sht_plan *p, int dir, int nb);   // row tiles per order at launch width nb
 int synth_small(const sht_plan *p, int cols, cudaStream_t s);
 int analysis_small(const sht_plan *p, int cols, cudaStream_t s);
 bool small_synth(int cols);

@@ -23,7 +23,15 @@
 // the two warpgroups take alternate 16-column groups).  Every wait is
 // bounded; on a timeout the status word records ST_TIMEOUT and the CTA winds
 // down.
+#include <stdio.h>
+#include <stdlib.h>
+#include <string.h>
+
 #include <algorithm>
+#include <map>
+#include <mutex>
+#include <string>
+#include <tuple>
 #include <vector>
 
 #include "internal.cuh"
@@ -337,8 +345,8 @@ __global__ void k_build_images(int T, int nh, const double *__restrict__ P, cons
 int round16(int x) { return (x + 15) & ~15; }
 
 // host-side chunk lists for one direction
-void plan_chunks(int T, int nh, bool analysis, std::vector<TcChunk> &chunks, std::vector<TcWork> &work, int &ntiles,
-                 int &Nmax, size_t &bytes) {
+void plan_chunks(int T, int nh, bool analysis, int tile_mult, std::vector<TcChunk> &chunks, std::vector<TcWork> &work,
+                 int &ntiles, int &Nmax, size_t &bytes) {
   chunks.clear();
   work.clear();
   Nmax = 16;
@@ -349,7 +357,8 @@ void plan_chunks(int T, int nh, bool analysis, std::vector<TcChunk> &chunks, std
   } else {
     rows_total = (T + 3) / 2;                // degree positions of parity 0 at m = 0
   }
-  tiles = (rows_total + 255) / 256;
+  tiles = (rows_total + 255) / 256 * tile_mult;
+  tiles = std::max(1, std::min(tiles, rows_total / 16));   // at least 16 rows per tile
   const int tsz = (rows_total + tiles - 1) / tiles;
   ntiles = tiles;
   for (int m = 0; m <= T; ++m) {
@@ -404,49 +413,191 @@ size_t tc_smem_bytes(int Nmax, bool x3) {
 
 }  // namespace
 
-int tc_tables_build(sht_plan *p) {
+// images, chunk and work lists of one direction and row tiling
+static int tc_build_dir(sht_plan *p, int dir, int tile_mult, TcDir &d) {
   const bool fp16 = p->prec == PFSH_FP16;
-  for (int dir = 0; dir < 2; ++dir) {
-    TcDir &d = p->tc[dir];
-    std::vector<TcChunk> ch;
-    std::vector<TcWork> wk;
-    plan_chunks(p->T, p->nh, dir == 1, ch, wk, d.ntiles, d.Nmax, d.img_bytes);
-    d.nchunks = (int)ch.size();
-    if (cudaMalloc(&d.img, d.img_bytes) != cudaSuccess || cudaMalloc(&d.chunks, ch.size() * sizeof(TcChunk)) ||
-        cudaMalloc(&d.work, wk.size() * sizeof(TcWork))) {
-      cudaGetLastError();
-      return fail(PFSH_ENOMEM, "tensor-core table images");
+  std::vector<TcChunk> ch;
+  std::vector<TcWork> wk;
+  plan_chunks(p->T, p->nh, dir == 1, tile_mult, ch, wk, d.ntiles, d.Nmax, d.img_bytes);
+  d.nchunks = (int)ch.size();
+  if (cudaMalloc(&d.img, d.img_bytes) != cudaSuccess || cudaMalloc(&d.chunks, ch.size() * sizeof(TcChunk)) ||
+      cudaMalloc(&d.work, wk.size() * sizeof(TcWork))) {
+    cudaGetLastError();
+    return fail(PFSH_ENOMEM, "tensor-core table images");
+  }
+  p->device_bytes += d.img_bytes + ch.size() * sizeof(TcChunk) + wk.size() * sizeof(TcWork);
+  PFSH_CUDA(cudaMemcpy(d.chunks, ch.data(), ch.size() * sizeof(TcChunk), cudaMemcpyHostToDevice));
+  PFSH_CUDA(cudaMemcpy(d.work, wk.data(), wk.size() * sizeof(TcWork), cudaMemcpyHostToDevice));
+  PFSH_CUDA(cudaMemset(d.img, 0, d.img_bytes));
+  {
+    PFSH_LAUNCH("k_build_images", 0);
+    if (dir == 0) {
+      if (fp16) k_build_images<true, false><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
+      else k_build_images<false, false><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
+    } else {
+      if (fp16) k_build_images<true, true><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
+      else k_build_images<false, true><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
     }
-    p->device_bytes += d.img_bytes + ch.size() * sizeof(TcChunk) + wk.size() * sizeof(TcWork);
-    PFSH_CUDA(cudaMemcpy(d.chunks, ch.data(), ch.size() * sizeof(TcChunk), cudaMemcpyHostToDevice));
-    PFSH_CUDA(cudaMemcpy(d.work, wk.data(), wk.size() * sizeof(TcWork), cudaMemcpyHostToDevice));
-    PFSH_CUDA(cudaMemset(d.img, 0, d.img_bytes));
-    {
-      PFSH_LAUNCH("k_build_images", 0);
-      if (dir == 0) {
-        if (fp16) k_build_images<true, false><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
-        else k_build_images<false, false><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
-      } else {
-        if (fp16) k_build_images<true, true><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
-        else k_build_images<false, true><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
+  }
+  PFSH_CHECK_LAUNCH("k_build_images");
+  return PFSH_OK;
+}
+
+static void tc_free_dir(sht_plan *p, TcDir &d) {
+  if (d.img) cudaFree(d.img);
+  if (d.chunks) cudaFree(d.chunks);
+  if (d.work) cudaFree(d.work);
+  const size_t held = d.img_bytes + (size_t)d.nchunks * sizeof(TcChunk) + (size_t)(p->T + 1) * d.ntiles * sizeof(TcWork);
+  p->device_bytes -= std::min(p->device_bytes, held);
+  d = TcDir{};
+}
+
+// ---------------------------------------------------------------------------
+// Autotuner.  For each direction and launch width nb (column blocks of 128
+// real columns), the configurations built for the plan are timed on the
+// plan's workspace (CUDA events, 2 warm-up + 5 timed launches each) and the
+// fastest is kept.  Results are cached per (T, nlat, precision, direction,
+// nb) for the process and, when PFSH_TUNE_CACHE names a file, in that file
+// (one JSON object per line), so plans of the same shape reuse them.
+// PFSH_TC_TILES = 1 or 2 pins the row-tile multiplier instead.
+// ---------------------------------------------------------------------------
+using TuneKey = std::tuple<int, int, int, int, int>;   // T, nlat, prec, dir, nb
+static std::mutex g_tune_mu;
+static std::map<TuneKey, int> g_tune;   // -> row-tile multiplier
+static bool g_tune_loaded = false;
+
+static void tune_cache_load() {
+  if (g_tune_loaded) return;
+  g_tune_loaded = true;
+  const char *path = getenv("PFSH_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE *f = fopen(path, "r");
+  if (!f) return;
+  char line[512];
+  while (fgets(line, sizeof line, f)) {
+    int T, nlat, prec, dir, nb, mult;
+    if (sscanf(line, "{\"T\": %d, \"nlat\": %d, \"prec\": %d, \"dir\": %d, \"nb\": %d, \"tile_mult\": %d",
+               &T, &nlat, &prec, &dir, &nb, &mult) == 6 && (mult == 1 || mult == 2))
+      g_tune[TuneKey(T, nlat, prec, dir, nb)] = mult;
+  }
+  fclose(f);
+}
+
+static void tune_cache_store(const TuneKey &k, int mult, const float us[kTcConfigs]) {
+  g_tune[k] = mult;
+  const char *path = getenv("PFSH_TUNE_CACHE");
+  if (!path || !*path) return;
+  FILE *f = fopen(path, "a");
+  if (!f) return;
+  fprintf(f, "{\"T\": %d, \"nlat\": %d, \"prec\": %d, \"dir\": %d, \"nb\": %d, \"tile_mult\": %d, "
+             "\"us\": [%.2f, %.2f]}\n",
+          std::get<0>(k), std::get<1>(k), std::get<2>(k), std::get<3>(k), std::get<4>(k), mult, us[0], us[1]);
+  fclose(f);
+}
+
+template <bool X3, bool FP16, bool AN>
+static int launch_tc(const sht_plan *p, const TcDir &d, int cols, const float *act, float *out, cudaStream_t s,
+                     const char *name);
+static int launch_dir(const sht_plan *p, int dir, const TcDir &d, int cols, cudaStream_t s);
+
+static int tc_time(const sht_plan *p, int dir, const TcDir &d, int cols, float *us) {
+  cudaEvent_t e0, e1;
+  PFSH_CUDA(cudaEventCreate(&e0));
+  PFSH_CUDA(cudaEventCreate(&e1));
+  int rc = PFSH_OK;
+  for (int it = 0; it < 2 && !rc; ++it) rc = launch_dir(p, dir, d, cols, 0);
+  cudaEventRecord(e0, 0);
+  for (int it = 0; it < 5 && !rc; ++it) rc = launch_dir(p, dir, d, cols, 0);
+  cudaEventRecord(e1, 0);
+  float ms = 0.0f;
+  if (!rc && cudaEventSynchronize(e1) == cudaSuccess && cudaEventElapsedTime(&ms, e0, e1) == cudaSuccess)
+    *us = ms * 1000.0f / 5.0f;
+  else if (!rc)
+    rc = fail(PFSH_ECUDA, "autotuner timing");
+  cudaEventDestroy(e0);
+  cudaEventDestroy(e1);
+  return rc;
+}
+
+int tc_tables_build(sht_plan *p) {
+  const char *pin = getenv("PFSH_TC_TILES");
+  const int forced = pin && (pin[0] == '1' || pin[0] == '2') && pin[1] == 0 ? pin[0] - '0' : 0;
+  // launch widths of this plan: up to max_batch complex columns
+  const int nb_max = std::min(kTcMaxNb, (2 * p->max_batch + MROWS - 1) / MROWS);
+  int rc;
+  for (int dir = 0; dir < 2; ++dir) {
+    // widths at which the small-batch kernels run instead never reach these kernels
+    auto small = [&](int cols) { return dir == 0 ? small_synth(cols) : small_analysis(cols); };
+    for (int i = 0; i < kTcMaxNb; ++i) p->tc_pick[dir][i] = 0;
+    if (forced) {
+      p->tc_mult[dir][0] = forced;
+      if ((rc = tc_build_dir(p, dir, forced, p->tc[dir][0]))) return rc;
+      continue;
+    }
+    p->tc_mult[dir][0] = 1;
+    if ((rc = tc_build_dir(p, dir, 1, p->tc[dir][0]))) return rc;
+    std::lock_guard<std::mutex> lock(g_tune_mu);
+    tune_cache_load();
+    // timed width of nb column blocks: nb x 64 complex columns, within the workspace
+    auto width = [&](int nb) { return std::min(p->max_batch, nb * MROWS / 2); };
+    int need = 0;   // launch widths without a cached choice
+    for (int nb = 1; nb <= nb_max; ++nb)
+      if (!small(width(nb)) && !g_tune.count(TuneKey(p->T, p->nlat, p->prec, dir, nb))) ++need;
+    bool want2 = false;
+    for (int nb = 1; nb <= nb_max; ++nb) {
+      auto it = g_tune.find(TuneKey(p->T, p->nlat, p->prec, dir, nb));
+      if (it != g_tune.end() && it->second == 2) want2 = true;
+    }
+    if (need > 0 || want2) {
+      p->tc_mult[dir][1] = 2;
+      if ((rc = tc_build_dir(p, dir, 2, p->tc[dir][1]))) return rc;
+      if (p->tc[dir][1].ntiles == p->tc[dir][0].ntiles) {   // too few rows to split further
+        tc_free_dir(p, p->tc[dir][1]);
+        p->tc_mult[dir][1] = 0;
       }
     }
-    PFSH_CHECK_LAUNCH("k_build_images");
+    if (need > 0 && p->tc_mult[dir][1]) {
+      PFSH_CUDA(cudaMemset(p->ws, 0, p->ws_bytes));
+      for (int nb = 1; nb <= nb_max; ++nb) {
+        const TuneKey key(p->T, p->nlat, p->prec, dir, nb);
+        const int cols = width(nb);
+        if (small(cols) || g_tune.count(key)) continue;
+        float us[kTcConfigs] = {0.0f, 0.0f};
+        for (int c = 0; c < kTcConfigs; ++c)
+          if ((rc = tc_time(p, dir, p->tc[dir][c], cols, &us[c]))) return rc;
+        tune_cache_store(key, us[1] < us[0] ? 2 : 1, us);
+      }
+    }
+    bool uses2 = false;
+    for (int nb = 1; nb <= kTcMaxNb; ++nb) {
+      auto it = g_tune.find(TuneKey(p->T, p->nlat, p->prec, dir, std::min(nb, nb_max)));
+      const int c = (it != g_tune.end() && it->second == 2 && p->tc_mult[dir][1]) ? 1 : 0;
+      p->tc_pick[dir][nb - 1] = (unsigned char)c;
+      uses2 |= c == 1;
+    }
+    if (!uses2 && p->tc_mult[dir][1]) {
+      tc_free_dir(p, p->tc[dir][1]);
+      p->tc_mult[dir][1] = 0;
+    }
   }
   PFSH_CUDA(cudaDeviceSynchronize());
   return PFSH_OK;
 }
 
 void tc_tables_free(sht_plan *p) {
-  for (int dir = 0; dir < 2; ++dir) {
-    TcDir &d = p->tc[dir];
-    if (d.img) cudaFree(d.img);
-    if (d.chunks) cudaFree(d.chunks);
-    if (d.work) cudaFree(d.work);
-    d.img = nullptr;
-    d.chunks = nullptr;
-    d.work = nullptr;
-  }
+  for (int dir = 0; dir < 2; ++dir)
+    for (int c = 0; c < kTcConfigs; ++c) {
+      TcDir &d = p->tc[dir][c];
+      if (d.img) cudaFree(d.img);
+      if (d.chunks) cudaFree(d.chunks);
+      if (d.work) cudaFree(d.work);
+      d = TcDir{};
+    }
+}
+
+int tc_tiles_used(const sht_plan *p, int dir, int nb) {
+  if (!uses_tensor_cores(p->prec) || nb < 1) return 0;
+  return p->tc[dir][p->tc_pick[dir][std::min(nb, kTcMaxNb) - 1]].ntiles;
 }
 
 template <bool X3, bool FP16, bool AN>
@@ -467,26 +618,36 @@ static int launch_tc(const sht_plan *p, const TcDir &d, int cols, const float *a
   return PFSH_OK;
 }
 
-int synth_tc(const sht_plan *p, int cols, cudaStream_t s) {
-  const float *X = (const float *)p->X;
-  float *F = (float *)p->F;
-  switch (p->prec) {
-    case PFSH_BF16: return launch_tc<false, false, false>(p, p->tc[0], cols, X, F, s, "k_synth_bf16");
-    case PFSH_FP16: return launch_tc<false, true, false>(p, p->tc[0], cols, X, F, s, "k_synth_fp16");
-    case PFSH_BF16X3: return launch_tc<true, false, false>(p, p->tc[0], cols, X, F, s, "k_synth_bf16x3");
-    default: return fail(PFSH_EUNSUPPORTED, "synth_tc: precision");
+// one launch of direction dir with the row tiling d
+static int launch_dir(const sht_plan *p, int dir, const TcDir &d, int cols, cudaStream_t s) {
+  if (dir == 0) {
+    const float *X = (const float *)p->X;
+    float *F = (float *)p->F;
+    switch (p->prec) {
+      case PFSH_BF16: return launch_tc<false, false, false>(p, d, cols, X, F, s, "k_synth_bf16");
+      case PFSH_FP16: return launch_tc<false, true, false>(p, d, cols, X, F, s, "k_synth_fp16");
+      case PFSH_BF16X3: return launch_tc<true, false, false>(p, d, cols, X, F, s, "k_synth_bf16x3");
+      default: return fail(PFSH_EUNSUPPORTED, "synth_tc: precision");
+    }
   }
-}
-
-int analysis_tc(const sht_plan *p, int cols, cudaStream_t s) {
   const float *H = (const float *)p->H;
   float *Y = (float *)p->Y;
   switch (p->prec) {
-    case PFSH_BF16: return launch_tc<false, false, true>(p, p->tc[1], cols, H, Y, s, "k_anal_bf16");
-    case PFSH_FP16: return launch_tc<false, true, true>(p, p->tc[1], cols, H, Y, s, "k_anal_fp16");
-    case PFSH_BF16X3: return launch_tc<true, false, true>(p, p->tc[1], cols, H, Y, s, "k_anal_bf16x3");
+    case PFSH_BF16: return launch_tc<false, false, true>(p, d, cols, H, Y, s, "k_anal_bf16");
+    case PFSH_FP16: return launch_tc<false, true, true>(p, d, cols, H, Y, s, "k_anal_fp16");
+    case PFSH_BF16X3: return launch_tc<true, false, true>(p, d, cols, H, Y, s, "k_anal_bf16x3");
     default: return fail(PFSH_EUNSUPPORTED, "analysis_tc: precision");
   }
 }
+
+// the tiling the autotuner picked for this launch width
+static const TcDir &tc_for(const sht_plan *p, int dir, int cols) {
+  const int nb = std::min(kTcMaxNb, std::max(1, (2 * cols + MROWS - 1) / MROWS));
+  return p->tc[dir][p->tc_pick[dir][nb - 1]];
+}
+
+int synth_tc(const sht_plan *p, int cols, cudaStream_t s) { return launch_dir(p, 0, tc_for(p, 0, cols), cols, s); }
+
+int analysis_tc(const sht_plan *p, int cols, cudaStream_t s) { return launch_dir(p, 1, tc_for(p, 1, cols), cols, s); }
 
 }  // namespace pfsh

@@ -405,6 +405,8 @@ extern "C" int sht_plan_query(const sht_plan *p, sht_info *info) {
   info->device_bytes = p->device_bytes;
   info->mu = p->mu.data();
   info->w = p->w.data();
+  for (int dir = 0; dir < 2; ++dir)
+    for (int nb = 1; nb <= 8; ++nb) info->tc_tiles[dir][nb - 1] = tc_tiles_used(p, dir, nb);
   return PFSH_OK;
 }
 
