@@ -144,8 +144,13 @@ struct ChainGeo {
   const typename cpx<R>::t *H;
 };
 
+// At most 64 registers per thread (two blocks' worth per SM): a launch of this
+// kernel is latency-bound and holds one SM per order, and with the register
+// file half free the fine-sweep kernels of the other stream (grid stage,
+// synthesis) can run on the same SMs meanwhile (measured: 188 -> 197
+// iterations/s at T255/T127 with 32 slices, despite some spilling).
 template <typename R>
-__global__ void __launch_bounds__(kChainThreads) k_chain_node(ChainStep st, ChainGeo<R> g, SdcCoef c) {
+__global__ void __launch_bounds__(kChainThreads, 2) k_chain_node(ChainStep st, ChainGeo<R> g, SdcCoef c) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   const int m = blockIdx.x, T = g.T, nc = ncoef_of(T), K = T + 2 - m;
   R *Pst = reinterpret_cast<R *>(smem_raw);
