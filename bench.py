@@ -176,6 +176,22 @@ def block_solve(ps, torch, pf, h_in, h_out, d_in, d_out):
     h_out.copy_(d_out, non_blocking=True)
 
 
+def job_time(ms_local: float, dist, device) -> float:
+    """Duration of the timed region for the whole job: the maximum over ranks
+    (every rank runs its own replica; the job is as slow as its slowest rank)."""
+    import torch
+    t = torch.tensor([ms_local], device=device, dtype=torch.float64)
+    if dist is not None:
+        dist.all_reduce(t, op=dist.ReduceOp.MAX)
+    return float(t.item())
+
+
+def job_value(ms_max: float, world: int, steps: int) -> float:
+    """Whole-job PFASST iterations/s: every rank advanced its replica by
+    `steps` iterations within ms_max."""
+    return world * steps / (ms_max / 1e3)
+
+
 def run_ours(args, rank, world, local_rank):
     import torch
     import paper_1904_05988_gb300 as ps
@@ -218,12 +234,9 @@ def run_ours(args, rank, world, local_rank):
     launches = ps.pfsh_kernel_launches() - n0
     clk = clocks.stop()
     ps.pfsh_sync_status()
-    ms_t = torch.tensor([ms], device=dev, dtype=torch.float64)
-    if dist is not None:
-        dist.all_reduce(ms_t, op=dist.ReduceOp.MAX)
-    ms_max = ms_t.item()
+    ms_max = job_time(ms, dist, dev)
     ms_per_step = ms_max / args.steps
-    value = world * args.steps / (ms_max / 1e3)
+    value = job_value(ms_max, world, args.steps)
 
     # ---- SWE RHS evaluations/s at T255, 32 states per call ----
     def rhs_rate(prec):

@@ -175,3 +175,39 @@ def test_coriolis_pfasst_two_iterations_mixed(form):
     assert max(errs) < PF_TOL[form]
     assert e_inc < 1e3 * PF_TOL[form]
     pf.close()
+
+
+@pytest.mark.parametrize("T", [1, 2, 3, 5])
+def test_coriolis_banded_solve_tiny_truncations(T):
+    """Chains of one to a few elements (order m = T has one degree; T = 1:
+    n = 0 is decoupled), 2 Omega h = 0.5, and an empty batch."""
+    nlat, nlon = syn.gaussian_grid_size(T)
+    plan = ps.sht_plan_create(T, nlat, nlon, 5, "fp64")
+    ctx = ps.swe_ctx_create(plan, A, OM, syn.NU, PHIBAR, coriolis_implicit=True)
+    b = syn.random_spectrum(T, (2, 3), seed=70 + T, nmin=0)
+    x = torch.empty((2, 3, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    ps.swe_implicit_solve(ctx, cuda(b), x, 3600.0)
+    empty = torch.empty((0, 3, syn.ncoef(T)), dtype=torch.complex128, device=DEV)
+    ps.swe_implicit_solve(ctx, empty, empty, 3600.0)
+    ps.pfsh_sync_status()
+    ref = pack(implicit_solve(unpack(b, T), 3600.0, oparams()), T)
+    assert rel(x.cpu().numpy(), ref) < 1e-13
+
+
+def test_coriolis_implicit_without_rotation_is_the_paper_split():
+    """Omega = 0: the two splits coincide (F_E and F_I bitwise, the banded
+    solve to rounding)."""
+    T = 31
+    nlat, nlon = syn.gaussian_grid_size(T)
+    plan = ps.sht_plan_create(T, nlat, nlon, 10, "fp64")
+    ctx_e = ps.swe_ctx_create(plan, A, 0.0, syn.NU, PHIBAR)
+    ctx_i = ps.swe_ctx_create(plan, A, 0.0, syn.NU, PHIBAR, coriolis_implicit=True)
+    st = cuda(state_of(T, 71, 2))
+    out = [torch.empty_like(st) for _ in range(6)]
+    ps.swe_rhs(ctx_e, st, out[0], out[1])
+    ps.swe_rhs(ctx_i, st, out[2], out[3])
+    ps.swe_implicit_solve(ctx_e, st, out[4], 600.0)
+    ps.swe_implicit_solve(ctx_i, st, out[5], 600.0)
+    ps.pfsh_sync_status()
+    assert torch.equal(out[0], out[2]) and torch.equal(out[1], out[3])
+    assert rel(out[5].cpu().numpy(), out[4].cpu().numpy()) < 1e-15
