@@ -557,9 +557,17 @@ def cpu_baseline_sample(steps: int = 1):
     for _ in range(steps):
         pf.iteration(False)
     dt = (time.perf_counter() - t) / steps
+    # one T255 RHS evaluation (F_E and F_I of one state), best of 2
+    t_rhs = []
+    for _ in range(2):
+        t0 = time.perf_counter()
+        pf.f.eval_f(st)
+        t_rhs.append(time.perf_counter() - t0)
     return {"value": 1.0 / (dt * NTS / 2), "unit": "PFASST iterations/s", "cores": os.cpu_count(),
             "kind": "oracle", "sample": f"{steps} iteration(s) over 2 of 32 slices at T255/T127, scaled x16; "
-                                        f"{dt:.1f} s each; numpy {np.__version__}"}
+                                        f"{dt:.1f} s each; numpy {np.__version__}",
+            "swe_rhs_evals_per_s": 1.0 / min(t_rhs),
+            "swe_rhs_sample": f"one T255 state, best of 2 ({min(t_rhs):.2f} s)"}
 
 
 def run_reference(args, rank, world):

@@ -23,8 +23,9 @@
 // Chain c, position j: degree n = m + j, field (j + c) & 1 (0 zeta, 1 delta).
 // Forward elimination with w_j = D_j - a_j c'_{j-1}, c'_j = c_j / w_j,
 // y_j = (r_j - a_j y_{j-1}) / w_j, then x_j = y_j - c'_j x_{j+1}.
-// The factors {c'_j, 1/w_j} depend on h only: one table per SDC node; the
-// two substitution passes run as warp scans (band_chain_scan).
+// The factors {c'_j, 1/w_j} and the forward coefficients al_j = -a_j / w_j
+// depend on h only: one table per SDC node (band_table_entries); the two
+// substitution passes run as warp scans (band_chain_scan).
 #pragma once
 
 #include "internal.cuh"
@@ -55,10 +56,16 @@ __device__ __forceinline__ void coriolis_point(int m, int n, int T, const double
   *cd = make_double2(tw * (-q.z * d.y + q.x * zm.x + q.y * zp.x), tw * (q.z * d.x + q.x * zm.y + q.y * zp.y));
 }
 
+// factor table of one step size, in double4 units: [2][nc] {c', 1/w} (rows
+// of zeta, then of delta) followed by [2][nc] complex al = -a/w, packed two
+// per double4
+__host__ __device__ inline size_t band_table_entries(int nc) { return (size_t)3 * nc; }
+
 // shared-memory scratch of one order's banded solve besides its right-hand
-// sides (K = T+1 at most): factors [2][K] and alpha [K], plus alignment slack
+// sides (K = T+1 at most): factors [2][K], forward coefficients [2][K], plus
+// alignment slack
 __host__ __device__ inline size_t band_scratch_bytes(int T) {
-  return (size_t)(T + 1) * (2 * sizeof(double4_32a) + sizeof(double)) + 32;
+  return (size_t)(T + 1) * (2 * sizeof(double4_32a) + 2 * sizeof(double2)) + 32;
 }
 
 // complex FP64 helpers of the chain scans
@@ -83,23 +90,19 @@ __device__ __forceinline__ double2 zshfl_down(double2 v, int d) {
 // composes its affine maps, the lanes combine the composites in log2(32)
 // shuffle steps, and each lane re-runs its segment from its incoming value.
 // A sequential elimination would chain K dependent FP64 steps; this chains
-// about 2 S + 5.  sr[1 + field][j] holds r on entry, x on return.
-__device__ __forceinline__ void band_chain_scan(int c, int lane, int K, const double4_32a *stab, const double *sal,
+// about 2 S + 5.  sr[1 + field][j] holds r on entry, x on return (be_j in
+// between); stab [2][K] {c', 1/w}, sal [2][K] al, by field.
+__device__ __forceinline__ void band_chain_scan(int c, int lane, int K, const double4_32a *stab, const double2 *sal,
                                                 double2 *sr) {
   const int S = (K + 31) >> 5, j0 = min(K, lane * S), j1 = min(K, j0 + S);
-  auto coefs = [&](int j, double2 *al, double2 *be) {
-    const int f = (j + c) & 1;
-    const double4_32a q = stab[f * K + j];
-    const double a = f ? -sal[j] : sal[j];
-    const double2 iw = make_double2(q.z, q.w), r = sr[(1 + f) * K + j];
-    *al = make_double2(-a * iw.x, -a * iw.y);
-    *be = zmul(r, iw);
-  };
   // forward: composite of the lane's maps, inclusive scan, re-run
   double2 A = make_double2(1.0, 0.0), B = make_double2(0.0, 0.0);
   for (int j = j0; j < j1; ++j) {
-    double2 al, be;
-    coefs(j, &al, &be);
+    const int f = (j + c) & 1;
+    const double4_32a q = stab[f * K + j];
+    double2 *p = sr + (1 + f) * K + j;
+    const double2 al = sal[f * K + j], be = zmul(*p, make_double2(q.z, q.w));
+    *p = be;
     A = zmul(al, A);
     B = zfma(al, B, be);
   }
@@ -113,10 +116,10 @@ __device__ __forceinline__ void band_chain_scan(int c, int lane, int K, const do
   double2 y = zshfl_up(B, 1);
   if (lane == 0) y = make_double2(0.0, 0.0);
   for (int j = j0; j < j1; ++j) {
-    double2 al, be;
-    coefs(j, &al, &be);
-    y = zfma(al, y, be);
-    sr[(1 + ((j + c) & 1)) * K + j] = y;
+    const int f = (j + c) & 1;
+    double2 *p = sr + (1 + f) * K + j;
+    y = zfma(sal[f * K + j], y, *p);
+    *p = y;
   }
   // backward: maps x_{j+1} -> x_j composed from the right, suffix scan, re-run
   A = make_double2(1.0, 0.0);
@@ -147,34 +150,52 @@ __device__ __forceinline__ void band_chain_scan(int c, int lane, int K, const do
 }
 
 // Solve the order-m system in place.  sr[3][K] (Phi, zeta, delta rows of
-// order m, K = T+1-m) holds b on entry and x on return; tab = the node's
-// factor table [2][nc] (zeta rows, delta rows); scratch = band_scratch_bytes(T)
-// of shared memory (any 16-byte alignment).  Called by every thread of a
-// block of at least 64 threads (warps 0 and 1 solve the two chains); ends
-// with a barrier.
+// order m, K = T+1-m) holds b on entry and x on return; tab = the factor table
+// of the step size (band_table_entries); scratch = band_scratch_bytes(T) of
+// shared memory (any 16-byte alignment).  The per-degree constants of the Phi
+// elimination, g = h k / s and 1/s, come from the SDC node's factors `fac`
+// (layouts of k_sdc_node: one solve {s, 1/s, 1/det, h k}; `fac_split`
+// {1/det0, h k, h nu k, 1/s}, whose banded solve has nu = 0) or, with fac =
+// nullptr, are computed from h and nu.  Called by every thread of a block of
+// at least 64 threads (warps 0 and 1 solve the two chains); ends with a
+// barrier.
 __device__ __forceinline__ void band_order_solve(int m, int T, double h, double inva2, double nu, double phibar,
-                                                 CorArgs cor, const double4_32a *__restrict__ tab, double2 *sr,
+                                                 CorArgs cor, const double4_32a *__restrict__ tab,
+                                                 const double4_32a *__restrict__ fac, bool fac_split, double2 *sr,
                                                  void *scratch) {
   const int K = T + 1 - m, p0 = poff(T, m), nc = ncoef_of(T);
   double4_32a *stab = reinterpret_cast<double4_32a *>((reinterpret_cast<uintptr_t>(scratch) + 31) & ~uintptr_t(31));
-  double *sal = reinterpret_cast<double *>(stab + 2 * K);          // [K]
-  const double th = cor.tw * h;
+  double2 *sal = reinterpret_cast<double2 *>(stab + 2 * K);   // [2][K]
+  const double2 *tal = reinterpret_cast<const double2 *>(tab + 2 * (size_t)nc);
+  auto consts = [&](int n, double *g, double *is) {
+    if (fac) {
+      const double4_32a q = fac[n];
+      *g = fac_split ? q.y : q.w * q.y;
+      *is = fac_split ? 1.0 : q.y;
+    } else {
+      const double k = (double)n * (n + 1) * inva2;
+      *is = 1.0 / (1.0 + h * nu * k);
+      *g = h * k * *is;
+    }
+  };
   for (int j = threadIdx.x; j < K; j += blockDim.x) {
-    const int n = m + j;
-    const double k = (double)n * (n + 1) * inva2, s = 1.0 + h * nu * k, g = h * k / s;
+    double g, is;
+    consts(m + j, &g, &is);
     const double2 bP = sr[j];
     sr[2 * K + j].x = fma(g, bP.x, sr[2 * K + j].x);
     sr[2 * K + j].y = fma(g, bP.y, sr[2 * K + j].y);
     stab[j] = tab[p0 + j];
     stab[K + j] = tab[(size_t)nc + p0 + j];
-    sal[j] = th * cor.ab[p0 + j].x;
+    sal[j] = tal[p0 + j];
+    sal[K + j] = tal[(size_t)nc + p0 + j];
   }
   __syncthreads();
   if (threadIdx.x < 64) band_chain_scan(threadIdx.x >> 5, threadIdx.x & 31, K, stab, sal, sr);
   __syncthreads();
+  const double hp = h * phibar;
   for (int j = threadIdx.x; j < K; j += blockDim.x) {
-    const int n = m + j;
-    const double k = (double)n * (n + 1) * inva2, is = 1.0 / (1.0 + h * nu * k), hp = h * phibar;
+    double g, is;
+    consts(m + j, &g, &is);
     const double2 bP = sr[j], d = sr[2 * K + j];
     sr[j] = make_double2((bP.x - hp * d.x) * is, (bP.y - hp * d.y) * is);
   }

@@ -230,7 +230,7 @@ struct swe_ctx {
   swe_params prm;
   int max_states;     // states per RHS pass (plan->max_batch / 5)
   // Coriolis term implicit: coupling table [ncoef] and the factor table of
-  // swe_implicit_solve [2][ncoef] (banded.cu)
+  // swe_implicit_solve [3 ncoef] (banded.cuh band_table_entries)
   double4_32a *d_cor = nullptr;
   double4_32a *d_band_scr = nullptr;
   ~swe_ctx();
@@ -245,7 +245,7 @@ struct sdc_level {
   double Q[16][16], QE[16][16], QI[16][16];
   double *d_old = nullptr;   // [M][max_batch][3][ncoef] c128: node-update constants
   double *d_fac = nullptr;   // [M+1][T+1][4] implicit-solve factors per node and degree (solver.cu)
-  double4_32a *d_band = nullptr;   // Coriolis implicit: [M+1][2][ncoef] banded-solve factors per node
+  double4_32a *d_band = nullptr;   // Coriolis implicit: banded-solve factor tables per node [M+1][3 ncoef]
 };
 
 // CUDA graphs of iteration blocks keyed by (iterations, last): the first call

@@ -185,7 +185,7 @@ __global__ void __launch_bounds__(kChainThreads, 2) k_chain_node(ChainStep st, C
     __syncthreads();
   }
   if (g.cor.tw != 0.0)   // the analysis is done: its work region holds the banded solve's scratch
-    order_node_update_band(m, T, st.k, st.ns, c, st.h, g.dinva2, g.nu, g.phibar, g.split, g.cor, st.band,
+    order_node_update_band(m, T, st.k, st.ns, c, st.h, g.dinva2, g.nu, g.phibar, g.split, g.cor, st.band, st.fac,
                            st.O + (size_t)(st.k - 1) * 3 * nc, st.fe, st.fi, st.th, thk, work);
   else
     order_node_update(m, T, st.k, st.ns, c, st.hphibar, g.split, st.fac, st.O + (size_t)(st.k - 1) * 3 * nc, st.fe,
@@ -256,7 +256,7 @@ static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, doub
       st.hphibar = c.h[k] * ctx->prm.phibar;
       st.fac = (const double4_32a *)l->d_fac + (size_t)k * (p->T + 1);
       st.h = c.h[k];
-      st.band = l->d_band ? l->d_band + (size_t)k * 2 * p->ncoef : nullptr;
+      st.band = l->d_band ? l->d_band + (size_t)k * band_table_entries(p->ncoef) : nullptr;
       const bool recv = k == 1 && (n > n0 || recv_first);
       if (k > 1) {                                   // analysis of node k-1 of this slice
         st.a_th = st.th + (k - 1) * ns;

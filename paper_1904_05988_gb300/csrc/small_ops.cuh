@@ -396,10 +396,11 @@ __device__ __forceinline__ void order_node_update(int m, int T, int i, size_t ns
 // of order m are gathered in sm_th [3][T+1-m] and solved there by the banded
 // solve of banded.cuh (scratch: band_scratch_bytes(T) of shared memory; the
 // factor table `band` is built with nu = 0 when `split`, and the diffusion
-// substep follows as in order_node_update).
+// substep follows as in order_node_update; fac = the node's solve factors).
 __device__ __forceinline__ void order_node_update_band(int m, int T, int i, size_t ns, const SdcCoef &c, double h,
                                                        double inva2, double nu, double phibar, bool split,
                                                        CorArgs cor, const double4_32a *__restrict__ band,
+                                                       const double4_32a *__restrict__ fac,
                                                        const double2 *__restrict__ O, const double2 *__restrict__ fe,
                                                        const double2 *__restrict__ fi, double2 *__restrict__ th,
                                                        double2 *sm_th, void *scratch) {
@@ -415,8 +416,7 @@ __device__ __forceinline__ void order_node_update_band(int m, int T, int i, size
       v.y = fma(c.nI[i][j], g.y, fma(c.nE[i][j], a.y, v.y));
     }
     if (split) {   // r - h nu k old
-      const int n = m + (t - f * len);
-      const double hnk = h * nu * ((double)n * (n + 1) * inva2);
+      const double hnk = fac[m + (t - f * len)].z;
       const double2 o = out[e];
       v.x = fma(-hnk, o.x, v.x);
       v.y = fma(-hnk, o.y, v.y);
@@ -424,16 +424,15 @@ __device__ __forceinline__ void order_node_update_band(int m, int T, int i, size
     sm_th[t] = v;
   }
   __syncthreads();
-  band_order_solve(m, T, h, inva2, split ? 0.0 : nu, phibar, cor, band, sm_th, scratch);
+  band_order_solve(m, T, h, inva2, split ? 0.0 : nu, phibar, cor, band, fac, split, sm_th, scratch);
   for (int t = threadIdx.x; t < 3 * len; t += blockDim.x) {
     const int f = t / len;
     const size_t e = (size_t)f * nc + p0 + (t - f * len);
     double2 x = sm_th[t];
     if (split) {   // (x* + h nu k old) / s
-      const int n = m + (t - f * len);
-      const double hnk = h * nu * ((double)n * (n + 1) * inva2), is = 1.0 / (1.0 + hnk);
+      const double4_32a q = fac[m + (t - f * len)];
       const double2 o = out[e];
-      x = make_double2(fma(hnk, o.x, x.x) * is, fma(hnk, o.y, x.y) * is);
+      x = make_double2(fma(q.z, o.x, x.x) * q.w, fma(q.z, o.y, x.y) * q.w);
       sm_th[t] = x;
     }
     out[e] = x;

@@ -8,6 +8,7 @@
 #include <vector>
 
 #include "internal.cuh"
+#include "banded.cuh"
 
 namespace pfsh {
 
@@ -241,7 +242,7 @@ extern "C" int sdc_level_create(sdc_level **out, swe_ctx *ctx, int nodes, double
   }
   if (coriolis_implicit(ctx->prm)) {
     // banded-solve factors of nodes 1..M (h = dt QI[i][i]), computed on the device
-    const size_t per = (size_t)2 * ctx->plan->ncoef;
+    const size_t per = band_table_entries(ctx->plan->ncoef);
     int rc2 = PFSH_OK;
     if (cudaMalloc(&l->d_band, (size_t)nodes * per * sizeof(double4_32a)) != cudaSuccess) {
       cudaGetLastError();
