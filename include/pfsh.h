@@ -59,7 +59,7 @@ typedef enum {
   PFSH_EINVAL = -1,       /* invalid argument (checked on the host)          */
   PFSH_ENOMEM = -2,       /* device or host allocation failed in *_create     */
   PFSH_ECUDA = -3,        /* a CUDA runtime/driver call failed                */
-  PFSH_EUNSUPPORTED = -4, /* valid request this build/device cannot serve    */
+  PFSH_EUNSUPPORTED = -4, /* valid request the library/device cannot serve  */
   PFSH_ETIMEOUT = -5,     /* a bounded device-side wait gave up               */
   PFSH_ENUMERIC = -6      /* device-side check found a non-finite value       */
 } pfsh_status;

@@ -118,7 +118,7 @@ _lib.pfsh_profiler_report.restype = c_int
 
 
 def available_precisions() -> list[str]:
-    """Precision names this build serves (probed with argument-free checks)."""
+    """Precision names the compiled library serves (probed with argument-free checks)."""
     return [name for name, code in PREC_NAMES.items() if code in _BUILT_PRECISIONS]
 
 

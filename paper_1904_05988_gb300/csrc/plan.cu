@@ -290,7 +290,7 @@ extern "C" int sht_plan_create(sht_plan **out, int T, int nlat, int nlon, int ma
   if (nlon % 2 != 0 || nlon <= 2 * (T + 1)) return fail(PFSH_EINVAL, "sht_plan_create: nlon must be even and > 2(T+1)");
   if (max_batch < 1) return fail(PFSH_EINVAL, "sht_plan_create: max_batch must be >= 1");
   if (prec != PFSH_FP64 && prec != PFSH_FP32 && !uses_tensor_cores(prec))
-    return fail(PFSH_EUNSUPPORTED, "sht_plan_create: precision not available in this build");
+    return fail(PFSH_EUNSUPPORTED, "sht_plan_create: precision not compiled into the library");
   sht_plan *p = new (std::nothrow) sht_plan();
   if (!p) return fail(PFSH_ENOMEM, "sht_plan_create: host allocation");
   p->T = T;
