@@ -68,5 +68,6 @@ def test_tuning_cache_file(tmp_path, monkeypatch):
     assert all(r["T"] == T and r["nlat"] == nlat and r["tile_mult"] in (1, 2) and len(r["us"]) == 2 for r in rows)
     for r in rows:     # the plan uses what was measured faster: 1 tile per order below 256 rows, or 2
         assert tiles[r["dir"]][r["nb"] - 1] == r["tile_mult"]
-        assert (r["tile_mult"] == 2) == (r["us"][1] < r["us"][0])
+        chosen, other = r["us"][r["tile_mult"] - 1], r["us"][2 - r["tile_mult"]]
+        assert chosen <= other        # (times are printed to 0.01 us; a tie may go either way)
     print("\n" + "\n".join(json.dumps(r) for r in rows))
