@@ -92,3 +92,23 @@ def test_pfasst_single_slice_is_two_level_sdc():
     ref = _serial(f, th0, 1)
     out = PFASST(f, c, 1).run(th0, 8)
     assert np.max(np.abs(out - ref)) < 1e-12 * np.max(np.abs(ref))
+
+
+@pytest.mark.parametrize("coriolis,split", [(True, False), (False, True), (True, True)])
+def test_pfasst_with_other_splits_converges_to_the_same_collocation_solution(coriolis, split):
+    """The Coriolis term in F_I (which couples degrees n +- 1, so that
+    restriction and F_I no longer commute at the top coarse degree: the FAS
+    term absorbs it) and the two-substep node solve leave the fixed point of
+    Algorithm 1 unchanged: PFASST converges to the serial fine collocation
+    solution of the paper's split, for alpha < 1."""
+    Tf, Tc, n_ts, dt = 15, 7, 4, 600.0
+    f, _ = _levels(Tf, Tc, dt)
+    th0 = _state(Tf)
+    ref = _serial(f, th0, n_ts)
+    p = SWEParams(a=syn.EARTH_RADIUS, omega=syn.OMEGA, g=syn.GRAVITY, nu=1e5, phibar=syn.GRAVITY * syn.MEAN_DEPTH,
+                  coriolis_implicit=coriolis, implicit_split=split)
+    fo = SDCLevel(Tf, *syn.gaussian_grid_size(Tf), 5, dt, p)
+    co = SDCLevel(Tc, *syn.gaussian_grid_size(Tc), 3, dt, p)
+    errs = [np.max(np.abs(PFASST(fo, co, n_ts).run(th0, k) - ref)) for k in (2, 14)]
+    assert errs[1] < 1e-12 * np.max(np.abs(ref))
+    assert errs[1] < errs[0]
