@@ -438,11 +438,13 @@ def kernel_work_per_iteration(name: str, prec: str):
         return (nfs * (5 * ncf1 * 2 * elem + 3 * st_f) + ncb * (5 * ncc1 * 2 * elem + 3 * st_c), "byte",
                 ("hbm", None), None)
     if name == "k_sdc_old":
-        # fine sweeps of every slice: per complex coefficient 2 M (M+1) complex
-        # FMAs of real coefficients (F_E and F_I at every node into M old
-        # parts) = 8 M (M+1) real flops; FP64-pipe bound (measured 83% busy)
+        # fine sweeps of every slice: F_E and F_I at every node into M old
+        # parts; per real component M(M+1)/2 coefficient pairs take two FMAs
+        # and M(M+1)/2 (j = 0 or j > i, equal coefficients) one FMA on the sum
+        # F_E + F_I (M+1 additions): (M+1)(3M+1) flops, 2x per complex
+        # coefficient; FP64-pipe bound (measured 83% busy)
         mf = NF - 1
-        return NTS * 3 * ncf * 8 * mf * (mf + 1), "flop", ("alu", "FP64 pipe"), None
+        return NTS * 3 * ncf * 2 * (mf + 1) * (3 * mf + 1), "flop", ("alu", "FP64 pipe"), None
     if name == "k_chain_node":
         # every launch but the first of a group analyses one node (5 columns)
         # and synthesises the next (4 columns) of one T127 slice
@@ -468,7 +470,7 @@ def kernel_work_per_iteration(name: str, prec: str):
 # have none.
 NCU_TRAFFIC = {
     "k_chain_node": (5.14176e6, ("bf16x3", "bf16", "fp16", "fp32"), "profiles/k_chain_node_T127_bf16x3.md"),
-    "k_sdc_old": (354e6, ("bf16x3", "bf16", "fp16", "fp32", "fp64"), "profiles/k_sdc_old_T255_16slices.md"),
+    "k_sdc_old": (353.359616e6, ("bf16x3", "bf16", "fp16", "fp32", "fp64"), "profiles/k_sdc_old_T255_16slices.md"),
 }
 
 

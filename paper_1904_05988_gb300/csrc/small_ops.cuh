@@ -324,11 +324,17 @@ __device__ __forceinline__ void order_old_part(int m, int T, int M, size_t ns, c
     for (int j = 0; j <= MAXM; ++j) {
       if (j > M) break;
       const double2 a = fe[(size_t)j * ns + e], f = fi[(size_t)j * ns + e];
+      const double2 sj = make_double2(a.x + f.x, a.y + f.y);
 #pragma unroll
       for (int i = 1; i <= MAXM; ++i)
         if (i <= M) {
-          acc[i].x = fma(c.cI[i][j], f.x, fma(c.cE[i][j], a.x, acc[i].x));
-          acc[i].y = fma(c.cI[i][j], f.y, fma(c.cE[i][j], a.y, acc[i].y));
+          if (j == 0 || j > i) {   // cE[i][j] = cI[i][j] = dt Q[i][j] (as in k_sdc_old)
+            acc[i].x = fma(c.cE[i][j], sj.x, acc[i].x);
+            acc[i].y = fma(c.cE[i][j], sj.y, acc[i].y);
+          } else {
+            acc[i].x = fma(c.cI[i][j], f.x, fma(c.cE[i][j], a.x, acc[i].x));
+            acc[i].y = fma(c.cI[i][j], f.y, fma(c.cE[i][j], a.y, acc[i].y));
+          }
         }
     }
 #pragma unroll

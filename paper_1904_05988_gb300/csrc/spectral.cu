@@ -234,7 +234,10 @@ int implicit_solve_launch(int T, const double *b, double *x, double h, int B, co
 
 // O_i = theta_0 + sum_j cE[i][j] FE_j + cI[i][j] FI_j (+ tau_i),  i = 1..M
 // (M a template parameter: the accumulators stay in registers and no FP64
-// issue slot is spent on masked-off terms)
+// issue slot is spent on masked-off terms).  For j = 0 and j > i both
+// coefficients are dt Q[i][j] (the QE and QI corrections vanish there), so
+// those terms take one FMA on S_j = FE_j + FI_j: 35 instead of 40 FP64
+// operations per real component for M = 4 (the kernel is FP64-bound).
 template <int M>
 __global__ void __launch_bounds__(128) k_sdc_old(int nc3, int B, size_t nstride, SdcCoef c,
                                                  const double2 *__restrict__ th, const double2 *__restrict__ fe,
@@ -249,10 +252,16 @@ __global__ void __launch_bounds__(128) k_sdc_old(int nc3, int B, size_t nstride,
 #pragma unroll
   for (int j = 0; j <= M; ++j) {
     const double2 e = fe[(size_t)j * nstride + t], f = fi[(size_t)j * nstride + t];
+    const double2 sj = make_double2(e.x + f.x, e.y + f.y);
 #pragma unroll
     for (int i = 1; i <= M; ++i) {
-      acc[i].x = fma(c.cI[i][j], f.x, fma(c.cE[i][j], e.x, acc[i].x));
-      acc[i].y = fma(c.cI[i][j], f.y, fma(c.cE[i][j], e.y, acc[i].y));
+      if (j == 0 || j > i) {
+        acc[i].x = fma(c.cE[i][j], sj.x, acc[i].x);
+        acc[i].y = fma(c.cE[i][j], sj.y, acc[i].y);
+      } else {
+        acc[i].x = fma(c.cI[i][j], f.x, fma(c.cE[i][j], e.x, acc[i].x));
+        acc[i].y = fma(c.cI[i][j], f.y, fma(c.cE[i][j], e.y, acc[i].y));
+      }
     }
   }
 #pragma unroll
