@@ -112,3 +112,28 @@ def test_pfasst_with_other_splits_converges_to_the_same_collocation_solution(cor
     errs = [np.max(np.abs(PFASST(fo, co, n_ts).run(th0, k) - ref)) for k in (2, 14)]
     assert errs[1] < 1e-12 * np.max(np.abs(ref))
     assert errs[1] < errs[0]
+
+
+@pytest.mark.parametrize("npf,order", [(1, 1), (2, 2), (3, 3)])
+def test_pfasst_iterations_add_one_order_each(npf, order):
+    """alpha = 1: a fixed number N_PF of PFASST iterations per block converges
+    with order N_PF in dt (each iteration adds one order below the collocation
+    order, as for SDC sweeps; the paper prints no rates, so this pins the
+    iteration structure).  T10, 4 slices, 5/3 nodes, window 19200 s in 1, 2
+    and 4 blocks, against SDC(5) run to convergence with 1/8 of the step."""
+    import math
+    from oracle.sdc import sdc_run
+    T, n_ts, t_end = 10, 4, 19200.0
+    th0 = _state(T)
+    gf = syn.gaussian_grid_size(T)
+    ref = sdc_run(SDCLevel(T, *gf, 5, t_end / 32, _params()), th0, 32, 10)
+    errs = []
+    for blocks in (1, 2, 4):
+        dt = t_end / (n_ts * blocks)
+        f, c = _levels(T, T, dt)
+        x = th0
+        for _ in range(blocks):
+            x = PFASST(f, c, n_ts).run(x, npf)[-1]
+        errs.append(np.max(np.abs(x - ref)))
+    rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
+    assert abs(rates[-1] - order) < 0.3, rates
