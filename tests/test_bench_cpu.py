@@ -1,0 +1,48 @@
+"""The roofline arithmetic of bench.py (no GPU): achieved = algorithmic work
+of the profiled iterations / their summed duration, frac = achieved / peak,
+measured DRAM traffic only where one ncu capture describes every launch."""
+import os
+import sys
+
+import pytest
+
+ROOT = os.path.dirname(os.path.dirname(os.path.abspath(__file__)))
+sys.path.insert(0, ROOT)
+import bench  # noqa: E402
+
+
+def test_fp64_bound_entry_uses_the_work_model_and_the_fp64_peak():
+    work, unit, (bound, note), _ = bench.kernel_work_per_iteration("k_sdc_old", "bf16x3")
+    assert unit == "flop" and bound == "alu" and note == "FP64 pipe"
+    # 32 slices x 3 fields x ncoef(255) x 2 (M+1)(3M+1) flops with M = 4
+    assert work == 32 * 3 * 32896 * 2 * 5 * 13
+    e = bench.roofline_entry("k_sdc_old", 4, 0.84, "bf16x3", 2)
+    assert e["bound"] == "alu" and e["peak"] == bench.FP64_PEAK_TFLOPS and e["unit"] == "TFLOP/s"
+    assert abs(e["achieved"] - work * 2 / 0.84e-3 / 1e12) < 1e-12
+    assert abs(e["frac"] - e["achieved"] / e["peak"]) < 1e-15
+    assert e["mean_launch_ms"] == pytest.approx(0.21)
+    assert e["traffic"] == bench.NCU_TRAFFIC["k_sdc_old"][0]
+
+
+def test_traffic_only_for_captured_uniform_kernels():
+    assert bench.roofline_entry("k_grid_rhs", 160, 3.5, "bf16x3", 2)["traffic"] is None
+    assert bench.roofline_entry("k_chain_node", 132, 3.8, "fp64", 2)["traffic"] is None   # FP64 build of the kernel
+    assert bench.roofline_entry("k_chain_node", 132, 3.8, "bf16x3", 2)["traffic"] == \
+        bench.NCU_TRAFFIC["k_chain_node"][0]
+    for name, (_, _, src) in bench.NCU_TRAFFIC.items():
+        assert os.path.exists(os.path.join(ROOT, src)), src
+
+
+def test_hbm_entry_and_tensor_kernels_below_the_ridge():
+    pk, _ = bench.peaks()
+    e = bench.roofline_entry("k_grid_rhs", 160, 3.5, "bf16x3", 2)
+    assert e["bound"] == "hbm" and e["peak"] == pk["hbm_gbs"] and e["unit"] == "GB/s"
+    a = bench.roofline_entry("k_anal_bf16x3", 32, 1.8, "bf16x3", 2)
+    assert a["bound"] == "hbm"                                 # 3xBF16 GEMMs at these widths sit below the ridge
+    assert "below the ridge" in a["note"]
+
+
+def test_cores_used_is_cpu_time_over_wall_time():
+    assert bench.cores_used(10.0, 5.0) == 2
+    assert bench.cores_used(0.2, 5.0) == 1
+    assert bench.job_value(30.0, 2, 10) == pytest.approx(2 * 10 / 0.030)
