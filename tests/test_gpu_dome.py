@@ -14,10 +14,13 @@ the first time both step sizes reach (3 PFASST blocks of 16 x 100 s, 80
 reference steps), instead of the paper's 102,400 s window.
 
 Both runs are GPU runs of the library (the reference is the serial method the
-paper uses as reference); the oracle only projects the dome.  Bounds:
-measured values on GB300 in brackets.
+paper uses as reference); the oracle only projects the dome.  The printed
+values and the readings come from tests/golden/gaussian_dome_sec6_1.json.
+Bounds: measured values on GB300 in brackets.
 """
+import json
 import math
+import os
 
 import numpy as np
 import pytest
@@ -33,10 +36,15 @@ ensure_built()
 import paper_1904_05988_gb300 as ps  # noqa: E402
 
 DEV = torch.device("cuda:0")
-TF, TC = 255, 203
-NTS, NF, NC, NPF = 16, 5, 3, 8
-DT, DT_REF, T_END = 100.0, 60.0, 4800.0
-HBAR, AMP, ALPHA = 29400.0, 6000.0, 225.0
+with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "gaussian_dome_sec6_1.json")) as _fh:
+    _G = json.load(_fh)       # the printed set-up of Section 6.1 and the readings around it
+_P, _R = _G["printed"], _G["readings"]
+TF = _P["R_f"] - 1
+TC = _P["R_f"] * _P["pfasst"]["alpha"][0] // _P["pfasst"]["alpha"][1] - 1
+NTS, NF, NC, NPF = (_P["pfasst"][k] for k in ("n_ts", "fine_nodes", "coarse_nodes", "N_PF"))
+DT, DT_REF, T_END = _P["dt_s"], _R["reference_dt_s"], _R["window_used_s"]
+HBAR, AMP, ALPHA = _P["h_bar_m"], _P["A_m"], _R["dome_sharpness_alpha"]
+assert (TF, TC, NTS, NF, NC, NPF) == (255, 203, 16, 5, 3, 8)
 BOUNDS = {  # E_32, E_64, E_256 of PFASST against the reference
     "fp64": (1e-11, 5e-11, 2e-7),       # (1.3e-12, 6.4e-12, 3.5e-8)
     "bf16x3": (5e-10, 5e-10, 2e-7),     # (1.0e-10, 1.0e-10, 3.5e-8)
