@@ -43,11 +43,17 @@ over time slices in rank order; a send is a copy into the receiver's array.
   rejected.  Finally the fine right-hand side at node 0 is re-evaluated
   (last term of the iteration cost in Section 5.5).
 
+The steps that are independent across slices go through ``_each``, which
+either loops here or hands the same level method to worker processes
+(``oracle.pool``); the arithmetic is the same either way.
+
 Pins (tests/test_oracle_pfasst.py): R o P = identity; nested Lobatto time
 restriction is injection; the FAS invariant (a coarse sweep with tau leaves
 the restriction of a fine collocation solution unchanged); with enough
 iterations PFASST converges to the serial collocation solution of every
-slice, for alpha = 1 and alpha < 1.
+slice, for alpha = 1 and alpha < 1; the predictor's rounds equal the
+slice-by-slice statement (slice n sweeps n + 1 times, each time from its
+predecessor's value of the previous round); the worker pool changes no bit.
 """
 from __future__ import annotations
 
@@ -68,11 +74,24 @@ def interpolate_space(x: np.ndarray, Lf: int) -> np.ndarray:
 
 
 class PFASST:
-    def __init__(self, fine: SDCLevel, coarse: SDCLevel, n_ts: int):
+    """``pool`` (optional): an ``oracle.pool.SlicePool`` whose levels "f" and
+    "c" were built from ``fine.args`` and ``coarse.args``; the per-slice
+    independent steps then run in its worker processes (same arithmetic)."""
+
+    def __init__(self, fine: SDCLevel, coarse: SDCLevel, n_ts: int, pool=None):
         self.f, self.c, self.n_ts = fine, coarse, n_ts
         self.Lf, self.Lc = fine.T + 1, coarse.T + 1
         self.R_t = lagrange_matrix(fine.tau, coarse.tau)     # (Mc+1, Mf+1)
         self.P_t = lagrange_matrix(coarse.tau, fine.tau)     # (Mf+1, Mc+1)
+        self.pool = pool
+
+    def _each(self, level: str, method: str, arg_tuples: list) -> list:
+        """[getattr(level, method)(*a) for a in arg_tuples], slices in order;
+        the calls are independent of one another."""
+        if self.pool is None or len(arg_tuples) < 2:
+            lvl = self.f if level == "f" else self.c
+            return [getattr(lvl, method)(*a) for a in arg_tuples]
+        return self.pool.run(level, method, arg_tuples)
 
     # ---- transfer operators on space-time vectors [nodes, 3, L, L] ----
     def restrict(self, x_f: np.ndarray) -> np.ndarray:
@@ -88,13 +107,6 @@ class PFASST:
         QF_c = np.einsum("ij,j...->i...", self.c.Q, FE_c + FI_c)
         return self.f.dt * self.restrict(QF_f) - self.c.dt * QF_c
 
-    def _eval_nodes(self, level: SDCLevel, theta: np.ndarray):
-        FE = np.empty_like(theta)
-        FI = np.empty_like(theta)
-        for i in range(theta.shape[0]):
-            FE[i], FI[i] = level.eval_f(theta[i])
-        return FE, FI
-
     # ---- predictor (Section 5.2.1) ----
     def predict(self, theta0: np.ndarray) -> None:
         n_ts, Mc = self.n_ts, self.c.M
@@ -106,27 +118,30 @@ class PFASST:
         base_c = self.th_c.copy()
         for j in range(n_ts):
             ends = self.th_c[:, Mc].copy()           # values after round j-1
-            for n in range(j, n_ts):
-                if j > 0 and n > 0:
-                    self.th_c[n, 0] = ends[n - 1]
-                    self.FE_c[n, 0], self.FI_c[n, 0] = self.c.eval_f(self.th_c[n, 0])
-                self.th_c[n], self.FE_c[n], self.FI_c[n] = self.c.sweep(
-                    self.th_c[n], self.FE_c[n], self.FI_c[n])
+            recv = [n for n in range(max(j, 1), n_ts)] if j > 0 else []
+            for n in recv:
+                self.th_c[n, 0] = ends[n - 1]
+            for n, (fe, fi) in zip(recv, self._each("c", "eval_f", [(self.th_c[n, 0],) for n in recv])):
+                self.FE_c[n, 0], self.FI_c[n, 0] = fe, fi
+            swept = self._each("c", "sweep", [(self.th_c[n], self.FE_c[n], self.FI_c[n]) for n in range(j, n_ts)])
+            for n, (th, fe, fi) in zip(range(j, n_ts), swept):
+                self.th_c[n], self.FE_c[n], self.FI_c[n] = th, fe, fi
         Mf = self.f.M
         self.th_f = np.empty((n_ts, Mf + 1) + theta0.shape, dtype=np.complex128)
         self.FE_f = np.empty_like(self.th_f)
         self.FI_f = np.empty_like(self.th_f)
         for n in range(n_ts):
             self.th_f[n] = theta0[None] + self.interpolate(self.th_c[n] - base_c[n])
-            self.FE_f[n], self.FI_f[n] = self._eval_nodes(self.f, self.th_f[n])
+        for n, (fe, fi) in enumerate(self._each("f", "eval_nodes", [(self.th_f[n],) for n in range(n_ts)])):
+            self.FE_f[n], self.FI_f[n] = fe, fi
 
     # ---- one iteration of Algorithm 1 ----
     def iteration(self, last: bool = False) -> None:
         n_ts, Mf, Mc = self.n_ts, self.f.M, self.c.M
         # A) fine sweeps (parallel across slices)
-        for n in range(n_ts):
-            self.th_f[n], self.FE_f[n], self.FI_f[n] = self.f.sweep(
-                self.th_f[n], self.FE_f[n], self.FI_f[n])
+        swept = self._each("f", "sweep", [(self.th_f[n], self.FE_f[n], self.FI_f[n]) for n in range(n_ts)])
+        for n, (th, fe, fi) in enumerate(swept):
+            self.th_f[n], self.FE_f[n], self.FI_f[n] = th, fe, fi
         if last:
             return
         sent_f = self.th_f[:, Mf].copy()
@@ -134,7 +149,8 @@ class PFASST:
         tau = np.empty((n_ts, Mc + 1) + self.th_c.shape[2:], dtype=np.complex128)
         for n in range(n_ts):
             self.th_c[n] = self.restrict(self.th_f[n])
-            self.FE_c[n], self.FI_c[n] = self._eval_nodes(self.c, self.th_c[n])
+        for n, (fe, fi) in enumerate(self._each("c", "eval_nodes", [(self.th_c[n],) for n in range(n_ts)])):
+            self.FE_c[n], self.FI_c[n] = fe, fi
             tau[n] = self.fas(self.FE_f[n], self.FI_f[n], self.FE_c[n], self.FI_c[n])
         th_c_saved = self.th_c.copy()
         FE_c_saved = self.FE_c.copy()
@@ -156,8 +172,8 @@ class PFASST:
                 received = sent_f[n - 1]
                 self.th_f[n, 0] = received + interpolate_space(
                     self.th_c[n, 0] - restrict_space(received, self.Lc), self.Lf)
-        for n in range(n_ts):
-            self.FE_f[n, 0], self.FI_f[n, 0] = self.f.eval_f(self.th_f[n, 0])
+        for n, (fe, fi) in enumerate(self._each("f", "eval_f", [(self.th_f[n, 0],) for n in range(n_ts)])):
+            self.FE_f[n, 0], self.FI_f[n, 0] = fe, fi
 
     def run(self, theta0: np.ndarray, n_iter: int) -> np.ndarray:
         """Predictor + n_iter iterations (the last one is Step A only);

@@ -115,6 +115,7 @@ class SDCLevel:
 
     def __init__(self, T: int, nlat: int, nlon: int, num_nodes: int, dt: float,
                  params: SWEParams):
+        self.args = (T, nlat, nlon, num_nodes, dt, params)   # to rebuild it in a worker process
         self.T = T
         self.sht = SHT(T, nlat, nlon)
         self.p = params
@@ -127,6 +128,14 @@ class SDCLevel:
 
     def eval_f(self, theta: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
         return rhs(theta, self.sht, self.p)
+
+    def eval_nodes(self, theta: np.ndarray) -> tuple[np.ndarray, np.ndarray]:
+        """F_E, F_I at every node of theta [M+1, 3, L, L]."""
+        FE = np.empty_like(theta)
+        FI = np.empty_like(theta)
+        for i in range(theta.shape[0]):
+            FE[i], FI[i] = self.eval_f(theta[i])
+        return FE, FI
 
     def sweep(self, theta: np.ndarray, FE: np.ndarray, FI: np.ndarray,
               tau: np.ndarray | None = None):

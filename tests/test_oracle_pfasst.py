@@ -137,3 +137,64 @@ def test_pfasst_iterations_add_one_order_each(npf, order):
         errs.append(np.max(np.abs(x - ref)))
     rates = [math.log2(errs[i] / errs[i + 1]) for i in range(2)]
     assert abs(rates[-1] - order) < 0.3, rates
+
+
+def _spread_coarse(c, th0_c):
+    fe, fi = c.eval_f(th0_c)
+    M = c.M
+    return (np.repeat(th0_c[None], M + 1, 0), np.repeat(fe[None], M + 1, 0), np.repeat(fi[None], M + 1, 0))
+
+
+@pytest.mark.parametrize("Tf,Tc,n_ts", [(9, 9, 1), (9, 6, 1), (9, 6, 4)])
+def test_predictor_round_structure(Tf, Tc, n_ts):
+    """Section 5.2.1 written out slice by slice instead of round by round:
+    slice n sweeps n + 1 times on the coarse level; before its r-th sweep
+    (r >= 1) it takes as node-0 value the end value slice n-1 had after its
+    own r-th sweep (round r-1) and refreshes F there; every slice starts from
+    the spread restricted initial value.  The fine iterate is the initial
+    value plus the coarse increment interpolated in space (zero-padding) and
+    time (Lagrange), with F evaluated at every fine node.  With n_ts = 1 this
+    is one coarse sweep from the spread state.  A schedule with n sweeps for
+    slice n, or a receive from the wrong round, fails the equality."""
+    f, c = _levels(Tf, Tc, 600.0)
+    th0 = _state(Tf, seed=3)
+    pf = PFASST(f, c, n_ts)
+    pf.predict(th0)
+    base = _spread_coarse(c, restrict_space(th0, Tc + 1))
+    E = {}
+    finals = []
+    for n in range(n_ts):
+        th, FE, FI = (a.copy() for a in base)
+        for r in range(n + 1):
+            if r > 0:
+                th[0] = E[n - 1, r - 1]
+                FE[0], FI[0] = c.eval_f(th[0])
+            th, FE, FI = c.sweep(th, FE, FI)
+            E[n, r] = th[-1].copy()
+        finals.append(th)
+        assert np.array_equal(pf.th_c[n], th), n
+    P = lagrange_matrix(c.tau, f.tau)
+    for n in range(n_ts):
+        inc = interpolate_space(finals[n] - base[0], Tf + 1)
+        exp = th0[None] + np.einsum("ij,j...->i...", P, inc)
+        assert np.max(np.abs(pf.th_f[n] - exp)) <= 1e-15 * np.max(np.abs(exp))
+        for i in range(f.M + 1):
+            fe, fi = f.eval_f(pf.th_f[n, i])
+            assert np.array_equal(pf.FE_f[n, i], fe) and np.array_equal(pf.FI_f[n, i], fi)
+    if n_ts > 1:   # the later slices saw their predecessors' values: they differ from slice 0
+        assert np.max(np.abs(pf.th_c[n_ts - 1] - pf.th_c[0])) > 0
+
+
+def test_slice_pool_changes_no_arithmetic():
+    """The worker-process pool runs the same level methods: predictor + one
+    iteration give bitwise the same space-time arrays with and without it."""
+    from oracle.pool import SlicePool
+    f, c = _levels(9, 6, 600.0)
+    th0 = _state(9, seed=4)
+    a = PFASST(f, c, 3)
+    a.run(th0, 2)
+    with SlicePool({"f": f.args, "c": c.args}, workers=2) as pool:
+        b = PFASST(f, c, 3, pool=pool)
+        b.run(th0, 2)
+    for name in ("th_f", "FE_f", "FI_f", "th_c", "FE_c", "FI_c"):
+        assert np.array_equal(getattr(a, name), getattr(b, name)), name
