@@ -299,13 +299,16 @@ int pfasst_get(pfasst *pf, int level, int slice, int node, double *out,
  * inside this library, which every GPU that loads the library keeps until
  * the process exits.
  * Limits: 1 <= T <= 127, nlat even >= T+2, nlon even > 2(T+1) with prime
- * factors <= 61, and (T+1)*nlat*batch*16 bytes plus the latitudes
+ * factors <= 61 and 2*(nlon + nlon/16 + 1)*16 bytes <= 227 KiB (the
+ * longitude transform keeps two padded rows in shared memory, so nlon up to
+ * about 6800), and (T+1)*nlat*batch*16 bytes plus the latitudes
  * (nlat*8 bytes) and FFT twiddles (at most 3*nlon*16 bytes), each rounded up
  * to 256, within 4 MiB; larger requests return PFSH_EINVAL before any work
  * is queued (split the batch).
  * The first call on a device looks up the device address of that array
  * (cudaGetSymbolAddress) and remembers it; make that first call before any
- * stream capture.  All calls share the one array and every call rewrites
+ * stream capture.  The call launches on the current device: spec and grid
+ * must live there.  All calls share the one array and every call rewrites
  * what it reads, so no state carries over between calls; calls whose work
  * overlaps on the GPU (different streams, no ordering) race on it.
  * Asynchronous on `stream` like the other compute calls. */
@@ -335,6 +338,13 @@ unsigned long long pfsh_kernel_launches(void);
  * around every kernel launch (adds a little host overhead per launch);
  * on == 0: stop recording.  Enabling clears previous records. */
 int pfsh_profiler_enable(int on);
+
+/* Measured FMA throughput of the FP64 (prec = PFSH_FP64) or FP32
+ * (PFSH_FP32) pipe of the current device in TFLOP/s (FMA = 2 flops): a loop
+ * of independent FMA chains on every SM, timed with CUDA events, best of 5
+ * launches.  The roofline denominator of kernels bound by that pipe.
+ * Synchronises its own stream; takes well under a second. */
+int pfsh_alu_peak(int prec, double *tflops);
 
 /* Synchronise the device and write a JSON object
  * {"<kernel>": [launches, total_ms], ...} of the records so far into buf

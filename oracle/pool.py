@@ -34,19 +34,36 @@ def _call(task):
     return getattr(_LEVELS[name], method)(*args)
 
 
+def _ping(_):
+    return len(_LEVELS)
+
+
 class SlicePool:
     """``specs`` maps a level name to the ``SDCLevel`` constructor arguments
     (T, nlat, nlon, num_nodes, dt, params); every worker builds each level
     once.  ``run(name, method, arg_tuples)`` returns
     ``[getattr(level, method)(*a) for a in arg_tuples]``."""
 
+    # a worker that cannot start (an import error) would be restarted forever
+    # by multiprocessing.Pool: every wait below is bounded instead
+    START_TIMEOUT_S, CALL_TIMEOUT_S = 600, 7200
+
     def __init__(self, specs: dict, workers: int | None = None):
         self.workers = max(1, workers or (os.cpu_count() or 1))
         self._pool = mp.get_context("spawn").Pool(self.workers, initializer=_init, initargs=(specs,))
+        try:
+            self._pool.map_async(_ping, range(self.workers), chunksize=1).get(self.START_TIMEOUT_S)
+        except BaseException:
+            self.close()
+            raise
 
     def run(self, name: str, method: str, arg_tuples: list) -> list:
         tasks = [(name, method, tuple(a)) for a in arg_tuples]
-        return self._pool.map(_call, tasks, chunksize=1)
+        return self._pool.map_async(_call, tasks, chunksize=1).get(self.CALL_TIMEOUT_S)
+
+    def pids(self) -> list[int]:
+        """Process ids of the workers (to account for the CPU time they use)."""
+        return [p.pid for p in self._pool._pool] if self._pool is not None else []
 
     def close(self) -> None:
         if self._pool is not None:

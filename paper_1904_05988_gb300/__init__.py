@@ -31,7 +31,8 @@ EXPORTED = ["sht_plan_create", "sht_plan_destroy", "sht_plan_query", "sht_invers
             "pfasst_iteration", "pfasst_iterations", "pfasst_residual", "pfasst_get", "pfasst_ensemble_create",
             "pfasst_ensemble_destroy", "pfasst_ensemble_member", "pfasst_ensemble_predict",
             "pfasst_ensemble_iterations", "pfsh_sync_status", "pfsh_last_error",
-            "pfsh_kernel_launches", "pfsh_profiler_enable", "pfsh_profiler_report", "sht_inverse_noalloc"]
+            "pfsh_kernel_launches", "pfsh_profiler_enable", "pfsh_profiler_report", "sht_inverse_noalloc",
+            "pfsh_alu_peak"]
 
 
 class PfshError(RuntimeError):
@@ -115,6 +116,8 @@ _lib.pfsh_profiler_enable.argtypes = [c_int]
 _lib.pfsh_profiler_enable.restype = c_int
 _lib.pfsh_profiler_report.argtypes = [ctypes.c_char_p, c_size_t]
 _lib.pfsh_profiler_report.restype = c_int
+_lib.pfsh_alu_peak.argtypes = [c_int, ctypes.POINTER(c_double)]
+_lib.pfsh_alu_peak.restype = c_int
 
 
 def available_precisions() -> list[str]:
@@ -412,11 +415,25 @@ def pfsh_profiler_report() -> dict:
     return json.loads(buf.value.decode())
 
 
+def pfsh_alu_peak(prec: int | str) -> float:
+    """Measured FMA throughput (TFLOP/s) of the FP64 or FP32 pipe of the current device."""
+    prec = PREC_NAMES[prec] if isinstance(prec, str) else prec
+    out = c_double()
+    _check(_lib.pfsh_alu_peak(prec, ctypes.byref(out)))
+    return out.value
+
+
 def sht_inverse_noalloc(T: int, nlat: int, nlon: int, spec: torch.Tensor, grid: torch.Tensor,
                         stream=None) -> torch.Tensor:
     """FP64 synthesis that allocates no device memory (see include/pfsh.h):
     spec complex128 [batch, ncoef(T)] -> grid float64 [batch, nlat, nlon]."""
+    if spec.numel() % ncoef(T):
+        raise ValueError(f"spec holds {spec.numel()} coefficients, not a multiple of ncoef({T}) = {ncoef(T)}")
+    if spec.device != grid.device:
+        raise ValueError("spec and grid must live on the same device")
     batch = spec.numel() // ncoef(T)
-    _check(_lib.sht_inverse_noalloc(T, nlat, nlon, _ptr(spec, torch.complex128, batch * ncoef(T)),
-                                    _ptr(grid, torch.float64, batch * nlat * nlon), batch, _stream(stream)))
+    # the library launches on the current device: make it the tensors' device
+    with torch.cuda.device(spec.device):
+        _check(_lib.sht_inverse_noalloc(T, nlat, nlon, _ptr(spec, torch.complex128, batch * ncoef(T)),
+                                        _ptr(grid, torch.float64, batch * nlat * nlon), batch, _stream(stream)))
     return grid

@@ -13,6 +13,7 @@
 #include <math.h>
 
 #include <algorithm>
+#include <atomic>
 #include <string>
 
 #include "fft_core.cuh"
@@ -27,8 +28,9 @@ static __device__ __align__(256) unsigned char g_noalloc_scratch[kNoallocScratch
 
 // Device address of g_noalloc_scratch per device, looked up once (host code
 // must not pass the symbol itself: on the host it only stands in for the
-// device object).
-static void *g_noalloc_addr[64] = {nullptr};
+// device object).  Atomic so that host threads making their first call on
+// the same device at the same time do not race (both store the same value).
+static std::atomic<void *> g_noalloc_addr[64];
 
 struct PassTable {        // twiddle layout of the FFT passes (fft_core.cuh)
   int npass, full;
@@ -74,8 +76,12 @@ __global__ void k_noalloc_setup(int nlat, int nlon, PassTable pt, double *mu, do
 }
 
 // F_m(+-mu_j) = S_0 +- S_1 with S_p = sum_{n-m = p mod 2} c_n^m P_n^m(mu_j),
-// P_n^m by the normalised three-term recurrence (no scaling needed for
-// T <= 127 on Gaussian grids: the smallest sectoral value stays above 1e-250).
+// P_n^m by the normalised three-term recurrence without rescaling.  For
+// T <= 127 on grids with nlat up to a few times T, the sectoral start
+// P_m^m(mu_j) stays in the normal double range; on much finer grids it can
+// underflow to 0 at the latitudes nearest the poles (e.g. P_127^127 ~ 1e-370
+// at the first root when nlat ~ 2000), where the true terms lie below 1e-300
+// of the coefficients and do not change the result.
 __global__ void k_noalloc_synth(int T, int nlat, int batch, const double *__restrict__ mu,
                                 const double2 *__restrict__ spec, double2 *__restrict__ F) {
   const int j = blockIdx.x * blockDim.x + threadIdx.x;
@@ -166,6 +172,10 @@ extern "C" int sht_inverse_noalloc(int T, int nlat, int nlon, const double *spec
     pt.full = off;
   }
   const int ntw = pt.full + nlon;
+  // the inverse longitude transform holds two padded rows per block in shared memory
+  const size_t fft_smem = 2 * (size_t)padded(nlon) * sizeof(double2);
+  if (fft_smem > (size_t)227 * 1024)
+    return fail(PFSH_EINVAL, "sht_inverse_noalloc: nlon too long for the shared-memory row transform");
   // scratch: mu [nlat/2] | twiddles [nlon] | F [T+1][nlat][batch], each 256-byte aligned
   auto up = [](size_t v) { return (v + 255) & ~(size_t)255; };
   const size_t o_tw = up((size_t)(nlat / 2) * sizeof(double));
@@ -177,13 +187,13 @@ extern "C" int sht_inverse_noalloc(int T, int nlat, int nlon, const double *spec
   int dev = 0;
   PFSH_CUDA(cudaGetDevice(&dev));
   if (dev < 0 || dev >= 64) return fail(PFSH_EUNSUPPORTED, "sht_inverse_noalloc: device index");
-  if (!g_noalloc_addr[dev]) {
-    void *ptr = nullptr;
-    cudaError_t e = cudaGetSymbolAddress(&ptr, g_noalloc_scratch);
+  void *addr = g_noalloc_addr[dev].load(std::memory_order_acquire);
+  if (!addr) {
+    cudaError_t e = cudaGetSymbolAddress(&addr, g_noalloc_scratch);
     if (e != cudaSuccess) return cuda_fail(e, "sht_inverse_noalloc: cudaGetSymbolAddress");
-    g_noalloc_addr[dev] = ptr;
+    g_noalloc_addr[dev].store(addr, std::memory_order_release);
   }
-  unsigned char *base = (unsigned char *)g_noalloc_addr[dev];
+  unsigned char *base = (unsigned char *)addr;
   double *mu = (double *)base;
   double2 *tw = (double2 *)(base + o_tw);
   double2 *F = (double2 *)(base + o_F);

@@ -38,3 +38,16 @@ def test_argument_errors_are_reported_without_a_gpu():
         ps.sht_plan_create(31, 47, 96, 5, "fp64")   # odd nlat
     with pytest.raises(ps.PfshError):
         ps.sht_plan_create(31, 48, 62, 5, "fp64")   # nlon <= 2(T+1)
+
+
+def test_noalloc_binding_rejects_a_ragged_spectrum_before_the_library():
+    """A spectrum whose size is not a whole number of ncoef(T) fields is an
+    error in the binding (it would otherwise be truncated silently)."""
+    ensure_built()
+    import paper_1904_05988_gb300 as ps
+    import pytest
+    import torch
+    spec = torch.zeros(ps.ncoef(31) + 1, dtype=torch.complex128)
+    grid = torch.zeros((1, 48, 96), dtype=torch.float64)
+    with pytest.raises(ValueError):
+        ps.sht_inverse_noalloc(31, 48, 96, spec, grid)

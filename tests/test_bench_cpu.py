@@ -17,7 +17,8 @@ def test_fp64_bound_entry_uses_the_work_model_and_the_fp64_peak():
     # 32 slices x 3 fields x ncoef(255) x 2 (M+1)(3M+1) flops with M = 4
     assert work == 32 * 3 * 32896 * 2 * 5 * 13
     e = bench.roofline_entry("k_sdc_old", 4, 0.84, "bf16x3", 2)
-    assert e["bound"] == "alu" and e["peak"] == bench.FP64_PEAK_TFLOPS and e["unit"] == "TFLOP/s"
+    assert e["bound"] == "alu" and e["peak"] == bench.ALU_PEAKS["fp64"][0] and e["unit"] == "TFLOP/s"
+    assert e["peak_source"] == bench.ALU_PEAKS["fp64"][1]
     assert abs(e["achieved"] - work * 2 / 0.84e-3 / 1e12) < 1e-12
     assert abs(e["frac"] - e["achieved"] / e["peak"]) < 1e-15
     assert e["mean_launch_ms"] == pytest.approx(0.21)
@@ -46,3 +47,21 @@ def test_cores_used_is_cpu_time_over_wall_time():
     assert bench.cores_used(10.0, 5.0) == 2
     assert bench.cores_used(0.2, 5.0) == 1
     assert bench.job_value(30.0, 2, 10) == pytest.approx(2 * 10 / 0.030)
+
+
+def test_both_arms_print_the_same_metric_and_unit():
+    """The reference arm and the GPU arm share METRIC/UNIT, so the two lines
+    can be compared."""
+    src = open(os.path.join(ROOT, "bench.py")).read()
+    assert src.count('"metric": METRIC') == 2
+    assert '"unit": UNIT' in src
+
+
+def test_proc_cpu_seconds_counts_this_process():
+    import time
+    t0 = bench.proc_cpu_seconds([os.getpid()])
+    x = 0
+    end = time.process_time() + 0.3
+    while time.process_time() < end:
+        x += 1
+    assert bench.proc_cpu_seconds([os.getpid()]) - t0 > 0.1

@@ -56,3 +56,29 @@ def test_noalloc_refuses_requests_beyond_its_scratch():
     assert e.value.code == ps.PFSH_EINVAL
     with pytest.raises(ps.PfshError):
         ps.sht_inverse_noalloc(255, 384, 768, spec[:1], grid[:1])
+
+
+def test_noalloc_synthesis_matches_oracle():
+    """The allocation-free synthesis against the oracle's definition of the
+    synthesis (Section 3), not only against the plan path."""
+    from oracle.sht import SHT, unpack
+    T = 42
+    nlat, nlon = syn.gaussian_grid_size(T)
+    spec = syn.random_spectrum(T, (2,), seed=73, nmin=0)
+    got = torch.empty((2, nlat, nlon), dtype=torch.float64, device=DEV)
+    ps.sht_inverse_noalloc(T, nlat, nlon, torch.tensor(spec, dtype=torch.complex128, device=DEV), got)
+    ps.pfsh_sync_status()
+    ref = SHT(T, nlat, nlon).synthesis(unpack(spec, T))
+    err = float(np.linalg.norm(got.cpu().numpy() - ref) / np.linalg.norm(ref))
+    assert err < TOL, err
+
+
+def test_noalloc_refuses_rows_too_long_for_shared_memory():
+    """An nlon whose row transform needs more than 227 KiB of shared memory is
+    refused before any work is queued, although its scratch would fit."""
+    spec = torch.zeros((1, syn.ncoef(1)), dtype=torch.complex128, device=DEV)
+    nlon = 2 ** 13                                   # 2 * 8705 * 16 B > 227 KiB
+    grid = torch.zeros((1, 4, nlon), dtype=torch.float64, device=DEV)
+    with pytest.raises(ps.PfshError) as e:
+        ps.sht_inverse_noalloc(1, 4, nlon, spec, grid)
+    assert e.value.code == ps.PFSH_EINVAL
