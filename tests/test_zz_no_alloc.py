@@ -54,8 +54,10 @@ def test_noalloc_refuses_requests_beyond_its_scratch():
     with pytest.raises(ps.PfshError) as e:
         ps.sht_inverse_noalloc(T, nlat, nlon, spec, grid)
     assert e.value.code == ps.PFSH_EINVAL
-    with pytest.raises(ps.PfshError):
-        ps.sht_inverse_noalloc(255, 384, 768, spec[:1], grid[:1])
+    spec255 = torch.zeros((1, syn.ncoef(255)), dtype=torch.complex128, device=DEV)
+    grid255 = torch.zeros((1, 384, 768), dtype=torch.float64, device=DEV)
+    with pytest.raises(ps.PfshError):                # T above the on-the-fly limit of 127
+        ps.sht_inverse_noalloc(255, 384, 768, spec255, grid255)
 
 
 def test_noalloc_synthesis_matches_oracle():
