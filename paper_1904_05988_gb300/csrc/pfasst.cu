@@ -42,7 +42,10 @@ __device__ __forceinline__ int tri_m2(int idx, int T) {
 
 // tau_c[i] = dt D( sum_k Rt[i][k] sum_j Qf[k][j] F_f,j ) - dt sum_j Qc[i][j] F_c,j
 // (FAS correction of Eq. tau_term_level_l+1 with tau_f = 0; the Theta terms
-// of A_c(R Theta_f) - R A_f(Theta_f) cancel.)
+// of A_c(R Theta_f) - R A_f(Theta_f) cancel.)  MF, MC bound the node counts
+// at compile time (nf <= MF, ncn <= MC) so that the per-node values stay in
+// registers.
+template <int MF, int MC>
 __global__ void k_fas(int Tf, int Tc, int nts, int nf, int ncn, double dt, Mat16 RQf, Mat16 Qc,
                       const double2 *__restrict__ fe_f, const double2 *__restrict__ fi_f,
                       const double2 *__restrict__ fe_c, const double2 *__restrict__ fi_c,
@@ -57,27 +60,39 @@ __global__ void k_fas(int Tf, int Tc, int nts, int nf, int ncn, double dt, Mat16
   for (int f = 0; f < 3; ++f) {
     const size_t fo = (size_t)b * 3 * ncf + (size_t)f * ncf + fidx;
     const size_t co = (size_t)b * 3 * ncc + (size_t)f * ncc + idx;
-    double2 Ff[16], Fc[16];
-    for (int k = 0; k < nf; ++k) Ff[k] = fe_f[k * fs + fo] + fi_f[k * fs + fo];
-    for (int k = 0; k < ncn; ++k) Fc[k] = fe_c[k * cs + co] + fi_c[k * cs + co];
-    for (int i = 0; i < ncn; ++i) {
+    double2 Ff[MF], Fc[MC];
+#pragma unroll
+    for (int k = 0; k < MF; ++k)
+      if (k < nf) Ff[k] = fe_f[k * fs + fo] + fi_f[k * fs + fo];
+#pragma unroll
+    for (int k = 0; k < MC; ++k)
+      if (k < ncn) Fc[k] = fe_c[k * cs + co] + fi_c[k * cs + co];
+#pragma unroll
+    for (int i = 0; i < MC; ++i) {
+      if (i >= ncn) break;
       double2 a = make_double2(0.0, 0.0);
-      for (int k = 0; k < nf; ++k) {
-        a.x += RQf.v[i][k] * Ff[k].x;
-        a.y += RQf.v[i][k] * Ff[k].y;
-      }
+#pragma unroll
+      for (int k = 0; k < MF; ++k)
+        if (k < nf) {
+          a.x += RQf.v[i][k] * Ff[k].x;
+          a.y += RQf.v[i][k] * Ff[k].y;
+        }
       double2 c = make_double2(0.0, 0.0);
-      for (int k = 0; k < ncn; ++k) {
-        c.x += Qc.v[i][k] * Fc[k].x;
-        c.y += Qc.v[i][k] * Fc[k].y;
-      }
+#pragma unroll
+      for (int k = 0; k < MC; ++k)
+        if (k < ncn) {
+          c.x += Qc.v[i][k] * Fc[k].x;
+          c.y += Qc.v[i][k] * Fc[k].y;
+        }
       tau[i * cs + co] = make_double2(dt * a.x - dt * c.x, dt * a.y - dt * c.y);
     }
   }
 }
 
 // x_f[k] += sum_i Pt[k][i] Z(x_c[i] - x_cs[i]) for fine nodes k >= kmin and
-// the coefficients the coarse level holds (zero-padding elsewhere).
+// the coefficients the coarse level holds (zero-padding elsewhere); node
+// counts bounded at compile time as in k_fas.
+template <int MF, int MC>
 __global__ void k_interp_inc(int Tf, int Tc, int nts, int nf, int ncn, int kmin, Mat16 Pt,
                              const double2 *__restrict__ xc, const double2 *__restrict__ xcs,
                              double2 *__restrict__ xf) {
@@ -91,14 +106,21 @@ __global__ void k_interp_inc(int Tf, int Tc, int nts, int nf, int ncn, int kmin,
   for (int f = 0; f < 3; ++f) {
     const size_t fo = (size_t)b * 3 * ncf + (size_t)f * ncf + fidx;
     const size_t co = (size_t)b * 3 * ncc + (size_t)f * ncc + idx;
-    double2 d[16];
-    for (int i = 0; i < ncn; ++i) d[i] = xc[i * cs + co] - xcs[i * cs + co];
-    for (int k = kmin; k < nf; ++k) {
+    double2 d[MC];
+#pragma unroll
+    for (int i = 0; i < MC; ++i)
+      if (i < ncn) d[i] = xc[i * cs + co] - xcs[i * cs + co];
+#pragma unroll
+    for (int k = 0; k < MF; ++k) {
+      if (k >= nf) break;
+      if (k < kmin) continue;
       double2 a = make_double2(0.0, 0.0);
-      for (int i = 0; i < ncn; ++i) {
-        a.x += Pt.v[k][i] * d[i].x;
-        a.y += Pt.v[k][i] * d[i].y;
-      }
+#pragma unroll
+      for (int i = 0; i < MC; ++i)
+        if (i < ncn) {
+          a.x += Pt.v[k][i] * d[i].x;
+          a.y += Pt.v[k][i] * d[i].y;
+        }
       double2 v = xf[k * fs + fo];
       xf[k * fs + fo] = v + a;
     }
@@ -158,6 +180,7 @@ __global__ void k_broadcast(size_t n2, int nts, const double2 *__restrict__ base
 }
 
 // Predictor: x_f[k][b] = theta0 + sum_i Pt[k][i] Z(x_c[i][b] - base_c[b])
+template <int MF, int MC>
 __global__ void k_pred_interp(int Tf, int Tc, int nts, int nf, int ncn, Mat16 Pt, const double2 *__restrict__ th0,
                               const double2 *__restrict__ xc, const double2 *__restrict__ basec,
                               double2 *__restrict__ xf) {
@@ -172,20 +195,26 @@ __global__ void k_pred_interp(int Tf, int Tc, int nts, int nf, int ncn, Mat16 Pt
   const int cidx = low ? poff(Tc, m) + (n - m) : 0;
   for (int f = 0; f < 3; ++f) {
     const double2 base = th0[(size_t)f * ncf + idx];
-    double2 d[16];
+    double2 d[MC];
     if (low) {
       const size_t co = (size_t)b * 3 * ncc + (size_t)f * ncc + cidx;
       const double2 bc = basec[(size_t)b * 3 * ncc + (size_t)f * ncc + cidx];
-      for (int i = 0; i < ncn; ++i) d[i] = xc[i * cs + co] - bc;
+#pragma unroll
+      for (int i = 0; i < MC; ++i)
+        if (i < ncn) d[i] = xc[i * cs + co] - bc;
     }
-    for (int k = 0; k < nf; ++k) {
+#pragma unroll
+    for (int k = 0; k < MF; ++k) {
+      if (k >= nf) break;
       double2 v = base;
       if (low) {
         double2 a = make_double2(0.0, 0.0);
-        for (int i = 0; i < ncn; ++i) {
-          a.x += Pt.v[k][i] * d[i].x;
-          a.y += Pt.v[k][i] * d[i].y;
-        }
+#pragma unroll
+        for (int i = 0; i < MC; ++i)
+          if (i < ncn) {
+            a.x += Pt.v[k][i] * d[i].x;
+            a.y += Pt.v[k][i] * d[i].y;
+          }
         v = v + a;
       }
       xf[k * fs + (size_t)b * 3 * ncf + (size_t)f * ncf + idx] = v;
@@ -386,7 +415,8 @@ static int predict_body(pfasst *pf, cudaStream_t s) {
   dim3 g((ncoef_of(pf->cfg.Tf) + 255) / 256, nts);
   {
     PFSH_LAUNCH("k_pred_interp", s);
-    k_pred_interp<<<g, 256, 0, s>>>(pf->cfg.Tf, pf->cfg.Tc, nts, Mf + 1, Mc + 1, P, (const double2 *)pf->theta0,
+    auto kern = (Mf + 1 == 5 && Mc + 1 == 3) ? k_pred_interp<5, 3> : k_pred_interp<9, 9>;
+    kern<<<g, 256, 0, s>>>(pf->cfg.Tf, pf->cfg.Tc, nts, Mf + 1, Mc + 1, P, (const double2 *)pf->theta0,
                                     (const double2 *)pf->th_c, (const double2 *)pf->base_c, (double2 *)pf->th_f);
   }
   PFSH_CHECK_LAUNCH("k_pred_interp");
@@ -440,7 +470,8 @@ static int steps_AB(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
   dim3 g((ncoef_of(c.Tc) + 255) / 256, cnt);
   {
     PFSH_LAUNCH("k_fas", s);
-    k_fas<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, c.dt, RQf, Qc, (const double2 *)(pf->fe_f + g0 * sf),
+    auto kern = (Mf + 1 == 5 && Mc + 1 == 3) ? k_fas<5, 3> : k_fas<9, 9>;
+    kern<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, c.dt, RQf, Qc, (const double2 *)(pf->fe_f + g0 * sf),
                             (const double2 *)(pf->fi_f + g0 * sf), (const double2 *)(pf->fe_c + g0 * sc),
                             (const double2 *)(pf->fi_c + g0 * sc), (double2 *)(pf->tau + g0 * sc));
   }
@@ -472,7 +503,8 @@ static int step_D(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
   for (int q = 0; q < 3; ++q) {
     {
       PFSH_LAUNCH("k_interp_inc", s);
-      k_interp_inc<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, 1, P, (const double2 *)(xc[q] + g0 * sc),
+      auto kern = (Mf + 1 == 5 && Mc + 1 == 3) ? k_interp_inc<5, 3> : k_interp_inc<9, 9>;
+      kern<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, 1, P, (const double2 *)(xc[q] + g0 * sc),
                                      (const double2 *)(xs[q] + g0 * sc), (double2 *)(xf[q] + g0 * sf));
     }
     PFSH_CHECK_LAUNCH("k_interp_inc");

@@ -362,8 +362,10 @@ extern "C" int sht_plan_create(sht_plan **out, int T, int nlat, int nlon, int ma
   // workspace: X [ne][cols], F [T+1][nlat][cols], H [T+1][2][nh][cols], Y [ne][cols]
   const size_t cols = (size_t)max_batch;
   const size_t celem = prec == PFSH_FP64 ? 16 : 8;
-  const size_t bX = (size_t)p->ne * cols * celem;
-  const size_t bF = (size_t)(T + 1) * nlat * cols * celem;
+  // each region starts on a 256-byte boundary (bulk copies read 16-byte aligned rows)
+  auto up256 = [](size_t b) { return (b + 255) & ~(size_t)255; };
+  const size_t bX = up256((size_t)p->ne * cols * celem);
+  const size_t bF = up256((size_t)(T + 1) * nlat * cols * celem);
   const size_t bH = bF;
   const size_t bY = bX;
   p->ws_bytes = bX + bF + bH + bY;
