@@ -14,14 +14,10 @@
 // (see tc.cuh).  The Legendre table side (B operand) is stored in global
 // memory as ready-made shared-memory images, one per (m, row tile, parity,
 // K chunk of <= 64), bf16 hi followed by bf16 lo, and is fetched with one
-// bulk TMA copy per chunk.  The activation side (A operand) arrives as fp32
-// rows: when the rows are 16-byte aligned (an even number of real columns per
-// 4), warp 0 fetches the rows of chunk q+R with bulk copies into a ring of R
-// raw fp32 buffers while chunk q is processed, so the eight warps convert
-// from shared memory with the data already there; otherwise the warps load
-// the rows themselves (column pairs, float2).  Either way the values are
-// split into bf16 hi/lo and stored in the canonical layout, and two stages
-// overlap the conversion of chunk q+1 with the MMAs of chunk q.  One thread issues the MMAs;
+// bulk TMA copy per chunk; the activation side (A operand) is read as fp32
+// (column pairs, float2) by the eight warps of the CTA, split into bf16
+// hi/lo and stored to shared memory.  Two stages overlap the conversion of
+// chunk q+1 with the MMAs of chunk q.  One thread issues the MMAs;
 // accumulators for both parities live in TMEM (2 x N <= 512 columns) and are
 // drained by both warpgroups (a warp reads the 32 TMEM lanes of its quadrant,
 // the two warpgroups take alternate 16-column groups).  Every wait is
@@ -54,13 +50,11 @@ constexpr int NTHREADS = 256;
 // spill at 128): a CTA then leaves room in the register file for a coarse-
 // chain block on the same SM, so the Step B transforms overlap the chain
 // better (measured: 197 -> 202 iterations/s, 3xBF16, T255/T127, 32 slices).
-constexpr uint32_t RAW_BYTES = KC * MROWS * 4;   // one raw fp32 activation chunk
-
-template <bool X3, bool FP16, bool ANALYSIS, bool BULK>
+template <bool X3, bool FP16, bool ANALYSIS>
 __global__ void __launch_bounds__(NTHREADS, 2)
     k_legendre_tc(int T, int nlat, int cols_real, int ntiles, const float *__restrict__ act,
                   const uint8_t *__restrict__ img, const TcChunk *__restrict__ chunks,
-                  const TcWork *__restrict__ work, int Nmax, int nraw, float *__restrict__ out, int *status) {
+                  const TcWork *__restrict__ work, int Nmax, float *__restrict__ out, int *status) {
   extern __shared__ __align__(1024) uint8_t smem_raw[];
   uint8_t *smem = (uint8_t *)(((uintptr_t)smem_raw + 1023) & ~(uintptr_t)1023);
   const int nh = nlat / 2;
@@ -73,13 +67,11 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   const uint32_t a_bytes = a_half * (X3 ? 2 : 1);
   const uint32_t b_half_max = (uint32_t)Nmax * KC * 2;
   const uint32_t b_bytes = b_half_max * (X3 ? 2 : 1);
-  // operand stages s = 0, 1: A image then B image (address arithmetic, no local array)
-  auto stA = [&](int st) { return smem + (size_t)st * (a_bytes + b_bytes); };
-  auto stB = [&](int st) { return smem + (size_t)st * (a_bytes + b_bytes) + a_bytes; };
-  float *raw = (float *)(smem + 2 * (a_bytes + b_bytes));             // BULK: [nraw][KC][MROWS]
-  uint64_t *bars = (uint64_t *)(smem + 2 * (a_bytes + b_bytes) + (BULK ? (size_t)nraw * RAW_BYTES : 0));
-  uint64_t *full = bars, *done = bars + 2, *fin = bars + 4, *rawbar = bars + 5;   // rawbar[nraw]
-  uint32_t *tmem_slot = (uint32_t *)(bars + 5 + (BULK ? nraw : 0));
+  uint8_t *stA[2] = {smem, smem + a_bytes + b_bytes};
+  uint8_t *stB[2] = {smem + a_bytes, smem + 2 * a_bytes + b_bytes};
+  uint64_t *bars = (uint64_t *)(smem + 2 * (a_bytes + b_bytes));
+  uint64_t *full = bars, *done = bars + 2, *fin = bars + 4;
+  uint32_t *tmem_slot = (uint32_t *)(bars + 5);
 
   uint32_t ncols = 32;
   while (ncols < (uint32_t)(2 * N)) ncols <<= 1;
@@ -89,8 +81,6 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     tc::mbar_init(&done[0], 1);
     tc::mbar_init(&done[1], 1);
     tc::mbar_init(fin, 1);
-    if (BULK)
-      for (int r = 0; r < nraw; ++r) tc::mbar_init(&rawbar[r], 1);
     tc::mbar_fence_init();
   }
   if (warp == 0) tc::tmem_alloc(tmem_slot, ncols);
@@ -101,30 +91,6 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   bool ok = true;
   const int m_len = T + 2 - m;          // degrees n = m .. T+1
   const size_t eo = (size_t)eoff(T, m);
-  const int ncolv = cols_real - cb * MROWS;   // real columns of this block present in the rows (> 0)
-
-  // rows of chunk ch that exist (k < nh for the analysis, n - m < m_len for
-  // the synthesis); the others are zero
-  auto valid_rows = [&](const TcChunk &ch) {
-    const int lim = ANALYSIS ? nh : (m_len - ch.p + 1) / 2;
-    return max(0, min(ch.klen, lim - ch.kstart));
-  };
-  // BULK: warp 0 fetches the rows of chunk q (16-byte aligned, ncolv real
-  // columns each) into raw slot q % nraw, completion on rawbar[q % nraw]
-  auto issue_raw = [&](int q) {
-    if (q >= wk.nchunks) return;
-    const TcChunk ch = chunks[wk.first + q];
-    const int slot = q % nraw, nv = valid_rows(ch);
-    const uint32_t rowb = (uint32_t)min(MROWS, ncolv) * 4u;
-    const int lane = tid & 31;
-    if (lane == 0) tc::mbar_arrive_expect_tx(&rawbar[slot], rowb * (uint32_t)nv);
-    __syncwarp();
-    float *dst = raw + (size_t)slot * (KC * MROWS);
-    for (int r = lane; r < nv; r += 32) {
-      const size_t row = ANALYSIS ? ((size_t)m * 2 + ch.p) * nh + ch.kstart + r : eo + 2 * (ch.kstart + r) + ch.p;
-      tc::bulk_g2s(dst + (size_t)r * MROWS, act + row * cols_real + (size_t)cb * MROWS, rowb, &rawbar[slot]);
-    }
-  };
 
   // activation items of one chunk (two adjacent columns x 8 consecutive K,
   // loaded as float2) into registers; zeros outside the tile
@@ -162,9 +128,9 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     if (tid == 0) {
       const uint32_t bytes = b_half * (X3 ? 2 : 1);
       tc::mbar_arrive_expect_tx(&full[s], bytes);
-      tc::bulk_g2s(stB(s), img + ch.off, bytes, &full[s]);
+      tc::bulk_g2s(stB[s], img + ch.off, bytes, &full[s]);
     }
-    uint8_t *Ahi = stA(s), *Alo = stA(s) + a_half;
+    uint8_t *Ahi = stA[s], *Alo = stA[s] + a_half;
     const int nit = (MROWS / 2) * (KL >> 3);
 #pragma unroll
     for (int uu = 0; uu < MAXIT; ++uu) {
@@ -198,7 +164,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       const uint32_t idesc = tc::make_idesc(MROWS, N, FP16);
       const uint32_t sbo = 16u * KL;
       const uint32_t a0 = tc::smem_u32(Ahi), a1 = tc::smem_u32(Alo);
-      const uint32_t b0 = tc::smem_u32(stB(s)), b1 = b0 + b_half;
+      const uint32_t b0 = tc::smem_u32(stB[s]), b1 = b0 + b_half;
       const uint32_t d = tmem + (uint32_t)(ch.p * N);
       for (int ks = 0; ks < KL / 16; ++ks) {
         const uint32_t acc = (ch.kstart == 0 && ks == 0) ? 0u : 1u;
@@ -215,76 +181,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       tc::mma_commit(&done[s]);
     }
   };
-  if constexpr (BULK) {
-    if (warp == 0)
-      for (int q = 0; q < nraw; ++q) issue_raw(q);
-    for (int q = 0; q < wk.nchunks; ++q) {
-      const TcChunk ch = chunks[wk.first + q];
-      const int s = q & 1, u = q >> 1;
-      if (q >= 2) ok &= tc::mbar_wait(&done[s], (u - 1) & 1);
-      const int KL = ch.klen;
-      const uint32_t b_half = (uint32_t)N * KL * 2;
-      if (tid == 0) {
-        const uint32_t bytes = b_half * (X3 ? 2 : 1);
-        tc::mbar_arrive_expect_tx(&full[s], bytes);
-        tc::bulk_g2s(stB(s), img + ch.off, bytes, &full[s]);
-      }
-      const int slot = q % nraw, nv = valid_rows(ch);
-      ok &= tc::mbar_wait(&rawbar[slot], (uint32_t)(q / nraw) & 1);
-      const float *rs = raw + (size_t)slot * (KC * MROWS);
-      uint8_t *Ahi = stA(s), *Alo = stA(s) + a_half;
-      for (int it = tid; it < (MROWS / 2) * (KL >> 3); it += NTHREADS) {
-        const int rp = it & (MROWS / 2 - 1), g = it >> 6;
-        const int r = 2 * rp;
-        uint16_t h0[8], l0[8], h1[8], l1[8];
-  #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          const int kl = g * 8 + i;
-          float2 v = make_float2(0.f, 0.f);
-          if (kl < nv && r < ncolv) v = *(const float2 *)(rs + (size_t)kl * MROWS + r);
-          tc::split2<FP16>(v.x, h0[i], l0[i]);
-          tc::split2<FP16>(v.y, h1[i], l1[i]);
-        }
-        const uint32_t off0 = tc::tile_offset(r, g * 8, KL), off1 = tc::tile_offset(r + 1, g * 8, KL);
-        *(uint4 *)(Ahi + off0) = make_uint4(h0[0] | (uint32_t)h0[1] << 16, h0[2] | (uint32_t)h0[3] << 16,
-                                            h0[4] | (uint32_t)h0[5] << 16, h0[6] | (uint32_t)h0[7] << 16);
-        *(uint4 *)(Ahi + off1) = make_uint4(h1[0] | (uint32_t)h1[1] << 16, h1[2] | (uint32_t)h1[3] << 16,
-                                            h1[4] | (uint32_t)h1[5] << 16, h1[6] | (uint32_t)h1[7] << 16);
-        if (X3) {
-          *(uint4 *)(Alo + off0) = make_uint4(l0[0] | (uint32_t)l0[1] << 16, l0[2] | (uint32_t)l0[3] << 16,
-                                              l0[4] | (uint32_t)l0[5] << 16, l0[6] | (uint32_t)l0[7] << 16);
-          *(uint4 *)(Alo + off1) = make_uint4(l1[0] | (uint32_t)l1[1] << 16, l1[2] | (uint32_t)l1[3] << 16,
-                                              l1[4] | (uint32_t)l1[5] << 16, l1[6] | (uint32_t)l1[7] << 16);
-        }
-      }
-      tc::fence_proxy_async();
-      __syncthreads();
-      // every thread has read raw slot `slot`: refill it with chunk q + nraw
-      if (warp == 0) issue_raw(q + nraw);
-      if (tid == 0) {
-        ok &= tc::mbar_wait(&full[s], u & 1);
-        tc::fence_after_sync();
-        const uint32_t idesc = tc::make_idesc(MROWS, N, FP16);
-        const uint32_t sbo = 16u * KL;
-        const uint32_t a0 = tc::smem_u32(Ahi), a1 = tc::smem_u32(Alo);
-        const uint32_t b0 = tc::smem_u32(stB(s)), b1 = b0 + b_half;
-        const uint32_t d = tmem + (uint32_t)(ch.p * N);
-        for (int ks = 0; ks < KL / 16; ++ks) {
-          const uint32_t acc = (ch.kstart == 0 && ks == 0) ? 0u : 1u;
-          const uint64_t ah = tc::make_desc(a0 + ks * 256, 128, sbo);
-          const uint64_t bh = tc::make_desc(b0 + ks * 256, 128, sbo);
-          tc::mma_f16(d, ah, bh, idesc, acc);
-          if (X3) {
-            const uint64_t al = tc::make_desc(a1 + ks * 256, 128, sbo);
-            const uint64_t bl = tc::make_desc(b1 + ks * 256, 128, sbo);
-            tc::mma_f16(d, ah, bl, idesc, 1u);
-            tc::mma_f16(d, al, bh, idesc, 1u);
-          }
-        }
-        tc::mma_commit(&done[s]);
-      }
-    }
-  } else if constexpr (ANALYSIS) {
+  if constexpr (ANALYSIS) {
     // analysis (K = latitudes, six chunks per CTA at T255): two register
     // sets, the loads of chunk q+1 in flight while chunk q is converted and
     // multiplied (unrolled by two so that both sets stay in registers)
@@ -311,11 +208,11 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       if (tid == 0) {
         const uint32_t bytes = b_half * (X3 ? 2 : 1);
         tc::mbar_arrive_expect_tx(&full[s], bytes);
-        tc::bulk_g2s(stB(s), img + ch.off, bytes, &full[s]);
+        tc::bulk_g2s(stB[s], img + ch.off, bytes, &full[s]);
       }
       // produce the activation chunk: rows = 128 real columns, K = KL; one
       // item = two adjacent columns x 8 consecutive K, loaded as float2
-      uint8_t *Ahi = stA(s), *Alo = stA(s) + a_half;
+      uint8_t *Ahi = stA[s], *Alo = stA[s] + a_half;
       const int groups = KL >> 3;
       for (int it = tid; it < (MROWS / 2) * groups; it += NTHREADS) {
         const int rp = it & (MROWS / 2 - 1), g = it >> 6;
@@ -360,7 +257,7 @@ __global__ void __launch_bounds__(NTHREADS, 2)
         const uint32_t idesc = tc::make_idesc(MROWS, N, FP16);
         const uint32_t sbo = 16u * KL;
         const uint32_t a0 = tc::smem_u32(Ahi), a1 = tc::smem_u32(Alo);
-        const uint32_t b0 = tc::smem_u32(stB(s)), b1 = b0 + b_half;
+        const uint32_t b0 = tc::smem_u32(stB[s]), b1 = b0 + b_half;
         const uint32_t d = tmem + (uint32_t)(ch.p * N);
         for (int ks = 0; ks < KL / 16; ++ks) {
           const uint32_t acc = (ch.kstart == 0 && ks == 0) ? 0u : 1u;
@@ -512,20 +409,10 @@ int set_smem_attr(K kernel, size_t bytes) {
   return ensure_smem((const void *)kernel, bytes);
 }
 
-constexpr size_t kSmemLimit = 227 * 1024;
-constexpr int kMaxRaw = 3;
-
-size_t tc_smem_bytes(int Nmax, bool x3, int nraw) {
+size_t tc_smem_bytes(int Nmax, bool x3) {
   const size_t a = (size_t)MROWS * KC * 2 * (x3 ? 2 : 1);
   const size_t b = (size_t)Nmax * KC * 2 * (x3 ? 2 : 1);
-  return 2 * (a + b) + (size_t)nraw * RAW_BYTES + 8 * (5 + nraw) + 8 + 1024;
-}
-
-// raw activation slots that fit beside the operand stages (0: none fit)
-int tc_raw_slots(int Nmax, bool x3) {
-  int r = kMaxRaw;
-  while (r > 0 && tc_smem_bytes(Nmax, x3, r) > kSmemLimit) --r;
-  return r;
+  return 2 * (a + b) + 64 + 1024;
 }
 
 }  // namespace
@@ -721,17 +608,15 @@ template <bool X3, bool FP16, bool AN>
 static int launch_tc(const sht_plan *p, const TcDir &d, int cols, const float *act, float *out, cudaStream_t s,
                      const char *name) {
   const int cols_real = 2 * cols;
-  // bulk-copied activation rows need 16-byte aligned rows and a raw slot that fits
-  const int nraw = (cols_real % 4 == 0 && ((uintptr_t)act & 15) == 0) ? tc_raw_slots(d.Nmax, X3) : 0;
-  const size_t smem = tc_smem_bytes(d.Nmax, X3, nraw);
-  auto kern = nraw > 0 ? k_legendre_tc<X3, FP16, AN, true> : k_legendre_tc<X3, FP16, AN, false>;
+  const size_t smem = tc_smem_bytes(d.Nmax, X3);
+  auto kern = k_legendre_tc<X3, FP16, AN>;
   int rc = set_smem_attr(kern, smem);
   if (rc) return rc;
   dim3 g((cols_real + MROWS - 1) / MROWS, d.ntiles, p->T + 1);
   {
     PFSH_LAUNCH(name, s);
-    kern<<<g, NTHREADS, smem, s>>>(p->T, p->nlat, cols_real, d.ntiles, act, d.img, d.chunks, d.work, d.Nmax, nraw,
-                                   out, device_status());
+    kern<<<g, NTHREADS, smem, s>>>(p->T, p->nlat, cols_real, d.ntiles, act, d.img, d.chunks, d.work, d.Nmax, out,
+                              device_status());
   }
   PFSH_CHECK_LAUNCH(name);
   return PFSH_OK;
