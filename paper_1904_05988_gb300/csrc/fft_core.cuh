@@ -140,6 +140,18 @@ template <int R, typename C> __device__ __forceinline__ void butterfly(C *v, boo
   }
 }
 
+// The five products of the grid stage at one point (packed north/south rows).
+template <typename C, typename Rl>
+__device__ __forceinline__ void grid_products(const C &eta, const C &php, const C &U, const C &V, Rl inv, Rl h,
+                                              C (&o)[5]) {
+  const Rl Ui = U.x * inv, Us = U.y * inv, Vi = V.x * inv, Vs = V.y * inv;
+  o[0] = mk<C>(eta.x * Ui, eta.y * Us);
+  o[1] = mk<C>(eta.x * Vi, eta.y * Vs);
+  o[2] = mk<C>(php.x * Ui, php.y * Us);
+  o[3] = mk<C>(php.x * Vi, php.y * Vs);
+  o[4] = mk<C>((U.x * U.x + V.x * V.x) * h, (U.y * U.y + V.y * V.y) * h);
+}
+
 // Twiddles are stored per pass: the pass with radix R after sub-transform
 // size Ns owns R*Ns entries, entry r*Ns + k = exp(-2 pi i k r / (Ns R)), so
 // the lanes of a warp (consecutive k) read consecutive entries.
@@ -170,6 +182,87 @@ __device__ __forceinline__ void pass_ct(const C *__restrict__ x, C *__restrict__
   __syncthreads();
 }
 
+// The first pass of an inverse grid-stage transform whose entries e with
+// T < e < N - T are zero: they are neither stored nor read.
+template <int R, int N, typename C>
+__device__ __forceinline__ void pass_first_pruned(const C *__restrict__ x, C *__restrict__ y, int nfft, int T) {
+  constexpr int NR = N / R;
+  const int NP = padded(N);
+  const int total = nfft * NR;
+  for (int t = threadIdx.x; t < total; t += blockDim.x) {
+    const int fi = t / NR, j = t - fi * NR;
+    const C *xs = x + fi * NP;
+    C *ys = y + fi * NP;
+    C v[R];
+#pragma unroll
+    for (int r = 0; r < R; ++r) {
+      const int e = j + r * NR;
+      v[r] = (e <= T || e >= N - T) ? xs[sidx(e)] : mk<C>(0.0, 0.0);
+    }
+    butterfly<R>(v, true);
+#pragma unroll
+    for (int q = 0; q < R; ++q) ys[sidx(j * R + q)] = v[q];
+  }
+  __syncthreads();
+}
+
+// The last pass of the 4 inverse grid-stage transforms (eta, Phi', U, V)
+// fused with the grid products: one thread takes the same butterfly of all
+// four rows (one twiddle load for the four), forms the five products at its
+// R output points and stores them as the 5 rows y of the forward transform.
+template <int R, int Ns, int N, int OFF, typename C, typename Rl>
+__device__ __forceinline__ void pass_last_products(const C *__restrict__ x, C *__restrict__ y,
+                                                   const C *__restrict__ tw, Rl inv, Rl h) {
+  constexpr int NR = N / R;
+  const int NP = padded(N);
+  for (int j = threadIdx.x; j < NR; j += blockDim.x) {
+    const int k = j % Ns, idx = (j / Ns) * (Ns * R) + k;
+    C w[R];
+#pragma unroll
+    for (int r = 1; r < R; ++r) w[r] = Ns > 1 ? twiddle(tw, OFF + r * Ns + k, true) : mk<C>(1.0, 0.0);
+    C v[4][R];
+#pragma unroll
+    for (int f = 0; f < 4; ++f) {
+#pragma unroll
+      for (int r = 0; r < R; ++r) {
+        C a = x[f * NP + sidx(j + r * NR)];
+        if (Ns > 1 && r > 0) a = cmul(a, w[r]);
+        v[f][r] = a;
+      }
+      butterfly<R>(v[f], true);
+    }
+#pragma unroll
+    for (int q = 0; q < R; ++q) {
+      C pr[5];
+      grid_products<C, Rl>(v[0][q], v[1][q], v[2][q], v[3][q], inv, h, pr);
+#pragma unroll
+      for (int p = 0; p < 5; ++p) y[p * NP + sidx(idx + q * Ns)] = pr[p];
+    }
+  }
+  __syncthreads();
+}
+
+// inverse transforms of the 4 grid-stage rows with the products fused into
+// the last pass (returns the buffer holding the 5 product rows)
+template <int N, int Ns, int OFF, int... Rs> struct PassListF;
+template <int N, int Ns, int OFF, int R> struct PassListF<N, Ns, OFF, R> {
+  template <typename C, typename Rl>
+  static __device__ __forceinline__ C *run(C *a, C *b, int, const C *tw, Rl inv, Rl h) {
+    pass_last_products<R, Ns, N, OFF>(a, b, tw, inv, h);
+    return b;
+  }
+};
+template <int N, int Ns, int OFF, int R, int R2, int... Rs> struct PassListF<N, Ns, OFF, R, R2, Rs...> {
+  template <typename C, typename Rl>
+  static __device__ __forceinline__ C *run(C *a, C *b, int T, const C *tw, Rl inv, Rl h) {
+    if constexpr (Ns == 1)
+      pass_first_pruned<R, N>(a, b, 4, T);
+    else
+      pass_ct<R, Ns, N, OFF>(a, b, 4, tw, true);
+    return PassListF<N, Ns * R, OFF + R * Ns, R2, Rs...>::run(b, a, T, tw, inv, h);
+  }
+};
+
 template <int N, int Ns, int OFF, int... Rs> struct PassList;
 template <int N, int Ns, int OFF> struct PassList<N, Ns, OFF> {
   template <typename C> static __device__ __forceinline__ C *run(C *a, C *, int, const C *, bool) { return a; }
@@ -182,7 +275,12 @@ template <int N, int Ns, int OFF, int R, int... Rs> struct PassList<N, Ns, OFF, 
 };
 
 template <int N_, int... Rs> struct ShapeCT {
+  static constexpr bool kCT = true;
   static __host__ __device__ int n(const FftArgs &) { return N_; }
+  template <typename C, typename Rl>
+  static __device__ __forceinline__ C *inverse_products(C *a, C *b, int T, const C *tw, Rl inv, Rl h) {
+    return PassListF<N_, 1, 0, Rs...>::run(a, b, T, tw, inv, h);
+  }
   template <typename C>
   static __device__ __forceinline__ C *run(const FftArgs &, C *a, C *b, int nfft, const C *tw, bool inv) {
     return PassList<N_, 1, 0, Rs...>::run(a, b, nfft, tw, inv);
@@ -191,6 +289,7 @@ template <int N_, int... Rs> struct ShapeCT {
 
 // run-time path: any length with prime factors <= 61
 struct ShapeRT {
+  static constexpr bool kCT = false;
   static __host__ __device__ int n(const FftArgs &f) { return f.N; }
   template <typename C>
   static __device__ C *run(const FftArgs &f, C *a, C *b, int nfft, const C *tw, bool inv) {
@@ -284,16 +383,32 @@ __device__ __forceinline__ void block_means(decltype(C().x) (&sx)[NF], decltype(
   __syncthreads();
 }
 
-// The five products of the grid stage at one point (packed north/south rows).
+// Hemispheric sums and differences of the 5 forward-transformed product rows
+// Z, weighted by w_j, into H[m][parity][j][b*5 + f] for m <= T (with the row
+// mean restored at wavenumber 0 when `center`).  Called by every thread.
 template <typename C, typename Rl>
-__device__ __forceinline__ void grid_products(const C &eta, const C &php, const C &U, const C &V, Rl inv, Rl h,
-                                              C (&o)[5]) {
-  const Rl Ui = U.x * inv, Us = U.y * inv, Vi = V.x * inv, Vs = V.y * inv;
-  o[0] = mk<C>(eta.x * Ui, eta.y * Us);
-  o[1] = mk<C>(eta.x * Vi, eta.y * Vs);
-  o[2] = mk<C>(php.x * Ui, php.y * Us);
-  o[3] = mk<C>(php.x * Vi, php.y * Vs);
-  o[4] = mk<C>((U.x * U.x + V.x * V.x) * h, (U.y * U.y + V.y * V.y) * h);
+__device__ __forceinline__ void grid_unpack(const C *Z, int N, int NP, int T, int j, int nlat, int colsH, int b,
+                                            const Rl *__restrict__ rowf, C *__restrict__ H, bool center) {
+  const Rl half = (Rl)0.5 / (Rl)N;
+  const Rl wj = rowf[2 * j + 1];
+  const int nh = nlat / 2;
+  for (int t = threadIdx.x; t < 5 * (T + 1); t += blockDim.x) {
+    const int m = t / 5, fld = t - 5 * m;   // consecutive threads: the 5 fields of one m
+    const C *z = Z + fld * NP;
+    C zm = z[sidx(m)];
+    C zc = cconj(z[sidx(m == 0 ? 0 : N - m)]);
+    if (center && m == 0) {                 // the row mean taken out before the transform
+      const C dc = (Rl)N * z[NP - 1];
+      zm = zm + dc;
+      zc = zc + cconj(dc);
+    }
+    C gn = half * (zm + zc);
+    C gs = half * times_i(zc - zm);
+    C he = wj * (gn + gs), ho = wj * (gn - gs);
+    H[(((size_t)m * 2 + 0) * nh + j) * colsH + b * 5 + fld] = he;
+    H[(((size_t)m * 2 + 1) * nh + j) * colsH + b * 5 + fld] = ho;
+  }
+  __syncthreads();
 }
 
 // Row means are taken out of the products before the forward transform and
@@ -326,8 +441,14 @@ __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat,
   C *Bf = A + 5 * NP;     // 5 padded transforms
   const int js = nlat - 1 - j;
   const int colsF = 4 * B, colsH = 5 * B;
-  for (int t = threadIdx.x; t < 4 * NP; t += blockDim.x) A[t] = mk<C>(0.0, 0.0);
-  __syncthreads();
+  // compile-time shapes without the row-mean removal: no zero fill (the first
+  // inverse pass never reads the wavenumbers above T) and the products fused
+  // into the last inverse pass
+  const bool fused = Shape::kCT && !center;
+  if (!fused) {
+    for (int t = threadIdx.x; t < 4 * NP; t += blockDim.x) A[t] = mk<C>(0.0, 0.0);
+    __syncthreads();
+  }
   for (int t = threadIdx.x; t < 4 * (T + 1); t += blockDim.x) {
     const int m = t >> 2, fld = t & 3;     // consecutive threads: the 4 fields of one m
     C fn = F[((size_t)m * nlat + j) * colsF + b * 4 + fld];
@@ -341,10 +462,18 @@ __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat,
     }
   }
   __syncthreads();
-  C *g = Shape::run(f, A, Bf, 4, tw, true);
-  C *o = (g == A) ? Bf : A;
   const Rl inv = rowf[2 * j];                // 1/(1 - mu_j^2)
   const Rl h = (Rl)0.5 * inv;
+  if constexpr (Shape::kCT) {
+    if (fused) {
+      C *o = Shape::inverse_products(A, Bf, T, tw, inv, h);
+      C *Z = Shape::run(f, o, (o == A) ? Bf : A, 5, tw, false);
+      grid_unpack<C, Rl>(Z, N, NP, T, j, nlat, colsH, b, rowf, H, false);
+      return;
+    }
+  }
+  C *g = Shape::run(f, A, Bf, 4, tw, true);
+  C *o = (g == A) ? Bf : A;
   C mean[5];
 #pragma unroll
   for (int q = 0; q < 5; ++q) mean[q] = mk<C>(0.0, 0.0);
@@ -379,26 +508,7 @@ __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat,
     }
   __syncthreads();
   C *Z = Shape::run(f, o, g, 5, tw, false);
-  const Rl half = (Rl)0.5 / (Rl)N;
-  const Rl wj = rowf[2 * j + 1];
-  const int nh = nlat / 2;
-  for (int t = threadIdx.x; t < 5 * (T + 1); t += blockDim.x) {
-    const int m = t / 5, fld = t - 5 * m;   // consecutive threads: the 5 fields of one m
-    const C *z = Z + fld * NP;
-    C zm = z[sidx(m)];
-    C zc = cconj(z[sidx(m == 0 ? 0 : N - m)]);
-    if (center && m == 0) {                 // the row mean taken out before the transform
-      const C dc = (Rl)N * z[NP - 1];
-      zm = zm + dc;
-      zc = zc + cconj(dc);
-    }
-    C gn = half * (zm + zc);
-    C gs = half * times_i(zc - zm);
-    C he = wj * (gn + gs), ho = wj * (gn - gs);
-    H[(((size_t)m * 2 + 0) * nh + j) * colsH + b * 5 + fld] = he;
-    H[(((size_t)m * 2 + 1) * nh + j) * colsH + b * 5 + fld] = ho;
-  }
-  __syncthreads();
+  grid_unpack<C, Rl>(Z, N, NP, T, j, nlat, colsH, b, rowf, H, center);
 }
 
 // The same grid stage for long rows (shared memory for 6 instead of 10
