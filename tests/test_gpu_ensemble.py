@@ -103,3 +103,38 @@ def test_uneven_batch_of_48_instances():
         picks.setdefault(T, i)
     for T, i in picks.items():   # one member of every truncation, including T170 (nlon 516 = 2^2 3 43)
         assert np.array_equal(together[i], run_alone(cfgs[i], states[i], 4)), T
+
+
+def test_ensemble_member_T170_matches_oracle():
+    """An ensemble member at the uneven batch's odd size, T170/T85 on 258 x 516
+    / 130 x 260 (nlon = 2^2 3 43, 2^2 5 13: the run-time FFT path and row
+    centring), beside a T63/T31 member, against the oracle: predictor and a
+    block of two iterations, end values of every slice (3xBF16: the end-value
+    bound of the mixed PFASST tests and the low-band change law of
+    tests/_lib.py).  The oracle runs its slice-independent steps on all host
+    cores."""
+    import os
+    from oracle.pfasst import PFASST
+    from oracle.pool import SlicePool
+    from oracle.sdc import SDCLevel
+    from oracle.sht import pack, unpack
+    from oracle.swe import SWEParams
+    from _lib import change_bound
+    if "bf16x3" not in ps.available_precisions():
+        pytest.skip("bf16x3 not built")
+    specs = [(170, 85, 4), (63, 31, 4)]
+    cfgs = [config(T, Tc, nts, "bf16x3") for T, Tc, nts in specs]
+    states = [initial_state(T, 60 + i) for i, (T, _, _) in enumerate(specs)]
+    got = run_ensemble(cfgs, states, 2, rounds=1)[0]
+    T, Tc, nts = specs[0]
+    p = SWEParams(a=A, omega=OM, g=G, nu=syn.NU, phibar=PHIBAR)
+    gf, gc = syn.gaussian_grid_size(T), syn.gaussian_grid_size(Tc)
+    f, c = SDCLevel(T, *gf, 5, cfgs[0].dt, p), SDCLevel(Tc, *gc, 3, cfgs[0].dt, p)
+    with SlicePool({"f": f.args, "c": c.args}, workers=min(nts, os.cpu_count() or 1)) as pool:
+        ref = PFASST(f, c, nts, pool=pool).run(unpack(states[0], T), 2)
+    st0 = states[0]
+    errs = [np.linalg.norm(got[n] - pack(ref[n], T)) / np.linalg.norm(pack(ref[n], T)) for n in range(nts)]
+    chg = np.linalg.norm((got[-1] - st0) - (pack(ref[-1], T) - st0)) / np.linalg.norm(pack(ref[-1], T) - st0)
+    print(f"\nensemble member T{T}/T{Tc} x {nts}: end values {max(errs):.2e}, change {chg:.2e}")
+    assert max(errs) < 5e-7
+    assert chg < change_bound("bf16x3", T)
