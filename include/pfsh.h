@@ -74,13 +74,18 @@ typedef enum {
  *               in the fp16 range (|x| < 65504, relative precision lost
  *               below 6e-5), which the right-hand side's flux products do
  *               not, so swe_ctx_create refuses FP16 plans (EUNSUPPORTED),
- *   PFSH_BF16X3 split bf16 hi/lo products (hi*hi + hi*lo + lo*hi), fp32 acc. */
+ *   PFSH_BF16X3 split bf16 hi/lo products (hi*hi + hi*lo + lo*hi), fp32 acc.
+ *               (each operand to about 16 bits),
+ *   PFSH_BF16X6 three-part bf16 split x = hi + mid + lo (about 24 bits, the
+ *               precision of fp32) and the six products of the parts whose
+ *               exponents sum above 2^-24, fp32 accumulation. */
 typedef enum {
   PFSH_FP64 = 0,
   PFSH_FP32 = 1,
   PFSH_BF16 = 2,
   PFSH_FP16 = 3,
-  PFSH_BF16X3 = 4
+  PFSH_BF16X3 = 4,
+  PFSH_BF16X6 = 5
 } pfsh_prec;
 
 typedef struct sht_plan sht_plan;
@@ -326,6 +331,23 @@ int pfsh_sync_status(pfsh_stream_t stream);
 
 /* Thread-local, NUL-terminated description of the last failure ("" if none). */
 const char *pfsh_last_error(void);
+
+/* on != 0: from now on swe_rhs (F_E, F_I), sdc_sweep (every node of theta),
+ * pfasst_predict, pfasst_iteration and pfasst_iterations (the fine end value
+ * of every slice) append one kernel that scans their results and records a
+ * non-finite component (NaN, +-Inf) in the status word, so that the next
+ * pfsh_sync_status returns PFSH_ENUMERIC.  Off by default (it costs one read
+ * of the results).  Process-wide; the check runs outside the CUDA graphs of
+ * the PFASST calls. */
+int pfsh_set_check_finite(int on);
+
+/* Self-test of the bounded device-side waits (no counterpart in the paper):
+ * one CTA allocates tensor memory, waits on an mbarrier that nothing arms
+ * with the poll limit `polls` (1..2^20) of the library's bounded wait, frees
+ * its tensor memory and returns; the status word then holds the timeout, so
+ * the next pfsh_sync_status returns PFSH_ETIMEOUT and the context stays
+ * usable.  Asynchronous on `stream`. */
+int pfsh_selftest_wait(unsigned polls, pfsh_stream_t stream);
 
 /* ------------------------------------------------------------------------ */
 /* Diagnostics (no counterpart in the paper)                                 */

@@ -21,8 +21,9 @@ import torch
 from .build import LIB
 
 PFSH_OK, PFSH_EINVAL, PFSH_ENOMEM, PFSH_ECUDA, PFSH_EUNSUPPORTED, PFSH_ETIMEOUT, PFSH_ENUMERIC = 0, -1, -2, -3, -4, -5, -6
-PFSH_FP64, PFSH_FP32, PFSH_BF16, PFSH_FP16, PFSH_BF16X3 = 0, 1, 2, 3, 4
-PREC_NAMES = {"fp64": PFSH_FP64, "fp32": PFSH_FP32, "bf16": PFSH_BF16, "fp16": PFSH_FP16, "bf16x3": PFSH_BF16X3}
+PFSH_FP64, PFSH_FP32, PFSH_BF16, PFSH_FP16, PFSH_BF16X3, PFSH_BF16X6 = 0, 1, 2, 3, 4, 5
+PREC_NAMES = {"fp64": PFSH_FP64, "fp32": PFSH_FP32, "bf16": PFSH_BF16, "fp16": PFSH_FP16, "bf16x3": PFSH_BF16X3,
+              "bf16x6": PFSH_BF16X6}
 
 EXPORTED = ["sht_plan_create", "sht_plan_destroy", "sht_plan_query", "sht_inverse", "sht_forward",
             "swe_ctx_create", "swe_ctx_destroy", "swe_rhs", "swe_implicit_solve",
@@ -32,7 +33,7 @@ EXPORTED = ["sht_plan_create", "sht_plan_destroy", "sht_plan_query", "sht_invers
             "pfasst_ensemble_destroy", "pfasst_ensemble_member", "pfasst_ensemble_predict",
             "pfasst_ensemble_iterations", "pfsh_sync_status", "pfsh_last_error",
             "pfsh_kernel_launches", "pfsh_profiler_enable", "pfsh_profiler_report", "sht_inverse_noalloc",
-            "pfsh_alu_peak"]
+            "pfsh_alu_peak", "pfsh_set_check_finite", "pfsh_selftest_wait"]
 
 
 class PfshError(RuntimeError):
@@ -116,6 +117,10 @@ _lib.pfsh_profiler_enable.argtypes = [c_int]
 _lib.pfsh_profiler_enable.restype = c_int
 _lib.pfsh_profiler_report.argtypes = [ctypes.c_char_p, c_size_t]
 _lib.pfsh_profiler_report.restype = c_int
+_lib.pfsh_set_check_finite.argtypes = [c_int]
+_lib.pfsh_set_check_finite.restype = c_int
+_lib.pfsh_selftest_wait.argtypes = [ctypes.c_uint, c_void_p]
+_lib.pfsh_selftest_wait.restype = c_int
 _lib.pfsh_alu_peak.argtypes = [c_int, ctypes.POINTER(c_double)]
 _lib.pfsh_alu_peak.restype = c_int
 
@@ -125,7 +130,7 @@ def available_precisions() -> list[str]:
     return [name for name, code in PREC_NAMES.items() if code in _BUILT_PRECISIONS]
 
 
-_BUILT_PRECISIONS = {PFSH_FP64, PFSH_FP32, PFSH_BF16, PFSH_FP16, PFSH_BF16X3}
+_BUILT_PRECISIONS = {PFSH_FP64, PFSH_FP32, PFSH_BF16, PFSH_FP16, PFSH_BF16X3, PFSH_BF16X6}
 
 
 def last_error() -> str:
@@ -413,6 +418,18 @@ def pfsh_profiler_report() -> dict:
     buf = ctypes.create_string_buffer(need + 16)
     _lib.pfsh_profiler_report(buf, len(buf))
     return json.loads(buf.value.decode())
+
+
+def pfsh_set_check_finite(on: bool) -> None:
+    """Opt-in device-side non-finite check of the results of swe_rhs, sdc_sweep
+    and the PFASST calls (PFSH_ENUMERIC at the next pfsh_sync_status)."""
+    _check(_lib.pfsh_set_check_finite(1 if on else 0))
+
+
+def pfsh_selftest_wait(polls: int, stream=None) -> None:
+    """One CTA waits on an mbarrier nothing arms, with a limit of `polls` polls;
+    the next pfsh_sync_status raises PfshError(PFSH_ETIMEOUT)."""
+    _check(_lib.pfsh_selftest_wait(polls, _stream(stream)))
 
 
 def pfsh_alu_peak(prec: int | str) -> float:

@@ -74,6 +74,8 @@ cudaError_t launch_pdl(void (*kern)(KArgs...), dim3 grid, dim3 block, size_t sme
 
 // sticky device status word shared by every object of the library
 int *device_status();
+// opt-in non-finite check of n doubles (checks.cu): records ST_NUMERIC
+int check_finite(const double *x, size_t n, cudaStream_t s);
 enum { ST_OK = 0, ST_TIMEOUT = 1, ST_NUMERIC = 2 };
 
 // ---------------------------------------------------------------------------

@@ -1,6 +1,9 @@
 // Legendre contractions per order m on tcgen05 tensor cores (the discrete
 // Legendre transform of Section 3) with bf16 operands and fp32 accumulation,
-// optionally as the split product hi*hi + hi*lo + lo*hi ("3xBF16").
+// optionally on split operands: two parts, hi*hi + hi*lo + lo*hi ("3xBF16",
+// about 16 bits of each operand), or three, x = hi + mid + lo with the six
+// products of the parts whose exponents sum above 2^-24 ("6xBF16", about 24
+// bits: fp32 accuracy on tensor cores).
 //
 // Both directions are GEMMs with the 128 real columns of a CTA (re/im of the
 // fields of a batch) as the MMA M dimension, so every accumulator row is one
@@ -41,8 +44,34 @@ namespace pfsh {
 
 namespace {
 
-constexpr int KC = 64;      // max K extent of one chunk
 constexpr int MROWS = 128;  // MMA M: real columns per CTA
+// max K extent of one chunk for NS split parts (three-part images are halved
+// in K so that two stages of both operands fit in shared memory)
+__host__ __device__ constexpr int kc_of(int ns) { return ns == 3 ? 32 : 64; }
+
+// the bf16/fp16 part products summed per K step for NS parts (a part, b part),
+// largest first
+__host__ __device__ constexpr int n_products(int ns) { return ns == 1 ? 1 : ns == 2 ? 3 : 6; }
+__device__ constexpr int kProdA[6] = {0, 0, 1, 0, 2, 1};
+__device__ constexpr int kProdB[6] = {0, 1, 0, 2, 0, 1};
+
+// x split into NS 16-bit parts, part k = round(x - parts 0..k-1)
+template <int NS, bool FP16>
+__device__ __forceinline__ void split_parts(float x, uint16_t (&out)[NS]) {
+  float r = x;
+#pragma unroll
+  for (int k = 0; k < NS; ++k) {
+    if (FP16) {
+      const __half h = __float2half_rn(r);
+      out[k] = __half_as_ushort(h);
+      r -= __half2float(h);
+    } else {
+      const __nv_bfloat16 h = __float2bfloat16_rn(r);
+      out[k] = __bfloat16_as_ushort(h);
+      r -= __bfloat162float(h);
+    }
+  }
+}
 
 constexpr int NTHREADS = 256;
 
@@ -50,7 +79,7 @@ constexpr int NTHREADS = 256;
 // spill at 128): a CTA then leaves room in the register file for a coarse-
 // chain block on the same SM, so the Step B transforms overlap the chain
 // better (measured: 197 -> 202 iterations/s, 3xBF16, T255/T127, 32 slices).
-template <bool X3, bool FP16, bool ANALYSIS>
+template <int NS, bool FP16, bool ANALYSIS>
 __global__ void __launch_bounds__(NTHREADS, 2)
     k_legendre_tc(int T, int nlat, int cols_real, int ntiles, const float *__restrict__ act,
                   const uint8_t *__restrict__ img, const TcChunk *__restrict__ chunks,
@@ -63,10 +92,11 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   if (wk.nchunks == 0) return;
   const int tid = threadIdx.x, warp = tid >> 5;
   const int N = wk.N;
-  const uint32_t a_half = MROWS * KC * 2;            // bytes of one A image (hi or lo)
-  const uint32_t a_bytes = a_half * (X3 ? 2 : 1);
+  constexpr int KC = kc_of(NS);
+  const uint32_t a_half = MROWS * KC * 2;            // bytes of one A image part
+  const uint32_t a_bytes = a_half * NS;
   const uint32_t b_half_max = (uint32_t)Nmax * KC * 2;
-  const uint32_t b_bytes = b_half_max * (X3 ? 2 : 1);
+  const uint32_t b_bytes = b_half_max * NS;
   uint8_t *stA[2] = {smem, smem + a_bytes + b_bytes};
   uint8_t *stB[2] = {smem + a_bytes, smem + 2 * a_bytes + b_bytes};
   uint64_t *bars = (uint64_t *)(smem + 2 * (a_bytes + b_bytes));
@@ -92,6 +122,43 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   const int m_len = T + 2 - m;          // degrees n = m .. T+1
   const size_t eo = (size_t)eoff(T, m);
 
+  // split one item (columns r, r+1 x 8 consecutive K from k0) into NS parts
+  // and store them in the parts of the A image A (tile K extent KL)
+  auto store_item = [&](uint8_t *A, int r, int k0, int KL, const float2 (&v)[8]) {
+    uint16_t p0[8][NS], p1[8][NS];
+#pragma unroll
+    for (int i = 0; i < 8; ++i) {
+      split_parts<NS, FP16>(v[i].x, p0[i]);
+      split_parts<NS, FP16>(v[i].y, p1[i]);
+    }
+    const uint32_t off0 = tc::tile_offset(r, k0, KL), off1 = tc::tile_offset(r + 1, k0, KL);
+#pragma unroll
+    for (int k = 0; k < NS; ++k) {
+      uint8_t *Ak = A + (size_t)k * a_half;
+      *(uint4 *)(Ak + off0) = make_uint4(p0[0][k] | (uint32_t)p0[1][k] << 16, p0[2][k] | (uint32_t)p0[3][k] << 16,
+                                         p0[4][k] | (uint32_t)p0[5][k] << 16, p0[6][k] | (uint32_t)p0[7][k] << 16);
+      *(uint4 *)(Ak + off1) = make_uint4(p1[0][k] | (uint32_t)p1[1][k] << 16, p1[2][k] | (uint32_t)p1[3][k] << 16,
+                                         p1[4][k] | (uint32_t)p1[5][k] << 16, p1[6][k] | (uint32_t)p1[7][k] << 16);
+    }
+  };
+  // MMAs of one chunk (stage A, stage B, K extent KL, parity p) into TMEM
+  auto issue_mmas = [&](const uint8_t *A, const uint8_t *Bimg, const TcChunk &ch) {
+    const int KL = ch.klen;
+    const uint32_t idesc = tc::make_idesc(MROWS, N, FP16);
+    const uint32_t sbo = 16u * KL;
+    const uint32_t b_half = (uint32_t)N * KL * 2;
+    const uint32_t a0 = tc::smem_u32(A), b0 = tc::smem_u32(Bimg);
+    const uint32_t d = tmem + (uint32_t)(ch.p * N);
+    for (int ks = 0; ks < KL / 16; ++ks) {
+#pragma unroll
+      for (int q = 0; q < n_products(NS); ++q) {
+        const uint32_t acc = (ch.kstart == 0 && ks == 0 && q == 0) ? 0u : 1u;
+        const uint64_t ad = tc::make_desc(a0 + kProdA[q] * a_half + ks * 256, 128, sbo);
+        const uint64_t bd = tc::make_desc(b0 + kProdB[q] * b_half + ks * 256, 128, sbo);
+        tc::mma_f16(d, ad, bd, idesc, acc);
+      }
+    }
+  };
   // activation items of one chunk (two adjacent columns x 8 consecutive K,
   // loaded as float2) into registers; zeros outside the tile
   constexpr int MAXIT = (MROWS / 2) * (KC / 8) / NTHREADS;
@@ -126,58 +193,24 @@ __global__ void __launch_bounds__(NTHREADS, 2)
     const int KL = ch.klen;
     const uint32_t b_half = (uint32_t)N * KL * 2;
     if (tid == 0) {
-      const uint32_t bytes = b_half * (X3 ? 2 : 1);
+      const uint32_t bytes = b_half * NS;
       tc::mbar_arrive_expect_tx(&full[s], bytes);
       tc::bulk_g2s(stB[s], img + ch.off, bytes, &full[s]);
     }
-    uint8_t *Ahi = stA[s], *Alo = stA[s] + a_half;
     const int nit = (MROWS / 2) * (KL >> 3);
 #pragma unroll
     for (int uu = 0; uu < MAXIT; ++uu) {
       const int it = tid + uu * NTHREADS;
       if (it >= nit) continue;
       const int rp = it & (MROWS / 2 - 1), g = it >> 6;
-      const int r = 2 * rp;
-      uint16_t h0[8], l0[8], h1[8], l1[8];
-#pragma unroll
-      for (int i = 0; i < 8; ++i) {
-        tc::split2<FP16>(v[uu][i].x, h0[i], l0[i]);
-        tc::split2<FP16>(v[uu][i].y, h1[i], l1[i]);
-      }
-      const uint32_t off0 = tc::tile_offset(r, g * 8, KL), off1 = tc::tile_offset(r + 1, g * 8, KL);
-      *(uint4 *)(Ahi + off0) = make_uint4(h0[0] | (uint32_t)h0[1] << 16, h0[2] | (uint32_t)h0[3] << 16,
-                                          h0[4] | (uint32_t)h0[5] << 16, h0[6] | (uint32_t)h0[7] << 16);
-      *(uint4 *)(Ahi + off1) = make_uint4(h1[0] | (uint32_t)h1[1] << 16, h1[2] | (uint32_t)h1[3] << 16,
-                                          h1[4] | (uint32_t)h1[5] << 16, h1[6] | (uint32_t)h1[7] << 16);
-      if (X3) {
-        *(uint4 *)(Alo + off0) = make_uint4(l0[0] | (uint32_t)l0[1] << 16, l0[2] | (uint32_t)l0[3] << 16,
-                                            l0[4] | (uint32_t)l0[5] << 16, l0[6] | (uint32_t)l0[7] << 16);
-        *(uint4 *)(Alo + off1) = make_uint4(l1[0] | (uint32_t)l1[1] << 16, l1[2] | (uint32_t)l1[3] << 16,
-                                            l1[4] | (uint32_t)l1[5] << 16, l1[6] | (uint32_t)l1[7] << 16);
-      }
+      store_item(stA[s], 2 * rp, g * 8, KL, v[uu]);
     }
     tc::fence_proxy_async();
     __syncthreads();
     if (tid == 0) {
       ok &= tc::mbar_wait(&full[s], u2 & 1);
       tc::fence_after_sync();
-      const uint32_t idesc = tc::make_idesc(MROWS, N, FP16);
-      const uint32_t sbo = 16u * KL;
-      const uint32_t a0 = tc::smem_u32(Ahi), a1 = tc::smem_u32(Alo);
-      const uint32_t b0 = tc::smem_u32(stB[s]), b1 = b0 + b_half;
-      const uint32_t d = tmem + (uint32_t)(ch.p * N);
-      for (int ks = 0; ks < KL / 16; ++ks) {
-        const uint32_t acc = (ch.kstart == 0 && ks == 0) ? 0u : 1u;
-        const uint64_t ah = tc::make_desc(a0 + ks * 256, 128, sbo);
-        const uint64_t bh = tc::make_desc(b0 + ks * 256, 128, sbo);
-        tc::mma_f16(d, ah, bh, idesc, acc);
-        if (X3) {
-          const uint64_t al = tc::make_desc(a1 + ks * 256, 128, sbo);
-          const uint64_t bl = tc::make_desc(b1 + ks * 256, 128, sbo);
-          tc::mma_f16(d, ah, bl, idesc, 1u);
-          tc::mma_f16(d, al, bh, idesc, 1u);
-        }
-      }
+      issue_mmas(stA[s], stB[s], ch);
       tc::mma_commit(&done[s]);
     }
   };
@@ -206,13 +239,12 @@ __global__ void __launch_bounds__(NTHREADS, 2)
       const int KL = ch.klen;
       const uint32_t b_half = (uint32_t)N * KL * 2;
       if (tid == 0) {
-        const uint32_t bytes = b_half * (X3 ? 2 : 1);
+        const uint32_t bytes = b_half * NS;
         tc::mbar_arrive_expect_tx(&full[s], bytes);
         tc::bulk_g2s(stB[s], img + ch.off, bytes, &full[s]);
       }
       // produce the activation chunk: rows = 128 real columns, K = KL; one
       // item = two adjacent columns x 8 consecutive K, loaded as float2
-      uint8_t *Ahi = stA[s], *Alo = stA[s] + a_half;
       const int groups = KL >> 3;
       for (int it = tid; it < (MROWS / 2) * groups; it += NTHREADS) {
         const int rp = it & (MROWS / 2 - 1), g = it >> 6;
@@ -231,46 +263,14 @@ __global__ void __launch_bounds__(NTHREADS, 2)
             }
           }
         }
-        uint16_t h0[8], l0[8], h1[8], l1[8];
-  #pragma unroll
-        for (int i = 0; i < 8; ++i) {
-          tc::split2<FP16>(v[i].x, h0[i], l0[i]);
-          tc::split2<FP16>(v[i].y, h1[i], l1[i]);
-        }
-        const uint32_t off0 = tc::tile_offset(r, g * 8, KL), off1 = tc::tile_offset(r + 1, g * 8, KL);
-        *(uint4 *)(Ahi + off0) = make_uint4(h0[0] | (uint32_t)h0[1] << 16, h0[2] | (uint32_t)h0[3] << 16,
-                                            h0[4] | (uint32_t)h0[5] << 16, h0[6] | (uint32_t)h0[7] << 16);
-        *(uint4 *)(Ahi + off1) = make_uint4(h1[0] | (uint32_t)h1[1] << 16, h1[2] | (uint32_t)h1[3] << 16,
-                                            h1[4] | (uint32_t)h1[5] << 16, h1[6] | (uint32_t)h1[7] << 16);
-        if (X3) {
-          *(uint4 *)(Alo + off0) = make_uint4(l0[0] | (uint32_t)l0[1] << 16, l0[2] | (uint32_t)l0[3] << 16,
-                                              l0[4] | (uint32_t)l0[5] << 16, l0[6] | (uint32_t)l0[7] << 16);
-          *(uint4 *)(Alo + off1) = make_uint4(l1[0] | (uint32_t)l1[1] << 16, l1[2] | (uint32_t)l1[3] << 16,
-                                              l1[4] | (uint32_t)l1[5] << 16, l1[6] | (uint32_t)l1[7] << 16);
-        }
+        store_item(stA[s], r, g * 8, KL, v);
       }
       tc::fence_proxy_async();
       __syncthreads();
       if (tid == 0) {
         ok &= tc::mbar_wait(&full[s], u & 1);
         tc::fence_after_sync();
-        const uint32_t idesc = tc::make_idesc(MROWS, N, FP16);
-        const uint32_t sbo = 16u * KL;
-        const uint32_t a0 = tc::smem_u32(Ahi), a1 = tc::smem_u32(Alo);
-        const uint32_t b0 = tc::smem_u32(stB[s]), b1 = b0 + b_half;
-        const uint32_t d = tmem + (uint32_t)(ch.p * N);
-        for (int ks = 0; ks < KL / 16; ++ks) {
-          const uint32_t acc = (ch.kstart == 0 && ks == 0) ? 0u : 1u;
-          const uint64_t ah = tc::make_desc(a0 + ks * 256, 128, sbo);
-          const uint64_t bh = tc::make_desc(b0 + ks * 256, 128, sbo);
-          tc::mma_f16(d, ah, bh, idesc, acc);
-          if (X3) {
-            const uint64_t al = tc::make_desc(a1 + ks * 256, 128, sbo);
-            const uint64_t bl = tc::make_desc(b1 + ks * 256, 128, sbo);
-            tc::mma_f16(d, ah, bl, idesc, 1u);
-            tc::mma_f16(d, al, bh, idesc, 1u);
-          }
-        }
+        issue_mmas(stA[s], stB[s], ch);
         tc::mma_commit(&done[s]);
       }
     }
@@ -309,15 +309,16 @@ __global__ void __launch_bounds__(NTHREADS, 2)
   if (!ok && tid == 0 && status) atomicExch(status, ST_TIMEOUT);
 }
 
-// Build the table images from the FP64 table: one block per chunk.
-template <bool FP16, bool ANALYSIS>
+// Build the table images from the FP64 table: one block per chunk; NS parts,
+// part k = round(P - parts 0..k-1) (the remainder carried in FP64).
+template <int NS, bool FP16, bool ANALYSIS>
 __global__ void k_build_images(int T, int nh, const double *__restrict__ P, const TcChunk *__restrict__ chunks,
                                uint8_t *__restrict__ img) {
   const TcChunk ch = chunks[blockIdx.x];
   const int N = ch.N, KL = ch.klen;
   const int m_len = T + 2 - ch.m;
   const size_t eo = (size_t)eoff(T, ch.m);
-  uint8_t *hi = img + ch.off, *lo = hi + (size_t)N * KL * 2;
+  uint8_t *base = img + ch.off;
   for (int e = threadIdx.x; e < N * KL; e += blockDim.x) {
     const int r = e / KL, k = e - r * KL;
     double v = 0.0;
@@ -330,27 +331,30 @@ __global__ void k_build_images(int T, int nh, const double *__restrict__ P, cons
         if (j < nh && noff < m_len) v = P[(eo + noff) * nh + j];
       }
     }
-    uint16_t h, l;
-    if (FP16) {
-      __half hh = __double2half(v);
-      h = __half_as_ushort(hh);
-      l = __half_as_ushort(__double2half(v - (double)__half2float(hh)));
-    } else {
-      __nv_bfloat16 hh = __double2bfloat16(v);
-      h = __bfloat16_as_ushort(hh);
-      l = __bfloat16_as_ushort(__double2bfloat16(v - (double)__bfloat162float(hh)));
-    }
     const uint32_t off = tc::tile_offset(r, k, KL);
-    *(uint16_t *)(hi + off) = h;
-    *(uint16_t *)(lo + off) = l;
+#pragma unroll
+    for (int q = 0; q < NS; ++q) {
+      uint16_t h;
+      if (FP16) {
+        const __half hh = __double2half(v);
+        h = __half_as_ushort(hh);
+        v -= (double)__half2float(hh);
+      } else {
+        const __nv_bfloat16 hh = __double2bfloat16(v);
+        h = __bfloat16_as_ushort(hh);
+        v -= (double)__bfloat162float(hh);
+      }
+      *(uint16_t *)(base + (size_t)q * N * KL * 2 + off) = h;
+    }
   }
 }
 
 int round16(int x) { return (x + 15) & ~15; }
 
 // host-side chunk lists for one direction
-void plan_chunks(int T, int nh, bool analysis, int tile_mult, std::vector<TcChunk> &chunks, std::vector<TcWork> &work,
-                 int &ntiles, int &Nmax, size_t &bytes) {
+void plan_chunks(int T, int nh, bool analysis, int tile_mult, int ns, std::vector<TcChunk> &chunks,
+                 std::vector<TcWork> &work, int &ntiles, int &Nmax, size_t &bytes) {
+  const int KC = kc_of(ns);
   chunks.clear();
   work.clear();
   Nmax = 16;
@@ -394,7 +398,7 @@ void plan_chunks(int T, int nh, bool analysis, int tile_mult, std::vector<TcChun
           c.N = w.N;
           c.row0 = w.row0;
           c.nrows = w.nrows;
-          bytes += (size_t)c.N * c.klen * 2 * 2;   // hi + lo
+          bytes += (size_t)c.N * c.klen * 2 * std::max(ns, 2);   // the parts (at least hi + lo)
           chunks.push_back(c);
         }
       }
@@ -409,20 +413,24 @@ int set_smem_attr(K kernel, size_t bytes) {
   return ensure_smem((const void *)kernel, bytes);
 }
 
-size_t tc_smem_bytes(int Nmax, bool x3) {
-  const size_t a = (size_t)MROWS * KC * 2 * (x3 ? 2 : 1);
-  const size_t b = (size_t)Nmax * KC * 2 * (x3 ? 2 : 1);
+size_t tc_smem_bytes(int Nmax, int ns) {
+  const size_t a = (size_t)MROWS * kc_of(ns) * 2 * ns;
+  const size_t b = (size_t)Nmax * kc_of(ns) * 2 * ns;
   return 2 * (a + b) + 64 + 1024;
 }
 
 }  // namespace
 
 // images, chunk and work lists of one direction and row tiling
+// 16-bit operand parts of a tensor-core precision
+static int ns_of(int prec) { return prec == PFSH_BF16X6 ? 3 : prec == PFSH_BF16X3 ? 2 : 1; }
+
 static int tc_build_dir(sht_plan *p, int dir, int tile_mult, TcDir &d) {
   const bool fp16 = p->prec == PFSH_FP16;
+  const int ns = ns_of(p->prec);
   std::vector<TcChunk> ch;
   std::vector<TcWork> wk;
-  plan_chunks(p->T, p->nh, dir == 1, tile_mult, ch, wk, d.ntiles, d.Nmax, d.img_bytes);
+  plan_chunks(p->T, p->nh, dir == 1, tile_mult, ns, ch, wk, d.ntiles, d.Nmax, d.img_bytes);
   d.nchunks = (int)ch.size();
   if (cudaMalloc(&d.img, d.img_bytes) != cudaSuccess || cudaMalloc(&d.chunks, ch.size() * sizeof(TcChunk)) ||
       cudaMalloc(&d.work, wk.size() * sizeof(TcWork))) {
@@ -435,12 +443,17 @@ static int tc_build_dir(sht_plan *p, int dir, int tile_mult, TcDir &d) {
   PFSH_CUDA(cudaMemset(d.img, 0, d.img_bytes));
   {
     PFSH_LAUNCH("k_build_images", 0);
+    auto launch = [&](auto kern) { kern<<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img); };
     if (dir == 0) {
-      if (fp16) k_build_images<true, false><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
-      else k_build_images<false, false><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
+      if (fp16) launch(k_build_images<1, true, false>);
+      else if (ns == 1) launch(k_build_images<1, false, false>);
+      else if (ns == 2) launch(k_build_images<2, false, false>);
+      else launch(k_build_images<3, false, false>);
     } else {
-      if (fp16) k_build_images<true, true><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
-      else k_build_images<false, true><<<d.nchunks, 256>>>(p->T, p->nh, p->d_P, d.chunks, d.img);
+      if (fp16) launch(k_build_images<1, true, true>);
+      else if (ns == 1) launch(k_build_images<1, false, true>);
+      else if (ns == 2) launch(k_build_images<2, false, true>);
+      else launch(k_build_images<3, false, true>);
     }
   }
   PFSH_CHECK_LAUNCH("k_build_images");
@@ -499,7 +512,7 @@ static void tune_cache_store(const TuneKey &k, int mult, const float us[kTcConfi
   fclose(f);
 }
 
-template <bool X3, bool FP16, bool AN>
+template <int NS, bool FP16, bool AN>
 static int launch_tc(const sht_plan *p, const TcDir &d, int cols, const float *act, float *out, cudaStream_t s,
                      const char *name);
 static int launch_dir(const sht_plan *p, int dir, const TcDir &d, int cols, cudaStream_t s);
@@ -604,12 +617,12 @@ int tc_tiles_used(const sht_plan *p, int dir, int nb) {
   return p->tc[dir][p->tc_pick[dir][std::min(nb, kTcMaxNb) - 1]].ntiles;
 }
 
-template <bool X3, bool FP16, bool AN>
+template <int NS, bool FP16, bool AN>
 static int launch_tc(const sht_plan *p, const TcDir &d, int cols, const float *act, float *out, cudaStream_t s,
                      const char *name) {
   const int cols_real = 2 * cols;
-  const size_t smem = tc_smem_bytes(d.Nmax, X3);
-  auto kern = k_legendre_tc<X3, FP16, AN>;
+  const size_t smem = tc_smem_bytes(d.Nmax, NS);
+  auto kern = k_legendre_tc<NS, FP16, AN>;
   int rc = set_smem_attr(kern, smem);
   if (rc) return rc;
   dim3 g((cols_real + MROWS - 1) / MROWS, d.ntiles, p->T + 1);
@@ -628,18 +641,20 @@ static int launch_dir(const sht_plan *p, int dir, const TcDir &d, int cols, cuda
     const float *X = (const float *)p->X;
     float *F = (float *)p->F;
     switch (p->prec) {
-      case PFSH_BF16: return launch_tc<false, false, false>(p, d, cols, X, F, s, "k_synth_bf16");
-      case PFSH_FP16: return launch_tc<false, true, false>(p, d, cols, X, F, s, "k_synth_fp16");
-      case PFSH_BF16X3: return launch_tc<true, false, false>(p, d, cols, X, F, s, "k_synth_bf16x3");
+      case PFSH_BF16: return launch_tc<1, false, false>(p, d, cols, X, F, s, "k_synth_bf16");
+      case PFSH_FP16: return launch_tc<1, true, false>(p, d, cols, X, F, s, "k_synth_fp16");
+      case PFSH_BF16X3: return launch_tc<2, false, false>(p, d, cols, X, F, s, "k_synth_bf16x3");
+      case PFSH_BF16X6: return launch_tc<3, false, false>(p, d, cols, X, F, s, "k_synth_bf16x6");
       default: return fail(PFSH_EUNSUPPORTED, "synth_tc: precision");
     }
   }
   const float *H = (const float *)p->H;
   float *Y = (float *)p->Y;
   switch (p->prec) {
-    case PFSH_BF16: return launch_tc<false, false, true>(p, d, cols, H, Y, s, "k_anal_bf16");
-    case PFSH_FP16: return launch_tc<false, true, true>(p, d, cols, H, Y, s, "k_anal_fp16");
-    case PFSH_BF16X3: return launch_tc<true, false, true>(p, d, cols, H, Y, s, "k_anal_bf16x3");
+    case PFSH_BF16: return launch_tc<1, false, true>(p, d, cols, H, Y, s, "k_anal_bf16");
+    case PFSH_FP16: return launch_tc<1, true, true>(p, d, cols, H, Y, s, "k_anal_fp16");
+    case PFSH_BF16X3: return launch_tc<2, false, true>(p, d, cols, H, Y, s, "k_anal_bf16x3");
+    case PFSH_BF16X6: return launch_tc<3, false, true>(p, d, cols, H, Y, s, "k_anal_bf16x6");
     default: return fail(PFSH_EUNSUPPORTED, "analysis_tc: precision");
   }
 }

@@ -633,11 +633,18 @@ static int run_block(pfasst *pf, int count, int last, cudaStream_t s) {
                     [&](cudaStream_t st) { return block_body(pf, count, last, st); });
 }
 
+// opt-in non-finite check of the fine end values of every slice (outside the graphs)
+static int check_ends(pfasst *pf, cudaStream_t s) {
+  const size_t n = (size_t)pf->cfg.n_ts * pf->sf;
+  return check_finite(pf->th_f + (size_t)pf->Mf * n, n, s);
+}
+
 extern "C" int pfasst_predict(pfasst *pf, pfsh_stream_t stream) {
   if (!pf) return fail(PFSH_EINVAL, "pfasst_predict: NULL argument");
   // graph key (0, 2): no iteration block has count 0
-  return run_cached(pf->graphs_, pf->graphs, pf->cap_stream, 0, 2, (cudaStream_t)stream,
-                    [&](cudaStream_t st) { return predict_body(pf, st); });
+  int rc = run_cached(pf->graphs_, pf->graphs, pf->cap_stream, 0, 2, (cudaStream_t)stream,
+                      [&](cudaStream_t st) { return predict_body(pf, st); });
+  return rc ? rc : check_ends(pf, (cudaStream_t)stream);
 }
 
 extern "C" int pfasst_residual(pfasst *pf, double *res, pfsh_stream_t stream) {
@@ -655,12 +662,14 @@ extern "C" int pfasst_residual(pfasst *pf, double *res, pfsh_stream_t stream) {
 
 extern "C" int pfasst_iteration(pfasst *pf, int last, pfsh_stream_t stream) {
   if (!pf) return fail(PFSH_EINVAL, "pfasst_iteration: NULL argument");
-  return run_block(pf, 1, last ? 1 : 0, (cudaStream_t)stream);
+  int rc = run_block(pf, 1, last ? 1 : 0, (cudaStream_t)stream);
+  return rc ? rc : check_ends(pf, (cudaStream_t)stream);
 }
 
 extern "C" int pfasst_iterations(pfasst *pf, int count, int last, pfsh_stream_t stream) {
   if (!pf || count < 1) return fail(PFSH_EINVAL, "pfasst_iterations: NULL argument or count < 1");
-  return run_block(pf, count, last ? 1 : 0, (cudaStream_t)stream);
+  int rc = run_block(pf, count, last ? 1 : 0, (cudaStream_t)stream);
+  return rc ? rc : check_ends(pf, (cudaStream_t)stream);
 }
 
 // ---------------------------------------------------------------------------

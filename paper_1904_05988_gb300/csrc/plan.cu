@@ -144,7 +144,9 @@ int convert_table_f32(const double *a, float *b, size_t n, cudaStream_t s) {
   return PFSH_OK;
 }
 
-bool uses_tensor_cores(int prec) { return prec == PFSH_BF16 || prec == PFSH_FP16 || prec == PFSH_BF16X3; }
+bool uses_tensor_cores(int prec) {
+  return prec == PFSH_BF16 || prec == PFSH_FP16 || prec == PFSH_BF16X3 || prec == PFSH_BF16X6;
+}
 
 // Batches of one or two states (the serial coarse chain of PFASST) take
 // latency-oriented CUDA-core kernels (fp64 for FP64 plans, fp32 otherwise):

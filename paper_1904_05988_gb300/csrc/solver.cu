@@ -175,7 +175,11 @@ extern "C" int swe_ctx_destroy(swe_ctx *c) {
 extern "C" int swe_rhs(swe_ctx *c, const double *state, double *fE, double *fI, int B, pfsh_stream_t stream) {
   if (!c || B < 0 || (B > 0 && (!state || !fE))) return fail(PFSH_EINVAL, "swe_rhs: invalid argument");
   if (B == 0) return PFSH_OK;
-  return rhs_eval(c, state, fE, fI, B, (cudaStream_t)stream);
+  const size_t n = (size_t)B * 3 * c->plan->ncoef * 2;
+  int rc = rhs_eval(c, state, fE, fI, B, (cudaStream_t)stream);
+  if (!rc) rc = check_finite(fE, n, (cudaStream_t)stream);
+  if (!rc && fI) rc = check_finite(fI, n, (cudaStream_t)stream);
+  return rc;
 }
 
 extern "C" int swe_implicit_solve(swe_ctx *c, const double *b, double *x, double h, int B, pfsh_stream_t stream) {
@@ -296,5 +300,7 @@ extern "C" int sdc_sweep(sdc_level *l, double *theta, double *fE, double *fI, co
   if (!l || B < 0 || (B > 0 && (!theta || !fE || !fI))) return fail(PFSH_EINVAL, "sdc_sweep: invalid argument");
   if (B == 0) return PFSH_OK;
   const size_t st = (size_t)3 * l->ctx->plan->ncoef * 2 * B;
-  return sdc_sweep_strided(l, theta, fE, fI, tau, st, B, (cudaStream_t)stream);
+  int rc = sdc_sweep_strided(l, theta, fE, fI, tau, st, B, (cudaStream_t)stream);
+  if (!rc) rc = check_finite(theta, st * l->nodes, (cudaStream_t)stream);
+  return rc;
 }

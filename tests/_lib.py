@@ -25,14 +25,15 @@ def declared_functions() -> list[str]:
 
 # Error laws of the mixed-precision forms (rounding-derived bounds of the GPU tests).
 # u = unit rounding of the form's operands: fp32 2^-24; bf16 2^-9 (8 stored
-# mantissa bits); 3xBF16 2^-17 (the hi/lo split keeps about 16 bits).  The
+# mantissa bits); 3xBF16 2^-17 (the hi/lo split keeps about 16 bits); 6xBF16
+# 2^-24 (the three-part split keeps about 24 bits, the precision of fp32).  The
 # transforms lose a few u; the nonlinear tendency F_E is a spectral derivative
 # (div/curl, factors n eps ~ n/2, and n(n+1)/a^2 on E) of analysed fluxes, so its
 # rounding error at degree n grows like u (n+1).  Measured on GB300 over
 # T63/T170/T255 and all three fields, max_n e_n / (u (n+1) |F_E|) <= 11.2 (fp32
 # delta tendency at T255; bf16 <= 3.4, 3xBF16 <= 1.2), the whole-field error
 # <= 37 u (T+1) and the error over the band n <= T/4 <= 5.1 u (T/4 + 1).
-U_FORM = {"fp32": 2.0 ** -24, "bf16": 2.0 ** -9, "bf16x3": 2.0 ** -17, "fp16": 2.0 ** -11}
+U_FORM = {"fp32": 2.0 ** -24, "bf16": 2.0 ** -9, "bf16x3": 2.0 ** -17, "bf16x6": 2.0 ** -24, "fp16": 2.0 ** -11}
 C_DEGREE, C_WHOLE, C_LOWBAND = 24.0, 48.0, 8.0
 
 

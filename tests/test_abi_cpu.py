@@ -51,3 +51,13 @@ def test_noalloc_binding_rejects_a_ragged_spectrum_before_the_library():
     grid = torch.zeros((1, 48, 96), dtype=torch.float64)
     with pytest.raises(ValueError):
         ps.sht_inverse_noalloc(31, 48, 96, spec, grid)
+
+
+def test_failure_detection_arguments_checked_without_a_gpu():
+    ensure_built()
+    import paper_1904_05988_gb300 as ps
+    import pytest
+    with pytest.raises(ps.PfshError) as e:
+        ps.pfsh_selftest_wait(0, stream=0)
+    assert e.value.code == ps.PFSH_EINVAL
+    ps.pfsh_set_check_finite(False)
