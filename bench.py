@@ -299,6 +299,7 @@ def run_ours(args, rank, world, local_rank):
 
     # ---- the plain FP64 GPU path on the same workload, for the speedup ----
     fp64 = None
+    fp64_end = None
     if args.prec != "fp64" and not args.no_fp64_path:
         pf64 = make("fp64")
         ps.pfasst_set_initial(pf64, d_st0)
@@ -309,6 +310,7 @@ def run_ours(args, rank, world, local_rank):
         block_solve(ps, torch, pf64, h_in, h_out, d_in, d_out)
         torch.cuda.synchronize()
         ref = h_out.numpy()
+        fp64_end = ref.copy()
         diff = float(np.linalg.norm(end_state - ref) / np.linalg.norm(ref))
         pert = end_state - st0
         pert_ref = ref - st0
@@ -341,6 +343,25 @@ def run_ours(args, rank, world, local_rank):
                 "value": world * 1e3 / msv, "unit": "PFASST iterations/s", "ms_per_step": msv, "steps": kv,
                 "end_state_change_rel_l2_vs_headline": float(np.linalg.norm((alt - st0) - (end_state - st0))
                                                              / np.linalg.norm(end_state - st0))}
+        # the same workload in the other arithmetic forms of the Legendre contractions
+        for prec in ("fp32", "bf16", "bf16x6"):
+            if prec == args.prec:
+                continue
+            pv = make(prec)
+            ps.pfasst_set_initial(pv, d_st0)
+            ps.pfasst_predict(pv)
+            kv = max(2, min(10, args.steps))
+            prepare_block(ps, pv, kv, 1)
+            msv = time_iterations(ps, torch, pv, stream, kv) / kv
+            block_solve(ps, torch, pv, h_in, h_out, d_in, d_out)
+            torch.cuda.synchronize()
+            alt = h_out.numpy()
+            pv.close()
+            variants["prec_" + prec] = {
+                "value": world * 1e3 / msv, "unit": "PFASST iterations/s", "ms_per_step": msv, "steps": kv,
+                "end_state_change_rel_l2_vs_fp64": (float(np.linalg.norm((alt - st0) - (fp64_end - st0))
+                                                          / np.linalg.norm(fp64_end - st0))
+                                                    if fp64_end is not None else None)}
 
     cpu = cpu_baseline_sample() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
@@ -446,7 +467,7 @@ def kernel_work_per_iteration(name: str, prec: str):
     ncf1, ncc1 = syn.ncoef(TF + 1), syn.ncoef(TC + 1)
     elem = 8 if prec == "fp64" else 4
     st_f, st_c = 48 * ncf, 48 * ncc       # bytes of one FP64 state (3 fields, complex)
-    tc = prec in ("bf16", "fp16", "bf16x3")
+    tc = prec in ("bf16", "fp16", "bf16x3", "bf16x6")
     simt_bound = ("alu", "FP64 pipe") if prec == "fp64" else ("alu", "FP32 pipe")
     if name.startswith("k_synth") or name.startswith("k_anal"):
         synth = name.startswith("k_synth")
@@ -459,7 +480,7 @@ def kernel_work_per_iteration(name: str, prec: str):
             spec = syn.ncoef(T + 1) * cols * 8
             four = (T + 1) * nlat * cols * 8
             return spec + four
-        tab = {"bf16x3": 4, "bf16": 2, "fp16": 2, "fp32": 4, "fp64": 8}[prec]
+        tab = {"bf16x6": 6, "bf16x3": 4, "bf16": 2, "fp16": 2, "fp32": 4, "fp64": 8}[prec]
         def table(T, nlat):
             return (T + 2) * (T + 3) // 2 * (nlat // 2) * tab
         groups = 1 if prec == "fp64" else 2
@@ -468,7 +489,7 @@ def kernel_work_per_iteration(name: str, prec: str):
         if prec == "fp64":
             byts *= 2   # fp64 complex activations and results
         if tc:
-            mult = 3 if prec == "bf16x3" else 1
+            mult = {"bf16x3": 3, "bf16x6": 6}.get(prec, 1)
             return w, "flop", ("tensor", f"{mult} MMA products per algorithmic flop"), byts
         return w, "flop", simt_bound, byts
     if name.startswith("k_small_synth") or name.startswith("k_small_anal"):
@@ -535,7 +556,7 @@ def roofline_entry(name: str, n: int, tot_ms: float, prec: str, iterations: int)
     if bound == "tensor" and byts:
         # per-order GEMMs at this batch: below the bf16 ridge (peak flops /
         # HBM bandwidth) the table and activation traffic bounds them
-        mult = 3 if "3 MMA" in (note or "") else 1
+        mult = int(note.split()[0]) if note and note.split()[0].isdigit() else 1
         intensity = mult * work / byts
         ridge = pk["bf16_tflops_sustained"] * 1e12 / (pk["hbm_gbs"] * 1e9)
         if intensity < ridge:
@@ -699,10 +720,11 @@ def main():
     ap.add_argument("--gpus", type=int, default=1)
     ap.add_argument("--steps", type=int, default=10)
     ap.add_argument("--warmup", type=int, default=3)
-    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "fp16", "bf16x3"])
+    ap.add_argument("--prec", default="bf16x3", choices=["fp64", "fp32", "bf16", "fp16", "bf16x3", "bf16x6"])
     ap.add_argument("--no-fp64-path", action="store_true", help="skip timing the FP64 GPU path")
     ap.add_argument("--no-variants", action="store_true",
-                    help="skip timing the Coriolis-implicit and two-substep variants of the workload")
+                    help="skip timing the Coriolis-implicit and two-substep variants of the workload and the other "
+                         "arithmetic forms")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
     args = ap.parse_args()
