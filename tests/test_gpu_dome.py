@@ -34,6 +34,8 @@ pytestmark = pytest.mark.gpu
 torch = pytest.importorskip("torch")
 ensure_built()
 import paper_1904_05988_gb300 as ps  # noqa: E402
+import sys  # noqa: E402
+sys.path.insert(0, os.path.dirname(os.path.abspath(__file__)))
 
 DEV = torch.device("cuda:0")
 with open(os.path.join(os.path.dirname(os.path.abspath(__file__)), "golden", "gaussian_dome_sec6_1.json")) as _fh:
@@ -116,3 +118,45 @@ def test_gaussian_dome_pfasst_against_sdc_reference(form, dome, reference):
           f"E_32 {errs[0]:.3e}  E_64 {errs[1]:.3e}  E_256 {errs[2]:.3e}")
     assert all(e < b for e, b in zip(errs, BOUNDS[form])), errs
     pf.close()
+
+
+# ---------------------------------------------------------------------------
+# Sensitivity to the number of iterations (the closing study of Section 6.1):
+# with dt = 100 s fixed, the error stops decreasing beyond a threshold N_PF,
+# because the coarse level cannot represent the modes above T_c; the paper
+# finds the threshold at N_PF = 2, 4 and 6 for alpha = 1/5, 1/2 and 4/5, and a
+# plateau error that falls as alpha grows.  Window 12,800 s (8 PFASST blocks);
+# the full 102,400 s study is tests/dome_study.py (tables in the design notes).
+# ---------------------------------------------------------------------------
+STUDY_WINDOW, STUDY_NPF = 12800.0, (1, 2, 4, 6, 8)
+
+
+def threshold(errs):
+    """Smallest N_PF whose error is within 2x of the error at the largest N_PF."""
+    last = errs[STUDY_NPF[-1]]
+    return min(n for n in STUDY_NPF if errs[n] <= 2.0 * last)
+
+
+def test_iteration_count_thresholds_follow_the_coarsening_ratio(dome):
+    import dome_study as ds
+    st, phibar = dome
+    ref, _ = ds.sdc_reference(ps, torch, st, phibar, STUDY_WINDOW)
+    e32, e256 = {}, {}
+    for name, alpha in ds.ALPHAS.items():
+        e32[name], e256[name] = {}, {}
+        for npf in STUDY_NPF:
+            phi = ds.pfasst_run(ps, torch, st, phibar, STUDY_WINDOW, 100.0, alpha, npf)[0]
+            e32[name][npf] = ds.e_norm(phi, ref[0], TF, 32)
+            e256[name][npf] = ds.e_norm(phi, ref[0], TF, 255)
+        print(f"\nalpha {name}: E_32 " + " ".join(f"{e32[name][n]:.2e}" for n in STUDY_NPF) +
+              "  E_256 " + " ".join(f"{e256[name][n]:.2e}" for n in STUDY_NPF))
+    t256 = {a: threshold(e256[a]) for a in ds.ALPHAS}
+    t32 = {a: threshold(e32[a]) for a in ds.ALPHAS}
+    # the paper's thresholds: 2 for alpha = 1/5 and 4 for 1/2 on the full
+    # spectrum, 6 for 4/5 on the large scales (R_norm = 32)
+    assert t256["1/5"] == 2 and t256["1/2"] == 4 and t32["4/5"] == 6, (t256, t32)
+    # thresholds grow with alpha in both norms; the plateau error falls
+    assert t256["1/5"] <= t256["1/2"] <= t256["4/5"] and t32["1/5"] <= t32["1/2"] <= t32["4/5"]
+    assert e256["1/5"][8] > 3 * e256["1/2"][8] > 3 * 3 * e256["4/5"][8]
+    # aggressive coarsening stagnates: alpha = 1/5 gains less than 2x from 2 to 8 iterations
+    assert e256["1/5"][8] > 0.5 * e256["1/5"][2]
