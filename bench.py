@@ -363,6 +363,10 @@ def run_ours(args, rank, world, local_rank):
                                                           / np.linalg.norm(fp64_end - st0))
                                                     if fp64_end is not None else None)}
 
+    # ---- opt-in: the large single instance and the uneven batch ----
+    large = large_instance(ps, torch, stream, world, args.prec) if args.config5 else None
+    uneven = uneven_batch(ps, torch, stream, world, args.prec) if args.uneven else None
+
     cpu = cpu_baseline_sample() if (rank == 0 and world == 1 and not args.no_cpu_baseline) else None
     if rank == 0:
         dtype = "f64" if args.prec == "fp64" else \
@@ -393,6 +397,8 @@ def run_ours(args, rank, world, local_rank):
             "alu_peaks": alu["raw"],
             "kernels_ms_per_iteration": {k: round(v[1] / 2, 4) for k, v in sorted(prof.items(), key=lambda kv: -kv[1][1])},
             "cpu_baseline": cpu,
+            "large_instance": large,
+            "uneven_batch": uneven,
             # short keys last, so that they stay in the visible end of the line
             "fp64_gpu_it_s": fp64["value"] if fp64 else None,
             "speedup_vs_fp64": fp64["speedup_of_value"] if fp64 else None,
@@ -400,6 +406,83 @@ def run_ours(args, rank, world, local_rank):
         print(json.dumps(line), flush=True)
     if dist is not None:
         dist.destroy_process_group()
+
+
+def large_instance(ps, torch, stream, world, prec):
+    """T1279 on 1920 x 3840 / T639 on 960 x 1920, 16 slices x 5 / 3 nodes x 3
+    fields, dt = 30 s, 3 PFASST iterations timed after one untimed; balanced
+    jet plus seeded n^-3 vorticity and divergence spectra of area-rms 1e-6 1/s
+    (seed 5).  Tables streamed from HBM (not recomputed on the fly)."""
+    W = Workload(1279, 639, 16, 5, 3)
+    st = syn.zonal_jet(W.TF)
+    pert = syn.random_spectrum(W.TF, (2,), seed=5, rms=1e-6)
+    st[1] += pert[0]
+    st[2] += pert[1]
+    phibar = st[0, 0].real / math.sqrt(2.0)
+    t0 = time.perf_counter()
+    pf = ps.pfasst_create(W.NTS, W.NF, W.NC, W.TF, *W.GRID_F, W.TC, *W.GRID_C, 30.0, syn.EARTH_RADIUS, syn.OMEGA,
+                          syn.NU, phibar, prec)
+    ps.pfasst_set_initial(pf, torch.tensor(st, dtype=torch.complex128, device="cuda"))
+    ps.pfasst_predict(pf)
+    prepare_block(ps, pf, 3, 1)
+    setup_s = time.perf_counter() - t0
+    ms = time_iterations(ps, torch, pf, stream, 3) / 3
+    ps.pfsh_profiler_enable(True)
+    ps.pfasst_iterations(pf, 1, False)
+    ps.pfsh_profiler_enable(False)
+    prof = ps.pfsh_profiler_report()
+    ps.pfsh_sync_status()
+    pf.close()
+    W.groups = 1 if prec == "fp64" else 2
+    roofs = rooflines_of(prof, prec, 1, top=3, W=W)
+    return {"workload": "T1279 (1920x3840, 5 nodes) / T639 (960x1920, 3 nodes), 16 slices, dt=30 s, jet + n^-3 "
+                        "vorticity/divergence (seed 5)", "prec": prec, "value": world * 1e3 / ms,
+            "unit": "PFASST iterations/s", "ms_per_step": ms, "steps": 3, "setup_s": setup_s,
+            "roofline": roofs[0] if roofs else None, "rooflines_top": roofs[1:],
+            "kernels_ms_per_iteration": {k: round(v[1], 3) for k, v in
+                                         sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+
+
+def uneven_batch(ps, torch, stream, world, prec):
+    """48 independent instances with T drawn from {63, 127, 170, 255} (seed 4),
+    coarse level T/2, 8 slices, 5 / 3 nodes, dt = 120 * 256 / (T + 1) s, advanced
+    together (pfasst_ensemble_*): instance-iterations/s over one block of 4
+    iterations after an untimed one."""
+    rng = np.random.default_rng(4)
+    Ts = [int(t) for t in rng.choice([63, 127, 170, 255], size=48)]
+    cfgs = []
+    for T in Ts:
+        gf, gc = syn.gaussian_grid_size(T), syn.gaussian_grid_size(T // 2)
+        cfgs.append(ps.pfasst_config(8, 5, 3, T, *gf, T // 2, *gc, 120.0 * 256 / (T + 1), syn.EARTH_RADIUS,
+                                     syn.OMEGA, syn.NU, syn.GRAVITY * syn.MEAN_DEPTH, prec))
+    t0 = time.perf_counter()
+    ens = ps.pfasst_ensemble_create(cfgs)
+    for i, T in enumerate(Ts):
+        st = syn.zonal_jet(T)
+        pert = syn.random_spectrum(T, (2,), seed=100 + i, rms=1e-6)
+        st[1] += pert[0]
+        st[2] += pert[1]
+        ps.pfasst_set_initial(ps.pfasst_ensemble_member(ens, i), torch.tensor(st, dtype=torch.complex128,
+                                                                              device="cuda"))
+    ps.pfasst_ensemble_predict(ens)
+    for _ in range(2):   # eager run, graph capture
+        ps.pfasst_ensemble_iterations(ens, 4, False)
+    torch.cuda.synchronize()
+    setup_s = time.perf_counter() - t0
+    e0, e1 = torch.cuda.Event(enable_timing=True), torch.cuda.Event(enable_timing=True)
+    e0.record(stream)
+    ps.pfasst_ensemble_iterations(ens, 4, False)
+    e1.record(stream)
+    torch.cuda.synchronize()
+    ms = e0.elapsed_time(e1)
+    ps.pfsh_sync_status()
+    ens.close()
+    return {"workload": "48 instances, T in {63,127,170,255} (seed 4; " +
+                        ", ".join(f"{t}: {Ts.count(t)}" for t in (63, 127, 170, 255)) +
+                        "), coarse T/2, 8 slices, 5/3 nodes", "prec": prec,
+            "value": world * 48 * 4 / (ms / 1e3), "unit": "instance-iterations/s", "ms_per_block": ms,
+            "iterations_per_block": 4, "setup_s": setup_s,
+            "path": "pfasst_ensemble_iterations: every member on its own stream pair, one CUDA graph"}
 
 
 def peaks():
@@ -447,21 +530,34 @@ def measure_alu_peaks(ps, torch, dev) -> dict:
     return out
 
 
-def rhs_states_per_iteration():
+class Workload:
+    """Sizes of a two-level PFASST workload (the default: the headline's)."""
+
+    def __init__(self, TF=TF, TC=TC, NTS=NTS, NF=NF, NC=NC, groups=None):
+        self.TF, self.TC, self.NTS, self.NF, self.NC = TF, TC, NTS, NF, NC
+        self.GRID_F, self.GRID_C = syn.gaussian_grid_size(TF), syn.gaussian_grid_size(TC)
+        self.groups = groups
+
+
+HEADLINE = Workload()
+
+
+def rhs_states_per_iteration(W: Workload = HEADLINE):
     """RHS evaluations in one (non-final) iteration of Algorithm 1 over all
     slices: fine = sweep nodes 1..Mf + node 0 after Step D (batched);
     coarse batched = every node in Step B; coarse chain = node 0 of slices
     1.. + sweep nodes 1..Mc, one state per call (small-batch kernels)."""
-    fine = NTS * (NF - 1) + NTS
-    coarse_batched = NTS * NC
-    coarse_chain = (NTS - 1) + NTS * (NC - 1)
+    fine = W.NTS * (W.NF - 1) + W.NTS
+    coarse_batched = W.NTS * W.NC
+    coarse_chain = (W.NTS - 1) + W.NTS * (W.NC - 1)
     return fine, coarse_batched, coarse_chain
 
 
-def kernel_work_per_iteration(name: str, prec: str):
+def kernel_work_per_iteration(name: str, prec: str, W: Workload = HEADLINE):
     """(algorithmic work, unit, bound, note) of all launches of `name` in one
-    iteration; None if the kernel has no model."""
-    nfs, ncb, ncs = rhs_states_per_iteration()
+    iteration of the workload W; None if the kernel has no model."""
+    TF, TC, NTS, NF, NC, GRID_F, GRID_C = W.TF, W.TC, W.NTS, W.NF, W.NC, W.GRID_F, W.GRID_C
+    nfs, ncb, ncs = rhs_states_per_iteration(W)
     (nlat_f, _), (nlat_c, _) = GRID_F, GRID_C
     ncf, ncc = syn.ncoef(TF), syn.ncoef(TC)
     ncf1, ncc1 = syn.ncoef(TF + 1), syn.ncoef(TC + 1)
@@ -483,7 +579,7 @@ def kernel_work_per_iteration(name: str, prec: str):
         tab = {"bf16x6": 6, "bf16x3": 4, "bf16": 2, "fp16": 2, "fp32": 4, "fp64": 8}[prec]
         def table(T, nlat):
             return (T + 2) * (T + 3) // 2 * (nlat // 2) * tab
-        groups = 1 if prec == "fp64" else 2
+        groups = W.groups if W.groups else (1 if prec == "fp64" else 2)
         byts = (nfs * per_state(TF, nlat_f) + ncb * per_state(TC, nlat_c) +
                 groups * (NF * table(TF, nlat_f) + NC * table(TC, nlat_c)))
         if prec == "fp64":
@@ -495,7 +591,7 @@ def kernel_work_per_iteration(name: str, prec: str):
     if name.startswith("k_small_synth") or name.startswith("k_small_anal"):
         cols = 4 if "synth" in name else 5
         return ncs * legendre_flops(TC, nlat_c, cols), "flop", simt_bound, None
-    if name == "k_grid_rhs":
+    if name in ("k_grid_rhs", "k_grid_rhs_long"):
         return (nfs * grid_rhs_bytes(TF, nlat_f, 1, elem) + (ncb + ncs) * grid_rhs_bytes(TC, nlat_c, 1, elem),
                 "byte", ("hbm", None), None)
     if name == "k_rhs_prep":
@@ -540,13 +636,13 @@ NCU_TRAFFIC = {
 }
 
 
-def roofline_entry(name: str, n: int, tot_ms: float, prec: str, iterations: int) -> dict:
-    tr = NCU_TRAFFIC.get(name)
+def roofline_entry(name: str, n: int, tot_ms: float, prec: str, iterations: int, W: Workload = HEADLINE) -> dict:
+    tr = NCU_TRAFFIC.get(name) if W is HEADLINE else None
     out = {"kernel": name, "launches": n, "mean_launch_ms": tot_ms / n,
            "traffic": tr[0] if tr and prec in tr[1] else None}
     if out["traffic"] is not None:
         out["traffic_source"] = f"ncu capture of one launch, {tr[2]}"
-    model = kernel_work_per_iteration(name, prec)
+    model = kernel_work_per_iteration(name, prec, W)
     if model is None:
         out.update({"bound": "unknown", "achieved": None, "peak": None, "unit": None, "frac": None})
         return out
@@ -582,14 +678,14 @@ def roofline_entry(name: str, n: int, tot_ms: float, prec: str, iterations: int)
     return out
 
 
-def rooflines_of(prof: dict, prec: str, iterations: int, top: int = 5) -> list:
+def rooflines_of(prof: dict, prec: str, iterations: int, top: int = 5, W: Workload = HEADLINE) -> list:
     """Rooflines of the `top` kernels by total time in the profiled pass:
     algorithmic work of their launches / their summed duration (= work per
     launch / mean launch duration).  The first entry is the dominant kernel."""
     if not prof:
         return []
     items = sorted(prof.items(), key=lambda kv: -kv[1][1])[:top]
-    return [roofline_entry(name, n, tot, prec, iterations) for name, (n, tot) in items]
+    return [roofline_entry(name, n, tot, prec, iterations, W) for name, (n, tot) in items]
 
 
 # ---------------------------------------------------------------------------
@@ -727,6 +823,10 @@ def main():
                          "arithmetic forms")
     ap.add_argument("--impl", default="ours", choices=["ours", "reference"])
     ap.add_argument("--no-cpu-baseline", action="store_true")
+    ap.add_argument("--config5", action="store_true",
+                    help="also time the large single instance (T1279/T639, 16 slices, 3 iterations)")
+    ap.add_argument("--uneven", action="store_true",
+                    help="also time the uneven batch of 48 instances (T from {63,127,170,255})")
     args = ap.parse_args()
     rank, world, local_rank = env_int("RANK", 0), env_int("WORLD_SIZE", 1), env_int("LOCAL_RANK", 0)
     if args.impl == "reference":
