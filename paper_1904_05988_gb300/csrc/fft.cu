@@ -105,12 +105,11 @@ __global__ void __launch_bounds__(256) k_grid_rhs(FftArgs f, int T, int nlat, in
                                                   const typename cpx<Rl>::t *__restrict__ F,
                                                   const Rl *__restrict__ rowf,
                                                   const typename cpx<Rl>::t *__restrict__ tw,
-                                                  typename cpx<Rl>::t *__restrict__ H, bool center,
-                                                  const typename cpx<Rl>::t *__restrict__ F2, int msplit) {
+                                                  typename cpx<Rl>::t *__restrict__ H, bool center) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_wait();
   grid_rhs_body<Rl, Shape>(f, T, nlat, B, blockIdx.x, blockIdx.y, F, rowf, tw, H,
-                           reinterpret_cast<typename cpx<Rl>::t *>(smem_raw), center, F2, msplit);
+                           reinterpret_cast<typename cpx<Rl>::t *>(smem_raw), center);
 }
 
 template <typename Rl, typename Shape>
@@ -197,7 +196,7 @@ constexpr size_t kGridSmemLimit = 227 * 1024;
 // longer ones k_grid_rhs_long (6 transforms).
 template <typename Rl>
 static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typename cpx<Rl>::t *tw, const Rl *rowf,
-                       cudaStream_t s, bool pdl, int msplit) {
+                       cudaStream_t s, bool pdl) {
   typedef typename cpx<Rl>::t C;
   const size_t sm10 = 10 * (size_t)padded(f.N) * sizeof(C), sm6 = 6 * (size_t)padded(f.N) * sizeof(C);
   const bool longrows = sm10 > kGridSmemLimit;
@@ -206,37 +205,18 @@ static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typenam
   // centre the product rows when the last pass's leak (multiples of
   // nlon / last radix) falls inside the retained band
   const bool center = f.N / f.radix[f.npass - 1] <= p->T;
-  if (msplit > 0 && (longrows || !p->F2)) return fail(PFSH_EINVAL, "grid stage: split Fourier sums need F2");
-  const C *F2 = msplit > 0 ? (const C *)p->F2 : nullptr;
   return with_shape(f.N, [&]<typename Shape>() -> int {
-    if (longrows) {
-      auto kern = k_grid_rhs_long<Rl, Shape>;
-      int rc = set_smem((const void *)kern, sm);
-      if (rc) return rc;
-      {
-        PFSH_LAUNCH("k_grid_rhs_long", s);
-        if (pdl) {
-          cudaError_t e = launch_pdl(kern, dim3(p->nh, B), dim3(256), sm, s, f, p->T, p->nlat, B, (const C *)p->F,
-                                     rowf, tw, (C *)p->H, center);
-          if (e != cudaSuccess) return cuda_fail(e, "k_grid_rhs_long");
-        } else {
-          kern<<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw, (C *)p->H, center);
-        }
-      }
-    } else {
-      auto kern = k_grid_rhs<Rl, Shape>;
-      int rc = set_smem((const void *)kern, sm);
-      if (rc) return rc;
-      {
-        PFSH_LAUNCH("k_grid_rhs", s);
-        if (pdl) {
-          cudaError_t e = launch_pdl(kern, dim3(p->nh, B), dim3(256), sm, s, f, p->T, p->nlat, B, (const C *)p->F,
-                                     rowf, tw, (C *)p->H, center, F2, msplit);
-          if (e != cudaSuccess) return cuda_fail(e, "k_grid_rhs");
-        } else {
-          kern<<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw, (C *)p->H, center, F2,
-                                               msplit);
-        }
+    auto kern = longrows ? k_grid_rhs_long<Rl, Shape> : k_grid_rhs<Rl, Shape>;
+    int rc = set_smem((const void *)kern, sm);
+    if (rc) return rc;
+    {
+      PFSH_LAUNCH(longrows ? "k_grid_rhs_long" : "k_grid_rhs", s);
+      if (pdl) {
+        cudaError_t e = launch_pdl(kern, dim3(p->nh, B), dim3(256), sm, s, f, p->T, p->nlat, B, (const C *)p->F,
+                                   rowf, tw, (C *)p->H, center);
+        if (e != cudaSuccess) return cuda_fail(e, "k_grid_rhs");
+      } else {
+        kern<<<dim3(p->nh, B), 256, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw, (C *)p->H, center);
       }
     }
     PFSH_CHECK_LAUNCH("k_grid_rhs");
@@ -244,10 +224,10 @@ static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typenam
   });
 }
 
-int grid_rhs(const sht_plan *p, int B, const swe_params &, cudaStream_t s, bool pdl, int msplit) {
+int grid_rhs(const sht_plan *p, int B, const swe_params &, cudaStream_t s, bool pdl) {
   FftArgs f = fft_args(p->fft);
-  if (p->prec == PFSH_FP64) return grid_launch<double>(p, f, B, p->fft.tw64, p->d_rowf, s, pdl, msplit);
-  return grid_launch<float>(p, f, B, p->fft.tw32, p->d_rowf32, s, pdl, msplit);
+  if (p->prec == PFSH_FP64) return grid_launch<double>(p, f, B, p->fft.tw64, p->d_rowf, s, pdl);
+  return grid_launch<float>(p, f, B, p->fft.tw32, p->d_rowf32, s, pdl);
 }
 
 }  // namespace pfsh

@@ -429,16 +429,12 @@ __device__ __forceinline__ void grid_unpack(const C *Z, int N, int NP, int T, in
 // -> forward FFTs -> hemispheric sums/differences weighted by w_j.
 // F columns b*4 + f, H columns b*5 + f; smem holds 10 padded transforms.
 // Called by every thread of a block.
-// F2 (nullable): second partial Fourier sums of the orders m < msplit (the
-// coarse chain splits the synthesis of those orders over two blocks), added
-// to F on loading.
 template <typename Rl, typename Shape>
 __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat, int B, int j, int b,
                                               const typename cpx<Rl>::t *__restrict__ F, const Rl *__restrict__ rowf,
                                               const typename cpx<Rl>::t *__restrict__ tw,
                                               typename cpx<Rl>::t *__restrict__ H, typename cpx<Rl>::t *smem,
-                                              bool center, const typename cpx<Rl>::t *__restrict__ F2 = nullptr,
-                                              int msplit = 0) {
+                                              bool center) {
   typedef typename cpx<Rl>::t C;
   const int N = Shape::n(f), NP = padded(N);
   C *A = smem;            // 5 padded transforms
@@ -457,10 +453,6 @@ __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat,
     const int m = t >> 2, fld = t & 3;     // consecutive threads: the 4 fields of one m
     C fn = F[((size_t)m * nlat + j) * colsF + b * 4 + fld];
     C fs = F[((size_t)m * nlat + js) * colsF + b * 4 + fld];
-    if (F2 && m < msplit) {
-      fn = fn + F2[((size_t)m * nlat + j) * colsF + b * 4 + fld];
-      fs = fs + F2[((size_t)m * nlat + js) * colsF + b * 4 + fld];
-    }
     C *z = A + fld * NP;
     if (m == 0) {
       z[0] = mk<C>(fn.x, fs.x);

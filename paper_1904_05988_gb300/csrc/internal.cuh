@@ -225,9 +225,6 @@ struct sht_plan {
   // float otherwise): X [ne][cols], F [T+1][nlat][cols], H [T+1][2][nh][cols],
   // Y [ne][cols]
   void *X = nullptr, *F = nullptr, *H = nullptr, *Y = nullptr;
-  // coarse chain (small.cu): second Fourier buffer [T+1][nlat][4] for the
-  // orders whose synthesis two blocks share (allocated by chain_prepare)
-  void *F2 = nullptr;
 };
 
 struct swe_ctx {
@@ -370,7 +367,7 @@ bool uses_tensor_cores(int prec);
 int ifft_rows(const sht_plan *p, int cols, void *grid, cudaStream_t s);        // F -> grid
 int fft_rows(const sht_plan *p, int cols, const void *grid, cudaStream_t s);   // grid -> H
 int grid_rhs(const sht_plan *p, int B, const swe_params &prm, cudaStream_t s,
-             bool pdl = false, int msplit = 0);   // F (+ F2 for orders m < msplit) -> H (RHS)
+             bool pdl = false);   // F -> H (RHS)
 int ifft_rows_f64_raw(int N, int npass, const int *radix, int full, int T, int nlat, int cols, const double2 *F,
                       const double2 *tw, double *grid, cudaStream_t s);
 
@@ -404,8 +401,6 @@ void lagrange_matrix(const double *src, int ns, const double *dst, int nd, doubl
 int chain_sweeps(sdc_level *l, double *th, double *fe, double *fi, const double *tau, size_t node_stride,
                  size_t slice_stride, int n0, int n1, bool recv_first, cudaStream_t s,
                  cudaEvent_t after_first = nullptr);
-// allocates the plan's second Fourier buffer used by chain_sweeps (B = 1 plans)
-int chain_prepare(sht_plan *p);
 
 // PFASST transfer kernels
 int restrict_launch(const double *Rt, int nf, int nc, const double *xf, size_t fstride,

@@ -301,7 +301,6 @@ extern "C" int pfasst_create(pfasst **out, const pfasst_config *cfg) {
       (rc = sdc_level_create(&pf->lev_f, pf->ctx_f, c.fine_nodes, c.dt, nts)) ||
       (rc = sdc_level_create(&pf->lev_c, pf->ctx_c, c.coarse_nodes, c.dt, nts)) ||
       (rc = sht_plan_create(&pf->plan_cc, c.Tc, c.nlat_c, c.nlon_c, 5, c.prec)) ||
-      (rc = chain_prepare(pf->plan_cc)) ||
       (rc = swe_ctx_create(&pf->ctx_cc, pf->plan_cc, &c.phys)) ||
       (rc = sdc_level_create(&pf->lev_cc, pf->ctx_cc, c.coarse_nodes, c.dt, 1))) {
     pf_free(pf);

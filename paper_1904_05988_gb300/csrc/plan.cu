@@ -279,7 +279,6 @@ static void plan_free(sht_plan *p) {
   if (p->d_rowf32) cudaFree(p->d_rowf32);
   if (p->d_ilap32) cudaFree(p->d_ilap32);
   if (p->ws) cudaFree(p->ws);
-  if (p->F2) cudaFree(p->F2);
   fft_plan_free(p->fft);
   tc_tables_free(p);
   delete p;

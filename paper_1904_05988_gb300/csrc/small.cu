@@ -220,416 +220,6 @@ static int chain_node_launch(const ChainStep &st, ChainGeo<R> g, const SdcCoef &
   return PFSH_OK;
 }
 
-// ---------------------------------------------------------------------------
-// Step C with the low orders shared by two blocks
-// ---------------------------------------------------------------------------
-// The block of order m does work in proportion to the K = T + 2 - m degree
-// rows n = m..T+1 of the order, so a launch lasts as long as the low orders.
-// Orders m < msplit are therefore shared by two blocks: part 0 owns the rows
-// i = n - m in [0, h), part 1 the rows in [h, K) (h even, about K/2).  Each
-// block computes what its own rows need: the analysed rows of the previous
-// node for [i0 - 2, i1 + 2) (the assembly of row i reads rows i +- 1), F_E and
-// F_I for [i0 - 1, i1 + 1), the node update for the same rows (the velocity
-// recovery of row i reads the stream function and velocity potential at
-// i +- 1), and the synthesis sums over its own rows only, into F (part 0) or
-// F2 (part 1), which the grid stage adds.  Both blocks compute the shared
-// halo rows the same way (each row's latitude sum is split into the same
-// segments in every block of a launch) and each stores only its own rows.
-// The node-0 values of a slice that receives are read from the sender's
-// arrays (global) or, for F_E and F_I of the node analysed in the same
-// launch, from shared memory, never from locations another block writes in
-// the same launch.  Used for the one-solve node update with the Coriolis term
-// explicit (the banded solve couples all degrees of an order, and the
-// two-substep solve reads the node's old iterate, which the other block of
-// the order overwrites).
-struct ChainRange {
-  int m, part, K;
-  int i0, i1;   // own rows
-  int u0, u1;   // rows whose F_E, F_I and updated state the block needs (coefficient rows, i <= K - 2)
-  int a0, a1;   // analysed rows
-};
-
-__host__ __device__ inline int chain_split_point(int K) { return ((K + 1) / 2 + 1) & ~1; }
-
-__host__ __device__ inline ChainRange chain_range(int T, int msplit, int bid) {
-  ChainRange r;
-  r.m = bid <= T ? bid : bid - (T + 1);
-  r.part = bid <= T ? 0 : 1;
-  r.K = T + 2 - r.m;
-  if (r.m < msplit) {
-    const int h = chain_split_point(r.K);
-    r.i0 = r.part ? h : 0;
-    r.i1 = r.part ? r.K : h;
-  } else {
-    r.i0 = 0;
-    r.i1 = r.K;
-  }
-  r.u0 = r.i0 > 0 ? r.i0 - 1 : 0;
-  r.u1 = r.i1 + 1 < r.K - 1 ? r.i1 + 1 : r.K - 1;
-  r.a0 = r.u0 > 0 ? r.u0 - 1 : 0;
-  r.a1 = r.u1 + 1 < r.K ? r.u1 + 1 : r.K;
-  return r;
-}
-
-template <typename R>
-struct SplitGeo {
-  int T, nlat, msplit;
-  int rows;          // Legendre rows staged at once (even)
-  int kw, S;         // analysis: rows per latitude group, latitude segments (fixed per launch)
-  int UL;            // stride of the per-block coefficient-row arrays (>= max u1 - u0)
-  int YL;            // rows of the analysed-row array (>= max a1 - a0)
-  int XL;            // rows of the synthesis input array (>= max i1 - i0)
-  size_t o_work, o_per;   // byte offsets: work region (union of analysis / synthesis), persistent arrays
-  R ma2, inva, inva2;
-  double dinva2, omega, nu, phibar;
-  SpecTables<R> tb;
-  const R *P;
-  typename cpx<R>::t *F, *F2;
-  const typename cpx<R>::t *H;
-};
-
-template <typename R>
-__global__ void __launch_bounds__(kChainThreads, 2) k_chain_split(ChainStep st, SplitGeo<R> g, SdcCoef c) {
-  typedef typename cpx<R>::t C;
-  extern __shared__ __align__(16) unsigned char smem_raw[];
-  const int T = g.T, nlat = g.nlat, nh = nlat / 2, ld = nh + 1, nc = ncoef_of(T);
-  const ChainRange rg = chain_range(T, g.msplit, blockIdx.x);
-  const int m = rg.m, UL = g.UL;
-  R *Pst = reinterpret_cast<R *>(smem_raw);
-  unsigned char *work = smem_raw + g.o_work;
-  double2 *per = reinterpret_cast<double2 *>(smem_raw + g.o_per);
-  double2 *feS = per, *fiS = per + 3 * UL, *O1S = per + 6 * UL, *thk = per + 9 * UL;   // [3][UL] each
-  const bool anal = st.a_th != nullptr;
-  const R *Pm = g.P + (size_t)eoff(T, m) * nh;
-  const int p0 = poff(T, m);
-  const size_t e0 = (size_t)poff(T + 1, m);   // extended-triangle row of (m, m)
-  // independent prologue: the first rows this block reads
-  const int s0 = anal ? rg.a0 : rg.i0, s1 = anal ? rg.a1 : rg.i1;
-  stage_rows_async(Pst, Pm + (size_t)s0 * nh, min(g.rows, s1 - s0), nh);
-  pdl_wait();
-  bool staged_all = s1 - s0 <= g.rows;   // Pst holds rows [s0, s1)
-  if (anal) {
-    // 1. analysis of rows [a0, a1) of the node st.a_th
-    C *Ys = reinterpret_cast<C *>(work);                                   // [YL][5]
-    C *Hs = Ys + (size_t)g.YL * 5;                                         // [2][nh][5]
-    C *Ws = Hs + (size_t)2 * nh * 5;                                       // [threads][5]
-    stage_async(Hs, g.H + (size_t)m * 2 * nh * 5, 2 * nh * 5);
-    for (int c0 = rg.a0; c0 < rg.a1; c0 += g.rows) {
-      const int cl = min(g.rows, rg.a1 - c0);
-      if (c0 != rg.a0) {
-        __syncthreads();
-        stage_rows_async(Pst, Pm + (size_t)c0 * nh, cl, nh);
-      }
-      stage_wait();
-      const int t = threadIdx.x, s = t / g.kw, il = t - s * g.kw;
-      if (s < g.S && il < cl) {
-        const int i = c0 + il, par = i & 1;
-        const int j0 = (int)(((long)nh * s) / g.S), j1 = (int)(((long)nh * (s + 1)) / g.S);
-        const C *h = Hs + (size_t)par * nh * 5;
-        const R *pr = Pst + (size_t)il * ld;
-        C acc[5];
-#pragma unroll
-        for (int f = 0; f < 5; ++f) acc[f] = mk<C>(0.0, 0.0);
-        for (int j = j0; j < j1; ++j) {
-          const R pv = pr[j];
-#pragma unroll
-          for (int f = 0; f < 5; ++f) {
-            const C v = h[(size_t)j * 5 + f];
-            acc[f].x += pv * v.x;
-            acc[f].y += pv * v.y;
-          }
-        }
-#pragma unroll
-        for (int f = 0; f < 5; ++f) Ws[(size_t)t * 5 + f] = acc[f];
-      }
-      __syncthreads();
-      for (int u = threadIdx.x; u < cl * 5; u += blockDim.x) {
-        const int il2 = u / 5, f = u - il2 * 5;
-        C a = mk<C>(0.0, 0.0);
-        for (int s2 = 0; s2 < g.S; ++s2) a = a + Ws[(size_t)(s2 * g.kw + il2) * 5 + f];
-        Ys[(size_t)(c0 - rg.a0 + il2) * 5 + f] = a;
-      }
-    }
-    __syncthreads();
-    // 2. F_E and F_I of rows [u0, u1) (shared memory), own rows also stored
-    for (int t = threadIdx.x; t < rg.u1 - rg.u0; t += blockDim.x) {
-      const int i = rg.u0 + t, n = m + i;
-      C cur[5], up[5], dn[5];
-#pragma unroll
-      for (int f = 0; f < 5; ++f) {
-        cur[f] = Ys[(size_t)(i - rg.a0) * 5 + f];
-        up[f] = Ys[(size_t)(i + 1 - rg.a0) * 5 + f];
-        dn[f] = i ? Ys[(size_t)(i - 1 - rg.a0) * 5 + f] : mk<C>(0.0, 0.0);
-      }
-      double2 fe[3], fi[3];
-      assemble_point<R, C>(m, n, cur, up, dn, i > 0, g.tb.eps[e0 + i + 1], g.tb.eps[e0 + i], g.inva, g.inva2, fe);
-      const size_t idx = (size_t)p0 + i;
-      linear_vals(m, n, T, st.a_th, nc, idx, g.dinva2, g.nu, g.phibar, CorArgs{nullptr, 0.0}, fi);
-      const bool own = i >= rg.i0 && i < rg.i1;
-#pragma unroll
-      for (int f = 0; f < 3; ++f) {
-        feS[f * UL + t] = fe[f];
-        fiS[f * UL + t] = fi[f];
-        if (own) {
-          st.a_fe[(size_t)f * nc + idx] = fe[f];
-          st.a_fi[(size_t)f * nc + idx] = fi[f];
-        }
-      }
-    }
-    __syncthreads();
-    staged_all = rg.a1 - rg.a0 <= g.rows;   // rows [a0, a1) are all in Pst
-  }
-  if (st.k == 0) {
-    if (!anal) stage_wait();
-    return;
-  }
-  const int K1 = rg.K - 1;   // coefficient rows i < K1 (n <= T)
-  const int c0r = rg.i0, c1r = min(rg.i1, K1);   // own coefficient rows
-  // 3. receive: own coefficient rows of node 0 from the sender's last node
-  if (st.r_th) {
-    for (int t = threadIdx.x; t < 3 * (c1r - c0r); t += blockDim.x) {
-      const int f = t / (c1r - c0r);
-      const size_t e = (size_t)f * nc + p0 + c0r + (t - f * (c1r - c0r));
-      st.th[e] = st.r_th[e];
-      st.fe[e] = st.r_fe[e];
-      st.fi[e] = st.r_fi[e];
-    }
-  }
-  const int M = st.M, k = st.k;
-  // node-0 sources for this launch (never a location another block writes now)
-  const double2 *th0 = st.r_th ? st.r_th : st.th;
-  const double2 *fe0 = st.r_fe ? st.r_fe : st.fe;
-  const double2 *fi0 = st.r_fi ? st.r_fi : st.fi;
-  // 4. old parts O_i (i = 1..M) of rows [u0, u1) at the first node; own rows stored
-  if (k == 1) {
-    for (int t = threadIdx.x; t < 3 * (rg.u1 - rg.u0); t += blockDim.x) {
-      const int f = t / (rg.u1 - rg.u0), tt = t - f * (rg.u1 - rg.u0), i = rg.u0 + tt;
-      const size_t e = (size_t)f * nc + p0 + i;
-      double2 acc[9];
-      const double2 t0 = th0[e];
-#pragma unroll
-      for (int q = 1; q <= 8; ++q)
-        if (q <= M) acc[q] = st.tau ? t0 + st.tau[(size_t)q * st.ns + e] : t0;
-#pragma unroll
-      for (int j = 0; j <= 8; ++j) {
-        if (j > M) break;
-        double2 a, fv;
-        if (j == 0) {
-          a = anal ? feS[f * UL + tt] : fe0[e];
-          fv = anal ? fiS[f * UL + tt] : fi0[e];
-        } else {
-          a = st.fe[(size_t)j * st.ns + e];
-          fv = st.fi[(size_t)j * st.ns + e];
-        }
-        const double2 sj = make_double2(a.x + fv.x, a.y + fv.y);
-#pragma unroll
-        for (int q = 1; q <= 8; ++q)
-          if (q <= M) {
-            if (j == 0 || j > q) {
-              acc[q].x = fma(c.cE[q][j], sj.x, acc[q].x);
-              acc[q].y = fma(c.cE[q][j], sj.y, acc[q].y);
-            } else {
-              acc[q].x = fma(c.cI[q][j], fv.x, fma(c.cE[q][j], a.x, acc[q].x));
-              acc[q].y = fma(c.cI[q][j], fv.y, fma(c.cE[q][j], a.y, acc[q].y));
-            }
-          }
-      }
-      O1S[f * UL + tt] = acc[1];
-      if (i >= c0r && i < c1r)
-#pragma unroll
-        for (int q = 1; q <= 8; ++q)
-          if (q <= M) st.O[(size_t)(q - 1) * 3 * nc + e] = acc[q];
-    }
-    __syncthreads();
-  }
-  // 5. node update of node k for rows [u0, u1): one solve per coefficient
-  for (int tt = threadIdx.x; tt < rg.u1 - rg.u0; tt += blockDim.x) {
-    const int i = rg.u0 + tt, n = m + i;
-    const size_t idx = (size_t)p0 + i;
-    double2 r[3];
-    for (int f = 0; f < 3; ++f) {
-      const size_t e = (size_t)f * nc + idx;
-      double2 v = k == 1 ? O1S[f * UL + tt] : st.O[(size_t)(k - 1) * 3 * nc + e];
-      for (int j = 1; j < k; ++j) {
-        const bool here = anal && j == k - 1;
-        const double2 a = here ? feS[f * UL + tt] : st.fe[(size_t)j * st.ns + e];
-        const double2 gi = here ? fiS[f * UL + tt] : st.fi[(size_t)j * st.ns + e];
-        v.x = fma(c.nI[k][j], gi.x, fma(c.nE[k][j], a.x, v.x));
-        v.y = fma(c.nI[k][j], gi.y, fma(c.nE[k][j], a.y, v.y));
-      }
-      r[f] = v;
-    }
-    const double4_32a q = st.fac[n];
-    const double2 x0 = make_double2((q.x * r[0].x - st.hphibar * r[2].x) * q.z, (q.x * r[0].y - st.hphibar * r[2].y) * q.z);
-    const double2 x1 = make_double2(r[1].x * q.y, r[1].y * q.y);
-    const double2 x2 = make_double2((q.x * r[2].x + q.w * r[0].x) * q.z, (q.x * r[2].y + q.w * r[0].y) * q.z);
-    thk[tt] = x0;
-    thk[UL + tt] = x1;
-    thk[2 * UL + tt] = x2;
-    if (i >= c0r && i < c1r) {
-      double2 *out = st.th + (size_t)k * st.ns;
-      out[idx] = x0;
-      out[nc + idx] = x1;
-      out[2 * nc + idx] = x2;
-    }
-  }
-  __syncthreads();
-  // 6. velocity recovery of the own rows and their synthesis sums
-  C *Xs = reinterpret_cast<C *>(work);                                      // [XL][4]
-  const int parts = max(1, (int)blockDim.x / nh);
-  C *Ps = Xs + (size_t)g.XL * 4;                                            // [parts][nh][2][4]
-  const int nown = rg.i1 - rg.i0;
-  for (int t = threadIdx.x; t < nown; t += blockDim.x) {
-    const int i = rg.i0 + t;
-    prep_point<R>(T, m, m + i, thk, thk + UL, thk + 2 * UL, -m - rg.u0, e0 + i, g.tb, g.ma2, g.inva, g.omega,
-                  g.phibar, Xs + (size_t)t * 4);
-  }
-  for (int t = threadIdx.x; t < parts * nh * 2 * 4; t += blockDim.x) Ps[t] = mk<C>(0.0, 0.0);
-  // rows [i0, i1) in Pst: reuse the analysis staging when it holds them, else stage
-  int pbase;   // row of Pst[0]
-  if (!anal) {
-    stage_wait();   // prologue rows [i0, ...)
-    pbase = rg.i0;
-  } else if (staged_all) {
-    __syncthreads();
-    pbase = rg.a0;
-  } else {
-    __syncthreads();
-    stage_rows_async(Pst, Pm + (size_t)rg.i0 * nh, min(g.rows, nown), nh);
-    stage_wait();
-    pbase = rg.i0;
-  }
-  for (int c0 = 0; c0 < nown; c0 += g.rows) {
-    const int cl = min(g.rows, nown - c0);
-    if (c0 > 0) {
-      __syncthreads();
-      stage_rows_async(Pst, Pm + (size_t)(rg.i0 + c0) * nh, cl, nh);
-      stage_wait();
-      pbase = rg.i0 + c0;
-    }
-    const int Kc = ((cl + parts - 1) / parts + 1) & ~1;   // even
-    for (int t = threadIdx.x; t < nh * parts; t += blockDim.x) {
-      const int j = t % nh, pp = t / nh;
-      const int q0 = pp * Kc, q1 = min(cl, q0 + Kc);
-      C e[4], o[4];
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) e[cc] = o[cc] = mk<C>(0.0, 0.0);
-      for (int q = q0; q < q1; q += 2) {
-        const int i = rg.i0 + c0 + q;              // even relative to the order's first row
-        const R pe = Pst[(size_t)(i - pbase) * ld + j];
-        const bool odd = q + 1 < q1;
-        const R po = odd ? Pst[(size_t)(i + 1 - pbase) * ld + j] : (R)0;
-        const C *xe = Xs + (size_t)(c0 + q) * 4, *xo = xe + 4;
-#pragma unroll
-        for (int cc = 0; cc < 4; ++cc) {
-          const C u = xe[cc];
-          e[cc].x += pe * u.x;
-          e[cc].y += pe * u.y;
-          if (odd) {
-            const C v = xo[cc];
-            o[cc].x += po * v.x;
-            o[cc].y += po * v.y;
-          }
-        }
-      }
-      C *ps = Ps + ((size_t)pp * nh + j) * 8;
-#pragma unroll
-      for (int cc = 0; cc < 4; ++cc) {
-        ps[cc] = ps[cc] + e[cc];
-        ps[4 + cc] = ps[4 + cc] + o[cc];
-      }
-    }
-  }
-  __syncthreads();
-  C *Fo = rg.part ? g.F2 : g.F;
-  for (int t = threadIdx.x; t < nh * 4; t += blockDim.x) {
-    const int j = t / 4, cc = t - j * 4;
-    C E = mk<C>(0.0, 0.0), O = mk<C>(0.0, 0.0);
-    for (int pp = 0; pp < parts; ++pp) {
-      const C *ps = Ps + ((size_t)pp * nh + j) * 8;
-      E = E + ps[cc];
-      O = O + ps[4 + cc];
-    }
-    Fo[((size_t)m * nlat + j) * 4 + cc] = E + O;
-    Fo[((size_t)m * nlat + (nlat - 1 - j)) * 4 + cc] = E - O;
-  }
-}
-
-// launch geometry of k_chain_split: per-block ranges, staging rows, offsets
-template <typename R>
-static SplitGeo<R> split_geo(const ChainGeo<R> &cg, const sht_plan *p, size_t budget) {
-  typedef typename cpx<R>::t C;
-  SplitGeo<R> g{};
-  const int T = cg.T, nh = cg.nlat / 2;
-  g.T = T;
-  g.nlat = cg.nlat;
-  // orders with more rows than about half of order 0's are shared by two blocks
-  int ms = 0;
-  while (ms <= T && T + 2 - ms > (T + 2) / 2 + 2) ++ms;
-  g.msplit = ms;
-  int UL = 0, YL = 0, XL = 0;
-  for (int b = 0; b < T + 1 + ms; ++b) {
-    const ChainRange r = chain_range(T, ms, b);
-    UL = std::max(UL, r.u1 - r.u0);
-    YL = std::max(YL, r.a1 - r.a0);
-    XL = std::max(XL, r.i1 - r.i0);
-  }
-  g.UL = std::max(UL, 1);
-  g.YL = YL;
-  g.XL = XL;
-  const int parts = std::max(1, kChainThreads / nh);
-  const size_t per = align16((size_t)12 * g.UL * sizeof(double2));
-  const size_t w_an = align16((size_t)g.YL * 5 * sizeof(C)) + align16((size_t)2 * nh * 5 * sizeof(C)) +
-                      align16((size_t)kChainThreads * 5 * sizeof(C));
-  const size_t w_sy = align16((size_t)g.XL * 4 * sizeof(C)) + align16((size_t)parts * nh * 2 * 4 * sizeof(C));
-  const size_t w = std::max(w_an, w_sy);
-  g.rows = small_stage_rows<R>(w + per, T, cg.nlat, budget);
-  g.rows = std::min(g.rows, (YL + 1) & ~1);
-  if (g.rows < 2) g.rows = 2;
-  g.o_work = small_stage_bytes<R>(cg.nlat, g.rows);
-  g.o_per = g.o_work + w;
-  g.kw = (std::min(g.rows, YL) + 31) & ~31;
-  g.S = std::max(1, std::min(kChainThreads / g.kw, nh));
-  g.ma2 = cg.ma2;
-  g.inva = cg.inva;
-  g.inva2 = cg.inva2;
-  g.dinva2 = cg.dinva2;
-  g.omega = cg.omega;
-  g.nu = cg.nu;
-  g.phibar = cg.phibar;
-  g.tb = cg.tb;
-  g.P = cg.P;
-  g.F = cg.F;
-  g.F2 = (C *)p->F2;
-  g.H = cg.H;
-  return g;
-}
-
-template <typename R>
-static size_t split_smem(const SplitGeo<R> &g) {
-  return g.o_per + align16((size_t)12 * g.UL * sizeof(double2));
-}
-
-template <typename R>
-static int chain_split_launch(const ChainStep &st, const SplitGeo<R> &g, const SdcCoef &c, cudaStream_t s,
-                              bool pdl) {
-  const size_t smem = split_smem(g);
-  int rc = ensure_smem((const void *)k_chain_split<R>, smem);
-  if (rc) return rc;
-  const int blocks = g.T + 1 + g.msplit;
-  {
-    PFSH_LAUNCH("k_chain_node", s);
-    if (pdl) {
-      cudaError_t e = launch_pdl(k_chain_split<R>, dim3(blocks), dim3(kChainThreads), smem, s, st, g, c);
-      if (e != cudaSuccess) return cuda_fail(e, "k_chain_node");
-    } else {
-      k_chain_split<R><<<blocks, kChainThreads, smem, s>>>(st, g, c);
-    }
-  }
-  PFSH_CHECK_LAUNCH("k_chain_node");
-  return PFSH_OK;
-}
-
 template <typename R>
 static ChainGeo<R> chain_geo(const swe_ctx *ctx, const R *P, SpecTables<R> tb) {
   typedef typename cpx<R>::t C;
@@ -652,14 +242,6 @@ static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, doub
   double2 *TH = (double2 *)th, *FE = (double2 *)fe, *FI = (double2 *)fi;
   const double2 *TAU = (const double2 *)tau;
   int rc;
-  // the low orders shared by two blocks: one-solve node update, Coriolis term explicit
-  const bool split = p->F2 && !g.split && g.cor.tw == 0.0;
-  SplitGeo<R> sg{};
-  if (split) sg = split_geo<R>(g, p, kChainBudget);
-  const int msplit = split ? sg.msplit : 0;
-  auto step = [&](const ChainStep &cs, bool pdl) {
-    return split ? chain_split_launch<R>(cs, sg, c, s, pdl) : chain_node_launch<R>(cs, g, c, s, pdl);
-  };
   for (int n = n0; n < n1; ++n) {
     for (int k = 1; k <= M; ++k) {
       ChainStep st = {};
@@ -691,9 +273,9 @@ static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, doub
         st.r_fi = FI + (n - 1) * ss + M * ns;
       }
       // the first launch of the chain follows other work of the stream
-      if ((rc = step(st, n > n0 || k > 1))) return rc;
+      if ((rc = chain_node_launch<R>(st, g, c, s, n > n0 || k > 1))) return rc;
       if (after_first && n == n0 && k == 1) PFSH_CUDA(cudaEventRecord(after_first, s));
-      if ((rc = grid_rhs(p, 1, ctx->prm, s, true, msplit))) return rc;
+      if ((rc = grid_rhs(p, 1, ctx->prm, s, true))) return rc;
     }
   }
   if (n1 > n0) {   // analysis of the last slice's last node
@@ -701,20 +283,8 @@ static int chain_typed(sdc_level *l, ChainGeo<R> g, double *th, double *fe, doub
     st.a_th = TH + (n1 - 1) * ss + M * ns;
     st.a_fe = FE + (n1 - 1) * ss + M * ns;
     st.a_fi = FI + (n1 - 1) * ss + M * ns;
-    if ((rc = step(st, true))) return rc;
+    if ((rc = chain_node_launch<R>(st, g, c, s, true))) return rc;
   }
-  return PFSH_OK;
-}
-
-int chain_prepare(sht_plan *p) {
-  if (p->F2) return PFSH_OK;
-  const size_t bytes = (size_t)(p->T + 1) * p->nlat * 4 * (p->prec == PFSH_FP64 ? 16 : 8);
-  if (cudaMalloc(&p->F2, bytes) != cudaSuccess) {
-    cudaGetLastError();
-    p->F2 = nullptr;
-    return fail(PFSH_ENOMEM, "chain_prepare: second Fourier buffer");
-  }
-  p->device_bytes += bytes;
   return PFSH_OK;
 }
 

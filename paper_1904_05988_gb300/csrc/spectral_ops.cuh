@@ -108,10 +108,10 @@ __device__ __forceinline__ void assemble_point(int m, int n, const C cur[5], con
   if (m == 0) { fe[0].y = 0.0; fe[1].y = 0.0; fe[2].y = 0.0; }
 }
 
-// F_I = L(state) (+ C(state) when cor.tw != 0) at packed index idx (always
-// double): the three values, and stored at oI[idx + f nc]
-__device__ __forceinline__ void linear_vals(int m, int n, int T, const double2 *__restrict__ st, int nc, size_t idx,
-                                            double inva2, double nu, double phibar, CorArgs cor, double2 o[3]) {
+// F_I = L(state) (+ C(state) when cor.tw != 0) at packed index idx (always double)
+__device__ __forceinline__ void linear_point(int m, int n, int T, const double2 *__restrict__ st, int nc, size_t idx,
+                                             double inva2, double nu, double phibar, CorArgs cor,
+                                             double2 *__restrict__ oI) {
   double2 Phi = st[idx], zeta = st[nc + idx], delta = st[2 * nc + idx];
   if (m == 0) { Phi.y = 0.0; zeta.y = 0.0; delta.y = 0.0; }
   const double k = (double)n * (n + 1) * inva2, nk = nu * k;
@@ -123,18 +123,9 @@ __device__ __forceinline__ void linear_vals(int m, int n, int T, const double2 *
     oz.x += cz.x; oz.y += cz.y;
     od.x += cd.x; od.y += cd.y;
   }
-  o[0] = make_double2(-phibar * delta.x - nk * Phi.x, -phibar * delta.y - nk * Phi.y);
-  o[1] = oz;
-  o[2] = od;
-}
-__device__ __forceinline__ void linear_point(int m, int n, int T, const double2 *__restrict__ st, int nc, size_t idx,
-                                             double inva2, double nu, double phibar, CorArgs cor,
-                                             double2 *__restrict__ oI) {
-  double2 o[3];
-  linear_vals(m, n, T, st, nc, idx, inva2, nu, phibar, cor, o);
-  oI[idx] = o[0];
-  oI[nc + idx] = o[1];
-  oI[2 * nc + idx] = o[2];
+  oI[idx] = make_double2(-phibar * delta.x - nk * Phi.x, -phibar * delta.y - nk * Phi.y);
+  oI[nc + idx] = oz;
+  oI[2 * nc + idx] = od;
 }
 
 }  // namespace pfsh
