@@ -64,6 +64,13 @@ def legendre_flops(T: int, nlat: int, cols_complex: int) -> float:
     return 4.0 * (nlat // 2) * K * cols_complex
 
 
+def grid_long_rows(nlon: int, elem: int) -> bool:
+    """True when the grid stage of rows of nlon points takes the long-row
+    kernel: 10 padded transforms (nlon + nlon/16 + 1 complex entries each)
+    exceed the 227 KB of shared memory of a block."""
+    return 10 * (nlon + nlon // 16 + 1) * 2 * elem > 227 * 1024
+
+
 def grid_rhs_bytes(T: int, nlat: int, B: int, elem: int) -> float:
     """HBM bytes of the fused FFT/grid kernel: read 4 spectra (m <= T) of every
     latitude, write 5 hemispheric spectra, complex of `elem`-byte reals."""
@@ -592,8 +599,10 @@ def kernel_work_per_iteration(name: str, prec: str, W: Workload = HEADLINE):
         cols = 4 if "synth" in name else 5
         return ncs * legendre_flops(TC, nlat_c, cols), "flop", simt_bound, None
     if name in ("k_grid_rhs", "k_grid_rhs_long"):
-        return (nfs * grid_rhs_bytes(TF, nlat_f, 1, elem) + (ncb + ncs) * grid_rhs_bytes(TC, nlat_c, 1, elem),
-                "byte", ("hbm", None), None)
+        want = name == "k_grid_rhs_long"
+        w = (nfs * grid_rhs_bytes(TF, nlat_f, 1, elem) * (grid_long_rows(GRID_F[1], elem) == want) +
+             (ncb + ncs) * grid_rhs_bytes(TC, nlat_c, 1, elem) * (grid_long_rows(GRID_C[1], elem) == want))
+        return w, "byte", ("hbm", None), None
     if name == "k_rhs_prep":
         return (nfs * (st_f + 4 * ncf1 * 2 * elem) + ncb * (st_c + 4 * ncc1 * 2 * elem), "byte", ("hbm", None), None)
     if name == "k_rhs_assemble":

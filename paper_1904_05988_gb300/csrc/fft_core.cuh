@@ -274,6 +274,14 @@ template <int N, int Ns, int OFF, int R, int... Rs> struct PassList<N, Ns, OFF, 
   }
 };
 
+// the same pass list with the first pass pruned (inverse, Ns = 1: no twiddles)
+template <int N, int R, int... Rs> struct PassListP {
+  template <typename C> static __device__ __forceinline__ C *run(C *a, C *b, int nfft, int T, const C *tw) {
+    pass_first_pruned<R, N>(a, b, nfft, T);
+    return PassList<N, R, R, Rs...>::run(b, a, nfft, tw, true);
+  }
+};
+
 template <int N_, int... Rs> struct ShapeCT {
   static constexpr bool kCT = true;
   static __host__ __device__ int n(const FftArgs &) { return N_; }
@@ -284,6 +292,11 @@ template <int N_, int... Rs> struct ShapeCT {
   template <typename C>
   static __device__ __forceinline__ C *run(const FftArgs &, C *a, C *b, int nfft, const C *tw, bool inv) {
     return PassList<N_, 1, 0, Rs...>::run(a, b, nfft, tw, inv);
+  }
+  // inverse transforms whose entries T < e < N - T are zero (never read)
+  template <typename C>
+  static __device__ __forceinline__ C *inverse_pruned(C *a, C *b, int nfft, int T, const C *tw) {
+    return PassListP<N_, Rs...>::run(a, b, nfft, T, tw);
   }
 };
 
@@ -511,10 +524,44 @@ __device__ __forceinline__ void grid_rhs_body(const FftArgs &f, int T, int nlat,
   grid_unpack<C, Rl>(Z, N, NP, T, j, nlat, colsH, b, rowf, H, center);
 }
 
-// The same grid stage for long rows (shared memory for 6 instead of 10
-// padded transforms): the 4 inverse transforms stay resident in G, then the
-// 5 products are formed, transformed and unpacked one after the other in the
-// two work buffers W0/W1.  Same arithmetic per element as grid_rhs_body.
+// Unpack of nf forward-transformed product rows Z (stride NP) holding fields
+// f0 .. f0+nf-1: the same arithmetic per entry as grid_unpack, no barrier.
+template <typename C, typename Rl>
+__device__ __forceinline__ void grid_unpack_range(const C *Z, int f0, int nf, int N, int NP, int T, int j, int nlat,
+                                                  int colsH, int b, const Rl *__restrict__ rowf,
+                                                  C *__restrict__ H, bool center) {
+  const Rl half = (Rl)0.5 / (Rl)N;
+  const Rl wj = rowf[2 * j + 1];
+  const int nh = nlat / 2;
+  for (int t = threadIdx.x; t < nf * (T + 1); t += blockDim.x) {
+    const int m = t / nf, q = t - nf * m;
+    const C *z = Z + q * NP;
+    C zm = z[sidx(m)];
+    C zc = cconj(z[sidx(m == 0 ? 0 : N - m)]);
+    if (center && m == 0) {
+      const C dc = (Rl)N * z[NP - 1];
+      zm = zm + dc;
+      zc = zc + cconj(dc);
+    }
+    C gn = half * (zm + zc);
+    C gs = half * times_i(zc - zm);
+    C he = wj * (gn + gs), ho = wj * (gn - gs);
+    H[(((size_t)m * 2 + 0) * nh + j) * colsH + b * 5 + f0 + q] = he;
+    H[(((size_t)m * 2 + 1) * nh + j) * colsH + b * 5 + f0 + q] = ho;
+  }
+}
+
+// The same grid stage for long rows, in shared memory for 6 instead of 10
+// padded transforms (slots S0..S5):
+//   1. the 4 spectra into S0..S3, inverse-transformed two at a time with
+//      S4/S5 as the ping-pong pair (the first pass skips the zero band
+//      T < e < N - T on compile-time shapes);
+//   2. the 5 products formed once, in place, into S0..S4 (every thread reads
+//      the 4 rows at the entries it writes), row means taken out when
+//      `center`;
+//   3. product 4 transformed with S5 as its work buffer and unpacked, then
+//      products 0/1 and 2/3 in pairs with S4/S5 as the work pair.
+// Same arithmetic per element as grid_rhs_body.
 template <typename Rl, typename Shape>
 __device__ __forceinline__ void grid_rhs_body_long(const FftArgs &f, int T, int nlat, int B, int j, int b,
                                                    const typename cpx<Rl>::t *__restrict__ F,
@@ -524,75 +571,85 @@ __device__ __forceinline__ void grid_rhs_body_long(const FftArgs &f, int T, int 
                                                    bool center) {
   typedef typename cpx<Rl>::t C;
   const int N = Shape::n(f), NP = padded(N);
-  C *G = smem;             // 4 padded transforms
-  C *W0 = G + 4 * NP, *W1 = W0 + NP;
+  C *S = smem;
+  C *W = S + 4 * NP;
   const int js = nlat - 1 - j;
   const int colsF = 4 * B, colsH = 5 * B;
-  for (int fld = 0; fld < 4; ++fld) {
-    C *z = G + fld * NP;
-    for (int t = threadIdx.x; t < NP; t += blockDim.x) z[t] = mk<C>(0.0, 0.0);
+  if constexpr (!Shape::kCT) {
+    for (int t = threadIdx.x; t < 4 * NP; t += blockDim.x) S[t] = mk<C>(0.0, 0.0);
     __syncthreads();
-    for (int m = threadIdx.x; m <= T; m += blockDim.x) {
-      C fn = F[((size_t)m * nlat + j) * colsF + b * 4 + fld];
-      C fs = F[((size_t)m * nlat + js) * colsF + b * 4 + fld];
-      if (m == 0) {
-        z[0] = mk<C>(fn.x, fs.x);
-      } else {
-        z[sidx(m)] = mk<C>(fn.x - fs.y, fn.y + fs.x);
-        z[sidx(N - m)] = mk<C>(fn.x + fs.y, -fn.y + fs.x);
-      }
+  }
+  for (int t = threadIdx.x; t < 4 * (T + 1); t += blockDim.x) {
+    const int fld = t / (T + 1), m = t - fld * (T + 1);
+    C *z = S + fld * NP;
+    C fn = F[((size_t)m * nlat + j) * colsF + b * 4 + fld];
+    C fs = F[((size_t)m * nlat + js) * colsF + b * 4 + fld];
+    if (m == 0) {
+      z[0] = mk<C>(fn.x, fs.x);
+    } else {
+      z[sidx(m)] = mk<C>(fn.x - fs.y, fn.y + fs.x);
+      z[sidx(N - m)] = mk<C>(fn.x + fs.y, -fn.y + fs.x);
     }
-    __syncthreads();
-    C *r = Shape::run(f, z, W0, 1, tw, true);
-    if (r != z) {
-      for (int k = threadIdx.x; k < N; k += blockDim.x) z[sidx(k)] = r[sidx(k)];
+  }
+  __syncthreads();
+#pragma unroll
+  for (int pr = 0; pr < 4; pr += 2) {
+    C *a = S + pr * NP;
+    C *r;
+    if constexpr (Shape::kCT)
+      r = Shape::inverse_pruned(a, W, 2, T, tw);
+    else
+      r = Shape::run(f, a, W, 2, tw, true);
+    if (r != a) {
+      for (int t = threadIdx.x; t < 2 * NP; t += blockDim.x) a[t] = r[t];
       __syncthreads();
     }
   }
   const Rl inv = rowf[2 * j];                // 1/(1 - mu_j^2)
   const Rl h = (Rl)0.5 * inv;
-  const Rl half = (Rl)0.5 / (Rl)N;
-  const Rl wj = rowf[2 * j + 1];
-  const int nh = nlat / 2;
-  for (int fld = 0; fld < 5; ++fld) {
-    C mean[1] = {mk<C>(0.0, 0.0)};
-    if (center) {
-      Rl sx[1] = {(Rl)0}, sy[1] = {(Rl)0};
-      for (int k = threadIdx.x; k < N; k += blockDim.x) {
-        const int e = sidx(k);
-        C pr[5];
-        grid_products<C, Rl>(G[e], G[NP + e], G[2 * NP + e], G[3 * NP + e], inv, h, pr);
-        sx[0] += pr[fld].x;
-        sy[0] += pr[fld].y;
-      }
-      block_means<C, 1>(sx, sy, N, W0, mean);
+  Rl sx[5], sy[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) sx[q] = sy[q] = (Rl)0;
+  for (int k = threadIdx.x; k < N; k += blockDim.x) {
+    const int e = sidx(k);
+    C pr[5];
+    grid_products<C, Rl>(S[e], S[NP + e], S[2 * NP + e], S[3 * NP + e], inv, h, pr);
+#pragma unroll
+    for (int q = 0; q < 5; ++q) {
+      S[q * NP + e] = pr[q];
+      sx[q] += pr[q].x;
+      sy[q] += pr[q].y;
     }
+  }
+  C mean[5];
+#pragma unroll
+  for (int q = 0; q < 5; ++q) mean[q] = mk<C>(0.0, 0.0);
+  if (center) {
+    block_means<C, 5>(sx, sy, N, W + NP, mean);
     for (int k = threadIdx.x; k < N; k += blockDim.x) {
       const int e = sidx(k);
-      C pr[5];
-      grid_products<C, Rl>(G[e], G[NP + e], G[2 * NP + e], G[3 * NP + e], inv, h, pr);
-      W0[e] = pr[fld] - mean[0];
+#pragma unroll
+      for (int q = 0; q < 5; ++q) S[q * NP + e] = S[q * NP + e] - mean[q];
     }
+  }
+  if (threadIdx.x == 0) {
+#pragma unroll
+    for (int q = 0; q < 5; ++q) S[q * NP + NP - 1] = mean[q];
+    W[2 * NP - 1] = mean[4];
+  }
+  __syncthreads();
+  const C *Z = Shape::run(f, W, W + NP, 1, tw, false);
+  grid_unpack_range<C, Rl>(Z, 4, 1, N, NP, T, j, nlat, colsH, b, rowf, H, center);
+  __syncthreads();
+#pragma unroll
+  for (int pr = 0; pr < 4; pr += 2) {
     if (threadIdx.x == 0) {
-      W0[NP - 1] = mean[0];
-      W1[NP - 1] = mean[0];
+      W[NP - 1] = mean[pr];
+      W[2 * NP - 1] = mean[pr + 1];
     }
     __syncthreads();
-    const C *Z = Shape::run(f, W0, W1, 1, tw, false);
-    for (int m = threadIdx.x; m <= T; m += blockDim.x) {
-      C zm = Z[sidx(m)];
-      C zc = cconj(Z[sidx(m == 0 ? 0 : N - m)]);
-      if (center && m == 0) {
-        const C dc = (Rl)N * Z[NP - 1];
-        zm = zm + dc;
-        zc = zc + cconj(dc);
-      }
-      C gn = half * (zm + zc);
-      C gs = half * times_i(zc - zm);
-      C he = wj * (gn + gs), ho = wj * (gn - gs);
-      H[(((size_t)m * 2 + 0) * nh + j) * colsH + b * 5 + fld] = he;
-      H[(((size_t)m * 2 + 1) * nh + j) * colsH + b * 5 + fld] = ho;
-    }
+    Z = Shape::run(f, S + pr * NP, W, 2, tw, false);
+    grid_unpack_range<C, Rl>(Z, pr, 2, N, NP, T, j, nlat, colsH, b, rowf, H, center);
     __syncthreads();
   }
 }
