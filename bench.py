@@ -442,12 +442,47 @@ def large_instance(ps, torch, stream, world, prec):
     pf.close()
     W.groups = 1 if prec == "fp64" else 2
     roofs = rooflines_of(prof, prec, 1, top=3, W=W)
+    rec = legendre_recurrence_vs_stream(ps, W, prec, prof)
     return {"workload": "T1279 (1920x3840, 5 nodes) / T639 (960x1920, 3 nodes), 16 slices, dt=30 s, jet + n^-3 "
                         "vorticity/divergence (seed 5)", "prec": prec, "value": world * 1e3 / ms,
             "unit": "PFASST iterations/s", "ms_per_step": ms, "steps": 3, "setup_s": setup_s,
             "roofline": roofs[0] if roofs else None, "rooflines_top": roofs[1:],
+            "legendre_recurrence_vs_stream": rec,
             "kernels_ms_per_iteration": {k: round(v[1], 3) for k, v in
                                          sorted(prof.items(), key=lambda kv: -kv[1][1])}}
+
+
+def legendre_recurrence_vs_stream(ps, W, prec: str, prof: dict) -> dict:
+    """The fine level's P_n^m(mu_j) (n <= T+1, one hemisphere) either come
+    from HBM as tensor-core images (what the Legendre launches do) or would be
+    generated by the FP64 n-recurrence inside each launch.  Measured: the
+    library's FP64 table kernel over every (m, n, j) of the fine level (event
+    profiler around an FP64 plan creation; it also evaluates the eps
+    coefficients with a square root and a division per step), and the fine
+    tensor-core launches of the timed workload.  Derived: the bare recurrence
+    (one multiply and one FMA per entry) at the measured FP64 peak, and the
+    images' bytes at the measured HBM bandwidth."""
+    entries = (W.TF + 2) * (W.TF + 3) // 2 * (W.GRID_F[0] // 2)
+    ps.pfsh_profiler_enable(True)
+    plan = ps.sht_plan_create(W.TF, *W.GRID_F, 1, "fp64")
+    ps.pfsh_profiler_enable(False)
+    rep = ps.pfsh_profiler_report()
+    plan.close()
+    table_ms = rep.get("k_legendre_table", [0, None])[1]
+    pk, src = peaks()
+    fp64_peak = ALU_PEAKS["fp64"][0]
+    part_bytes = {"bf16x6": 6, "bf16x3": 4, "bf16": 2, "fp16": 2}.get(prec)
+    out = {"entries_per_direction": entries, "fp64_table_kernel_ms": table_ms,
+           "fp64_table_kernel_ns_per_entry": table_ms * 1e6 / entries if table_ms else None,
+           "bare_fp64_recurrence_ms_at_peak": 2 * entries / (fp64_peak * 1e12) * 1e3,
+           "fp64_peak_tflops": fp64_peak}
+    if part_bytes:
+        out["image_gb_per_direction"] = entries * part_bytes / 1e9
+        out["image_stream_ms_at_hbm_peak"] = entries * part_bytes / (pk["hbm_gbs"] * 1e9) * 1e3
+        for name in (f"k_synth_{prec}", f"k_anal_{prec}"):
+            if name in prof:
+                out[f"{name}_ms_per_launch"] = prof[name][1] / prof[name][0]
+    return out
 
 
 def uneven_batch(ps, torch, stream, world, prec):
