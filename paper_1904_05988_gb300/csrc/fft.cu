@@ -34,7 +34,7 @@ __global__ void k_ifft_rows(FftArgs f, int T, int nlat, int cols, const typename
   const int N = Shape::n(f), NP = padded(N);
   C *a = reinterpret_cast<C *>(smem_raw);
   C *b = a + NP;
-  const int j = blockIdx.x, col = blockIdx.y, js = nlat - 1 - j;
+  const int j = blockIdx.y, col = blockIdx.x, js = nlat - 1 - j;
   for (int k = threadIdx.x; k < N; k += blockDim.x) a[sidx(k)] = mk<C>(0.0, 0.0);
   __syncthreads();
   for (int m = threadIdx.x; m <= T; m += blockDim.x) {
@@ -85,7 +85,7 @@ __global__ void k_fft_rows(FftArgs f, int T, int nlat, int cols, const Rl *__res
   const int N = Shape::n(f), NP = padded(N);
   C *a = reinterpret_cast<C *>(smem_raw);
   C *b = a + NP;
-  const int j = blockIdx.x, col = blockIdx.y, js = nlat - 1 - j;
+  const int j = blockIdx.y, col = blockIdx.x, js = nlat - 1 - j;
   const Rl *gn = grid + ((size_t)col * nlat + j) * N;
   const Rl *gs = grid + ((size_t)col * nlat + js) * N;
   for (int k = threadIdx.x; k < N; k += blockDim.x) a[sidx(k)] = mk<C>(gn[k], gs[k]);
@@ -108,7 +108,7 @@ __global__ void __launch_bounds__(256) k_grid_rhs(FftArgs f, int T, int nlat, in
                                                   typename cpx<Rl>::t *__restrict__ H, bool center) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_wait();
-  grid_rhs_body<Rl, Shape>(f, T, nlat, B, blockIdx.x, blockIdx.y, F, rowf, tw, H,
+  grid_rhs_body<Rl, Shape>(f, T, nlat, B, blockIdx.y, blockIdx.x, F, rowf, tw, H,
                            reinterpret_cast<typename cpx<Rl>::t *>(smem_raw), center);
 }
 
@@ -126,7 +126,7 @@ __global__ void __launch_bounds__(kLongThreads) k_grid_rhs_long(FftArgs f, int T
                                                        typename cpx<Rl>::t *__restrict__ H, bool center) {
   extern __shared__ __align__(16) unsigned char smem_raw[];
   pdl_wait();
-  grid_rhs_body_long<Rl, Shape>(f, T, nlat, B, blockIdx.x, blockIdx.y, F, rowf, tw, H,
+  grid_rhs_body_long<Rl, Shape>(f, T, nlat, B, blockIdx.y, blockIdx.x, F, rowf, tw, H,
                                 reinterpret_cast<typename cpx<Rl>::t *>(smem_raw), center);
 }
 
@@ -144,7 +144,7 @@ static int ifft_launch(const FftArgs &f, int T, int nlat, int cols, const typena
     if (rc) return rc;
     {
       PFSH_LAUNCH("k_ifft_rows", s);
-      k_ifft_rows<Rl, Shape><<<dim3(nlat / 2, cols), 256, sm, s>>>(f, T, nlat, cols, F, tw, grid);
+      k_ifft_rows<Rl, Shape><<<dim3(cols, nlat / 2), 256, sm, s>>>(f, T, nlat, cols, F, tw, grid);
     }
     PFSH_CHECK_LAUNCH("k_ifft_rows");
     return PFSH_OK;
@@ -181,7 +181,7 @@ static int fft_launch(const FftArgs &f, int T, int nlat, int cols, const Rl *gri
     if (rc) return rc;
     {
       PFSH_LAUNCH("k_fft_rows", s);
-      k_fft_rows<Rl, Shape><<<dim3(nlat / 2, cols), 256, sm, s>>>(f, T, nlat, cols, grid, w, tw, H);
+      k_fft_rows<Rl, Shape><<<dim3(cols, nlat / 2), 256, sm, s>>>(f, T, nlat, cols, grid, w, tw, H);
     }
     PFSH_CHECK_LAUNCH("k_fft_rows");
     return PFSH_OK;
@@ -219,11 +219,11 @@ static int grid_launch(const sht_plan *p, const FftArgs &f, int B, const typenam
     {
       PFSH_LAUNCH(longrows ? "k_grid_rhs_long" : "k_grid_rhs", s);
       if (pdl) {
-        cudaError_t e = launch_pdl(kern, dim3(p->nh, B), dim3(threads), sm, s, f, p->T, p->nlat, B, (const C *)p->F,
+        cudaError_t e = launch_pdl(kern, dim3(B, p->nh), dim3(threads), sm, s, f, p->T, p->nlat, B, (const C *)p->F,
                                    rowf, tw, (C *)p->H, center);
         if (e != cudaSuccess) return cuda_fail(e, "k_grid_rhs");
       } else {
-        kern<<<dim3(p->nh, B), threads, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw, (C *)p->H, center);
+        kern<<<dim3(B, p->nh), threads, sm, s>>>(f, p->T, p->nlat, B, (const C *)p->F, rowf, tw, (C *)p->H, center);
       }
     }
     PFSH_CHECK_LAUNCH("k_grid_rhs");

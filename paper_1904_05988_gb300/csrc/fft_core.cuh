@@ -580,7 +580,7 @@ __device__ __forceinline__ void grid_rhs_body_long(const FftArgs &f, int T, int 
     __syncthreads();
   }
   for (int t = threadIdx.x; t < 4 * (T + 1); t += blockDim.x) {
-    const int fld = t / (T + 1), m = t - fld * (T + 1);
+    const int m = t >> 2, fld = t & 3;     // consecutive threads: the 4 fields of one m
     C *z = S + fld * NP;
     C fn = F[((size_t)m * nlat + j) * colsF + b * 4 + fld];
     C fs = F[((size_t)m * nlat + js) * colsF + b * 4 + fld];
