@@ -25,11 +25,16 @@ __device__ __forceinline__ double eps_nm(int n, int m) {
 
 // ---------------------------------------------------------------------------
 // plain transforms: spec [b][ncoef] <-> X/Y [ext row][b]
+//
+// The kernels between a state-major array and a row-major X/Y take blocks
+// (state b, chunk of 256 rows): the blocks of all states that share a chunk of
+// rows run side by side, so each row of X/Y is read or written whole while it
+// is in L2 (at T1279 the arrays are larger than L2).
 // ---------------------------------------------------------------------------
 template <typename CX>
 __global__ void k_spec_to_X(int T, int ne, int batch, const double2 *__restrict__ spec, CX *__restrict__ X) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int b = blockIdx.y;
+  int idx = blockIdx.y * blockDim.x + threadIdx.x;
+  int b = blockIdx.x;
   if (idx >= ne) return;
   const int m = tri_m(idx, T + 1);  // extended triangle == packed triangle of degree T+1
   const int n = m + (idx - poff(T + 1, m));
@@ -43,8 +48,8 @@ __global__ void k_spec_to_X(int T, int ne, int batch, const double2 *__restrict_
 
 template <typename CY>
 __global__ void k_Y_to_spec(int T, int batch, const CY *__restrict__ Y, double2 *__restrict__ spec) {
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int b = blockIdx.y;
+  int idx = blockIdx.y * blockDim.x + threadIdx.x;
+  int b = blockIdx.x;
   const int nc = ncoef_of(T);
   if (idx >= nc) return;
   const int m = tri_m(idx, T);
@@ -55,7 +60,7 @@ __global__ void k_Y_to_spec(int T, int batch, const CY *__restrict__ Y, double2 
 }
 
 int spec_to_X(const sht_plan *p, const double *spec, int batch, cudaStream_t s) {
-  dim3 g((p->ne + 255) / 256, batch);
+  dim3 g(batch, (p->ne + 255) / 256);
   {
     PFSH_LAUNCH("k_spec_to_X", s);
     if (p->prec == PFSH_FP64)
@@ -68,7 +73,7 @@ int spec_to_X(const sht_plan *p, const double *spec, int batch, cudaStream_t s) 
 }
 
 int Y_to_spec(const sht_plan *p, double *spec, int batch, cudaStream_t s) {
-  dim3 g((p->ncoef + 255) / 256, batch);
+  dim3 g(batch, (p->ncoef + 255) / 256);
   {
     PFSH_LAUNCH("k_Y_to_spec", s);
     if (p->prec == PFSH_FP64)
@@ -92,8 +97,8 @@ template <typename M>
 __global__ void k_rhs_prep(int T, int ne, int B, M ma2, M inva, double omega, double phibar, SpecTables<M> tb,
                            const double2 *__restrict__ state, typename cpx<M>::t *__restrict__ X) {
   typedef typename cpx<M>::t C;
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int b = blockIdx.y;
+  int idx = blockIdx.y * blockDim.x + threadIdx.x;
+  int b = blockIdx.x;
   if (idx >= ne) return;
   const int nc = ncoef_of(T);
   const int m = tri_m(idx, T + 1);
@@ -109,7 +114,7 @@ __global__ void k_rhs_prep(int T, int ne, int B, M ma2, M inva, double omega, do
 }
 
 int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &prm, cudaStream_t s) {
-  dim3 g((p->ne + 255) / 256, B);
+  dim3 g(B, (p->ne + 255) / 256);
   {
     PFSH_LAUNCH("k_rhs_prep", s);
     if (p->prec == PFSH_FP64)
@@ -140,8 +145,8 @@ __global__ void k_rhs_assemble(int T, int B, M inva, M inva2, double dinva2, dou
                                const double2 *__restrict__ state, double2 *__restrict__ fE,
                                double2 *__restrict__ fI) {
   typedef typename cpx<M>::t C;
-  int idx = blockIdx.x * blockDim.x + threadIdx.x;
-  int b = blockIdx.y;
+  int idx = blockIdx.y * blockDim.x + threadIdx.x;
+  int b = blockIdx.x;
   const int nc = ncoef_of(T);
   if (idx >= nc) return;
   const int m = tri_m(idx, T);
@@ -167,7 +172,7 @@ __global__ void k_rhs_assemble(int T, int B, M inva, M inva2, double dinva2, dou
 
 int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
                  CorArgs cor, cudaStream_t s) {
-  dim3 g((p->ncoef + 255) / 256, B);
+  dim3 g(B, (p->ncoef + 255) / 256);
   const double inva = 1.0 / prm.a, inva2 = 1.0 / (prm.a * prm.a);
   {
     PFSH_LAUNCH("k_rhs_assemble", s);
