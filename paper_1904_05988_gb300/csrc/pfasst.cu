@@ -57,7 +57,8 @@ __global__ void k_fas(int Tf, int Tc, int nts, int nf, int ncn, double dt, Mat16
   const int m = tri_m2(idx, Tc);
   const int fidx = poff(Tf, m) + (idx - poff(Tc, m));
   const size_t fs = (size_t)nts * 3 * ncf, cs = (size_t)nts * 3 * ncc;
-  for (int f = 0; f < 3; ++f) {
+  {
+    const int f = blockIdx.z;   // one field per grid layer
     const size_t fo = (size_t)b * 3 * ncf + (size_t)f * ncf + fidx;
     const size_t co = (size_t)b * 3 * ncc + (size_t)f * ncc + idx;
     double2 Ff[MF], Fc[MC];
@@ -103,7 +104,8 @@ __global__ void k_interp_inc(int Tf, int Tc, int nts, int nf, int ncn, int kmin,
   const int m = tri_m2(idx, Tc);
   const int fidx = poff(Tf, m) + (idx - poff(Tc, m));
   const size_t fs = (size_t)nts * 3 * ncf, cs = (size_t)nts * 3 * ncc;
-  for (int f = 0; f < 3; ++f) {
+  {
+    const int f = blockIdx.z;   // one field per grid layer
     const size_t fo = (size_t)b * 3 * ncf + (size_t)f * ncf + fidx;
     const size_t co = (size_t)b * 3 * ncc + (size_t)f * ncc + idx;
     double2 d[MC];
@@ -193,7 +195,8 @@ __global__ void k_pred_interp(int Tf, int Tc, int nts, int nf, int ncn, Mat16 Pt
   const size_t fs = (size_t)nts * 3 * ncf, cs = (size_t)nts * 3 * ncc;
   const bool low = (n <= Tc);
   const int cidx = low ? poff(Tc, m) + (n - m) : 0;
-  for (int f = 0; f < 3; ++f) {
+  {
+    const int f = blockIdx.z;   // one field per grid layer
     const double2 base = th0[(size_t)f * ncf + idx];
     double2 d[MC];
     if (low) {
@@ -233,7 +236,8 @@ __global__ void k_node0(int Tf, int Tc, int first, const double2 *__restrict__ s
   if (idx >= ncf) return;
   const int m = tri_m2(idx, Tf);
   const int n = m + (idx - poff(Tf, m));
-  for (int f = 0; f < 3; ++f) {
+  {
+    const int f = blockIdx.z;   // one field per grid layer
     double2 v = sent[(size_t)(b - 1) * 3 * ncf + (size_t)f * ncf + idx];
     if (n <= Tc) {
       const double2 c = thc0[(size_t)b * 3 * ncc + (size_t)f * ncc + poff(Tc, m) + (n - m)];
@@ -412,7 +416,7 @@ static int predict_body(pfasst *pf, cudaStream_t s) {
   Mat16 P;
   for (int i = 0; i < 16; ++i)
     for (int k = 0; k < 16; ++k) P.v[i][k] = pf->Pt[i][k];
-  dim3 g((ncoef_of(pf->cfg.Tf) + 255) / 256, nts);
+  dim3 g((ncoef_of(pf->cfg.Tf) + 255) / 256, nts, 3);
   {
     PFSH_LAUNCH("k_pred_interp", s);
     auto kern = (Mf + 1 == 5 && Mc + 1 == 3) ? k_pred_interp<5, 3> : k_pred_interp<9, 9>;
@@ -467,7 +471,7 @@ static int steps_AB(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
     }
     for (int k = 0; k <= Mc; ++k) Qc.v[i][k] = pf->lev_c->Q[i][k];
   }
-  dim3 g((ncoef_of(c.Tc) + 255) / 256, cnt);
+  dim3 g((ncoef_of(c.Tc) + 255) / 256, cnt, 3);
   {
     PFSH_LAUNCH("k_fas", s);
     auto kern = (Mf + 1 == 5 && Mc + 1 == 3) ? k_fas<5, 3> : k_fas<9, 9>;
@@ -496,7 +500,7 @@ static int step_D(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
   Mat16 P;
   for (int i = 0; i < 16; ++i)
     for (int k = 0; k < 16; ++k) P.v[i][k] = pf->Pt[i][k];
-  dim3 g((ncoef_of(c.Tc) + 255) / 256, cnt);
+  dim3 g((ncoef_of(c.Tc) + 255) / 256, cnt, 3);
   const double *xc[3] = {pf->th_c, pf->fe_c, pf->fi_c};
   const double *xs[3] = {pf->th_cs, pf->fe_cs, pf->fi_cs};
   double *xf[3] = {pf->th_f, pf->fe_f, pf->fi_f};
@@ -511,7 +515,7 @@ static int step_D(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
   }
   const int first = g0 == 0 ? 1 : 0;
   if (cnt - first > 0) {
-    dim3 g0d((ncoef_of(c.Tf) + 255) / 256, cnt - first);
+    dim3 g0d((ncoef_of(c.Tf) + 255) / 256, cnt - first, 3);
     {
       PFSH_LAUNCH("k_node0", s);
       k_node0<<<g0d, 256, 0, s>>>(c.Tf, c.Tc, first, (const double2 *)(pf->sent + ((size_t)par * nts + g0) * sf),

@@ -420,7 +420,8 @@ __global__ void k_restrict(int Tf, int Tc, int B, int nf, int nc_nodes, TimeMat 
   if (idx >= ncc) return;
   const int m = tri_m(idx, Tc);
   const int fidx = poff(Tf, m) + (idx - poff(Tc, m));
-  for (int f = 0; f < 3; ++f) {
+  {
+    const int f = blockIdx.z;   // one field per grid layer
     for (int i = 0; i < nc_nodes; ++i) {
       double2 acc = make_double2(0.0, 0.0);
       for (int k = 0; k < nf; ++k) {
@@ -444,7 +445,7 @@ int restrict_launch(const double *Rt, int nf, int ncn, const double *xf, size_t 
   TimeMat R;
   for (int i = 0; i < 16; ++i)
     for (int k = 0; k < 16; ++k) R.v[i][k] = (i < ncn && k < nf) ? Rt[i * 16 + k] : 0.0;
-  dim3 g((ncoef_of(Tc) + 255) / 256, B);
+  dim3 g((ncoef_of(Tc) + 255) / 256, B, 3);
   // fbstride: batch stride inside a node (one fine state) unless broadcasting
   {
     PFSH_LAUNCH("k_restrict", s);
