@@ -374,9 +374,12 @@ int ifft_rows_f64_raw(int N, int npass, const int *radix, int full, int T, int n
 // spectral pre/post processing
 int spec_to_X(const sht_plan *p, const double *spec, int batch, cudaStream_t s);
 int Y_to_spec(const sht_plan *p, double *spec, int batch, cudaStream_t s);
-int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &prm, cudaStream_t s);
+// The batch of B states is cnt consecutive states (stride 3 ncoef complex)
+// in each of B / cnt groups nstride doubles apart (cnt = 0: one group of B).
+int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &prm, cudaStream_t s, int cnt = 0,
+             size_t nstride = 0);
 int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI, int B,
-                 const swe_params &prm, CorArgs cor, cudaStream_t s);
+                 const swe_params &prm, CorArgs cor, cudaStream_t s, int cnt = 0, size_t nstride = 0);
 
 // banded implicit solve of the split with the Coriolis term implicit (banded.cu)
 int band_ctx_init(swe_ctx *c);
@@ -389,6 +392,10 @@ int implicit_solve_launch(int T, const double *b, double *x, double h, int B,
 
 // internal RHS on a contiguous batch (chunks over ctx->max_states)
 int rhs_eval(swe_ctx *c, const double *state, double *fE, double *fI, int B, cudaStream_t s);
+// F_E, F_I of `nodes` groups of cnt consecutive states, node_stride doubles
+// apart (one pass over all nodes x cnt states when the context holds them)
+int rhs_eval_nodes(swe_ctx *c, const double *state, double *fE, double *fI, int nodes, int cnt, size_t node_stride,
+                   cudaStream_t s);
 
 // SDC pieces: node arrays are [nodes][..] with a node stride (in doubles)
 int sdc_sweep_strided(sdc_level *l, double *theta, double *fE, double *fI, const double *tau,

@@ -448,10 +448,10 @@ static int steps_AB(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
                               cnt, s)))
       return rc;
   }
-  for (int i = 0; i <= Mc; ++i) {
-    const size_t o = i * cnode + g0 * sc;
-    if ((rc = rhs_eval(pf->ctx_c, pf->th_c + o, pf->fe_c + o, pf->fi_c + o, cnt, s))) return rc;
-  }
+  // coarse F at every node: one pass over the (Mc+1) x cnt states
+  if ((rc = rhs_eval_nodes(pf->ctx_c, pf->th_c + g0 * sc, pf->fe_c + g0 * sc, pf->fi_c + g0 * sc, Mc + 1, cnt, cnode,
+                           s)))
+    return rc;
   const double *src[3] = {pf->th_c, pf->fe_c, pf->fi_c};
   double *dst[3] = {pf->th_cs, pf->fe_cs, pf->fi_cs};
   for (int q = 0; q < 3; ++q)

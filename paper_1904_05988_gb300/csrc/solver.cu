@@ -14,15 +14,18 @@ namespace pfsh {
 
 // One RHS pass: velocity recovery -> synthesis of 4 fields -> inverse FFT,
 // grid products, forward FFT -> analysis of 5 fields -> assembly.
-static int rhs_pass(swe_ctx *c, const double *state, double *fE, double *fI, int B, cudaStream_t s) {
+// cnt, nstride: the batch is B / cnt groups of cnt consecutive states,
+// nstride doubles apart (cnt = 0: contiguous; the small path needs that)
+static int rhs_pass(swe_ctx *c, const double *state, double *fE, double *fI, int B, cudaStream_t s, int cnt = 0,
+                    size_t nstride = 0) {
   const sht_plan *p = c->plan;
   if (small_rhs(B)) return rhs_small(p, state, fE, fI, B, c->prm, cor_args(c), s);
   int rc;
-  if ((rc = rhs_prep(p, state, B, c->prm, s))) return rc;
+  if ((rc = rhs_prep(p, state, B, c->prm, s, cnt, nstride))) return rc;
   if ((rc = legendre_synth(p, 4 * B, s))) return rc;
   if ((rc = grid_rhs(p, B, c->prm, s))) return rc;
   if ((rc = legendre_analysis(p, 5 * B, s))) return rc;
-  return rhs_assemble(p, state, fE, fI, B, c->prm, cor_args(c), s);
+  return rhs_assemble(p, state, fE, fI, B, c->prm, cor_args(c), s, cnt, nstride);
 }
 
 int rhs_eval(swe_ctx *c, const double *state, double *fE, double *fI, int B, cudaStream_t s) {
@@ -30,6 +33,19 @@ int rhs_eval(swe_ctx *c, const double *state, double *fE, double *fI, int B, cud
   for (int b0 = 0; b0 < B; b0 += c->max_states) {
     const int nb = std::min(c->max_states, B - b0);
     int rc = rhs_pass(c, state + b0 * st, fE + b0 * st, fI ? fI + b0 * st : nullptr, nb, s);
+    if (rc) return rc;
+  }
+  return PFSH_OK;
+}
+
+int rhs_eval_nodes(swe_ctx *c, const double *state, double *fE, double *fI, int nodes, int cnt, size_t node_stride,
+                   cudaStream_t s) {
+  const int B = nodes * cnt;
+  if (nodes > 1 && B <= c->max_states && !small_rhs(B))
+    return rhs_pass(c, state, fE, fI, B, s, cnt, node_stride);
+  for (int i = 0; i < nodes; ++i) {
+    const size_t o = (size_t)i * node_stride;
+    int rc = rhs_eval(c, state + o, fE + o, fI ? fI + o : nullptr, cnt, s);
     if (rc) return rc;
   }
   return PFSH_OK;

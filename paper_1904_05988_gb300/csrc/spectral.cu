@@ -94,8 +94,9 @@ int Y_to_spec(const sht_plan *p, double *spec, int batch, cudaStream_t s) {
 //   V_n = [i m psi_n - (n-1) eps_n chi_{n-1} + (n+2) eps_{n+1} chi_{n+1}] / a
 // ---------------------------------------------------------------------------
 template <typename M>
-__global__ void k_rhs_prep(int T, int ne, int B, M ma2, M inva, double omega, double phibar, SpecTables<M> tb,
-                           const double2 *__restrict__ state, typename cpx<M>::t *__restrict__ X) {
+__global__ void k_rhs_prep(int T, int ne, int B, int cnt, size_t nstride, M ma2, M inva, double omega,
+                           double phibar, SpecTables<M> tb, const double2 *__restrict__ state,
+                           typename cpx<M>::t *__restrict__ X) {
   typedef typename cpx<M>::t C;
   int idx = blockIdx.y * blockDim.x + threadIdx.x;
   int b = blockIdx.x;
@@ -103,7 +104,7 @@ __global__ void k_rhs_prep(int T, int ne, int B, M ma2, M inva, double omega, do
   const int nc = ncoef_of(T);
   const int m = tri_m(idx, T + 1);
   const int n = m + (idx - poff(T + 1, m));
-  const double2 *Phi = state + (size_t)b * 3 * nc;
+  const double2 *Phi = state + (size_t)(b / cnt) * nstride + (size_t)(b % cnt) * 3 * nc;
   C out[4];
   prep_point<M>(T, m, n, Phi, Phi + nc, Phi + 2 * nc, poff(T, m) - m, (size_t)idx, tb, ma2, inva, omega, phibar, out);
   C *row = X + (size_t)idx * (4 * B) + b * 4;
@@ -113,17 +114,20 @@ __global__ void k_rhs_prep(int T, int ne, int B, M ma2, M inva, double omega, do
   row[3] = out[3];
 }
 
-int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &prm, cudaStream_t s) {
+int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &prm, cudaStream_t s, int cnt,
+             size_t nstride) {
+  if (cnt <= 0) cnt = B;
+  nstride /= 2;   // doubles -> complex elements
   dim3 g(B, (p->ne + 255) / 256);
   {
     PFSH_LAUNCH("k_rhs_prep", s);
     if (p->prec == PFSH_FP64)
-      k_rhs_prep<double><<<g, 256, 0, s>>>(p->T, p->ne, B, -prm.a * prm.a, 1.0 / prm.a, omega_explicit(prm),
+      k_rhs_prep<double><<<g, 256, 0, s>>>(p->T, p->ne, B, cnt, nstride, -prm.a * prm.a, 1.0 / prm.a, omega_explicit(prm),
                                            prm.phibar,
                                            SpecTables<double>{p->d_eps, p->d_ilap}, (const double2 *)state,
                                            (double2 *)p->X);
     else
-      k_rhs_prep<float><<<g, 256, 0, s>>>(p->T, p->ne, B, (float)(-prm.a * prm.a), (float)(1.0 / prm.a),
+      k_rhs_prep<float><<<g, 256, 0, s>>>(p->T, p->ne, B, cnt, nstride, (float)(-prm.a * prm.a), (float)(1.0 / prm.a),
                                           omega_explicit(prm), prm.phibar, SpecTables<float>{p->d_eps32, p->d_ilap32},
                                           (const double2 *)state, (float2 *)p->X);
   }
@@ -140,7 +144,8 @@ int rhs_prep(const sht_plan *p, const double *state, int B, const swe_params &pr
 //   F_I = [-Phibar delta - nu k Phi, -nu k zeta, k Phi - nu k delta], k = n(n+1)/a^2
 // ---------------------------------------------------------------------------
 template <typename M>
-__global__ void k_rhs_assemble(int T, int B, M inva, M inva2, double dinva2, double nu, double phibar,
+__global__ void k_rhs_assemble(int T, int B, int cnt, size_t nstride, M inva, M inva2, double dinva2, double nu,
+                               double phibar,
                                CorArgs cor, const M *__restrict__ eps, const typename cpx<M>::t *__restrict__ Y,
                                const double2 *__restrict__ state, double2 *__restrict__ fE,
                                double2 *__restrict__ fI) {
@@ -162,26 +167,28 @@ __global__ void k_rhs_assemble(int T, int B, M inva, M inva2, double dinva2, dou
   }
   double2 fe[3];
   assemble_point<M, C>(m, n, cur, up, dn, n > m, eps[r0 + 1], eps[r0], inva, inva2, fe);
-  double2 *oE = fE + (size_t)b * 3 * nc;
+  const size_t sb = (size_t)(b / cnt) * nstride + (size_t)(b % cnt) * 3 * nc;   // state b of the batch
+  double2 *oE = fE + sb;
   oE[idx] = fe[0];
   oE[nc + idx] = fe[1];
   oE[2 * nc + idx] = fe[2];
-  if (fI)
-    linear_point(m, n, T, state + (size_t)b * 3 * nc, nc, idx, dinva2, nu, phibar, cor, fI + (size_t)b * 3 * nc);
+  if (fI) linear_point(m, n, T, state + sb, nc, idx, dinva2, nu, phibar, cor, fI + sb);
 }
 
 int rhs_assemble(const sht_plan *p, const double *state, double *fE, double *fI, int B, const swe_params &prm,
-                 CorArgs cor, cudaStream_t s) {
+                 CorArgs cor, cudaStream_t s, int cnt, size_t nstride) {
+  if (cnt <= 0) cnt = B;
+  nstride /= 2;   // doubles -> complex elements
   dim3 g(B, (p->ncoef + 255) / 256);
   const double inva = 1.0 / prm.a, inva2 = 1.0 / (prm.a * prm.a);
   {
     PFSH_LAUNCH("k_rhs_assemble", s);
     if (p->prec == PFSH_FP64)
-      k_rhs_assemble<double><<<g, 256, 0, s>>>(p->T, B, inva, inva2, inva2, prm.nu, prm.phibar, cor, p->d_eps,
+      k_rhs_assemble<double><<<g, 256, 0, s>>>(p->T, B, cnt, nstride, inva, inva2, inva2, prm.nu, prm.phibar, cor, p->d_eps,
                                                (const double2 *)p->Y, (const double2 *)state, (double2 *)fE,
                                                (double2 *)fI);
     else
-      k_rhs_assemble<float><<<g, 256, 0, s>>>(p->T, B, (float)inva, (float)inva2, inva2, prm.nu, prm.phibar,
+      k_rhs_assemble<float><<<g, 256, 0, s>>>(p->T, B, cnt, nstride, (float)inva, (float)inva2, inva2, prm.nu, prm.phibar,
                                               cor, p->d_eps32, (const float2 *)p->Y, (const double2 *)state,
                                               (double2 *)fE, (double2 *)fI);
   }
