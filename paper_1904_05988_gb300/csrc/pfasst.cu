@@ -93,19 +93,28 @@ __global__ void k_fas(int Tf, int Tc, int nts, int nf, int ncn, double dt, Mat16
 // x_f[k] += sum_i Pt[k][i] Z(x_c[i] - x_cs[i]) for fine nodes k >= kmin and
 // the coefficients the coarse level holds (zero-padding elsewhere); node
 // counts bounded at compile time as in k_fas.
+// The three arrays (theta, F_E, F_I) in one launch: grid layer z = 3 q + f
+// takes field f of array q.
+struct InterpArrays {
+  const double2 *xc[3], *xcs[3];
+  double2 *xf[3];
+};
+
 template <int MF, int MC>
-__global__ void k_interp_inc(int Tf, int Tc, int nts, int nf, int ncn, int kmin, Mat16 Pt,
-                             const double2 *__restrict__ xc, const double2 *__restrict__ xcs,
-                             double2 *__restrict__ xf) {
+__global__ void k_interp_inc(int Tf, int Tc, int nts, int nf, int ncn, int kmin, Mat16 Pt, InterpArrays arr) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
+  const int q = blockIdx.z / 3;
+  const double2 *__restrict__ xc = arr.xc[q];
+  const double2 *__restrict__ xcs = arr.xcs[q];
+  double2 *__restrict__ xf = arr.xf[q];
   const int ncc = ncoef_of(Tc), ncf = ncoef_of(Tf);
   if (idx >= ncc) return;
   const int m = tri_m2(idx, Tc);
   const int fidx = poff(Tf, m) + (idx - poff(Tc, m));
   const size_t fs = (size_t)nts * 3 * ncf, cs = (size_t)nts * 3 * ncc;
   {
-    const int f = blockIdx.z;   // one field per grid layer
+    const int f = blockIdx.z - 3 * q;   // field f of array q
     const size_t fo = (size_t)b * 3 * ncf + (size_t)f * ncf + fidx;
     const size_t co = (size_t)b * 3 * ncc + (size_t)f * ncc + idx;
     double2 d[MC];
@@ -161,6 +170,34 @@ __global__ void k_residual(size_t n2, const double2 *__restrict__ cur, double2 *
     }
     res[b] = mv > 0.0 ? md / mv : md;
   }
+}
+
+// Three device copies of the same shape in one launch: rows x n2 complex
+// elements, row pitches spitch / dpitch (complex elements); layer z = array.
+struct Copy3 {
+  const double2 *src[3];
+  double2 *dst[3];
+};
+
+__global__ void k_copy3(Copy3 c, size_t n2, size_t spitch, size_t dpitch) {
+  const size_t e = (size_t)blockIdx.x * blockDim.x + threadIdx.x;
+  const int row = blockIdx.y, q = blockIdx.z;
+  if (e < n2) c.dst[q][(size_t)row * dpitch + e] = c.src[q][(size_t)row * spitch + e];
+}
+
+static int copy3(const double *const src[3], double *const dst[3], size_t n2, int rows, size_t spitch,
+                 size_t dpitch, cudaStream_t s) {
+  Copy3 c;
+  for (int q = 0; q < 3; ++q) {
+    c.src[q] = (const double2 *)src[q];
+    c.dst[q] = (double2 *)dst[q];
+  }
+  {
+    PFSH_LAUNCH("k_copy3", s);
+    k_copy3<<<dim3((unsigned)((n2 + 255) / 256), rows, 3), 256, 0, s>>>(c, n2, spitch, dpitch);
+  }
+  PFSH_CHECK_LAUNCH("k_copy3");
+  return PFSH_OK;
 }
 
 // Predictor start: the restricted initial value (state 0 of base_c) and its
@@ -402,11 +439,11 @@ static int predict_body(pfasst *pf, cudaStream_t s) {
   // rounds: slices n >= j take slice n-1's round j-1 end value and sweep
   for (int j = 0; j < nts; ++j) {
     const int cnt = nts - j;
-    if (j > 0) {
-      const size_t from = Mc * cnode + (j - 1) * sc, to = j * sc, bytes = cnt * sc * 8;
-      PFSH_CUDA(cudaMemcpyAsync(pf->th_c + to, pf->th_c + from, bytes, cudaMemcpyDeviceToDevice, s));
-      PFSH_CUDA(cudaMemcpyAsync(pf->fe_c + to, pf->fe_c + from, bytes, cudaMemcpyDeviceToDevice, s));
-      PFSH_CUDA(cudaMemcpyAsync(pf->fi_c + to, pf->fi_c + from, bytes, cudaMemcpyDeviceToDevice, s));
+    if (j > 0) {   // node 0 of slices j.. <- last node of slices j-1.. (distinct nodes: no overlap)
+      const size_t from = Mc * cnode + (j - 1) * sc, to = j * sc;
+      const double *src[3] = {pf->th_c + from, pf->fe_c + from, pf->fi_c + from};
+      double *const dst[3] = {pf->th_c + to, pf->fe_c + to, pf->fi_c + to};
+      if ((rc = copy3(src, dst, cnt * sc / 2, 1, 0, 0, s))) return rc;
     }
     if ((rc = sdc_sweep_strided(pf->lev_c, pf->th_c + j * sc, pf->fe_c + j * sc, pf->fi_c + j * sc, nullptr, cnode,
                                 cnt, s)))
@@ -454,9 +491,11 @@ static int steps_AB(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
     return rc;
   const double *src[3] = {pf->th_c, pf->fe_c, pf->fi_c};
   double *dst[3] = {pf->th_cs, pf->fe_cs, pf->fi_cs};
-  for (int q = 0; q < 3; ++q)
-    PFSH_CUDA(cudaMemcpy2DAsync(dst[q] + g0 * sc, cnode * 8, src[q] + g0 * sc, cnode * 8, cnt * sc * 8, Mc + 1,
-                                cudaMemcpyDeviceToDevice, s));
+  {
+    const double *s3[3] = {src[0] + g0 * sc, src[1] + g0 * sc, src[2] + g0 * sc};
+    double *const d3[3] = {dst[0] + g0 * sc, dst[1] + g0 * sc, dst[2] + g0 * sc};
+    if ((rc = copy3(s3, d3, cnt * sc / 2, Mc + 1, cnode / 2, cnode / 2, s))) return rc;
+  }
   Mat16 RQf, Qc;
   for (int i = 0; i < 16; ++i)
     for (int k = 0; k < 16; ++k) {
@@ -500,19 +539,22 @@ static int step_D(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
   Mat16 P;
   for (int i = 0; i < 16; ++i)
     for (int k = 0; k < 16; ++k) P.v[i][k] = pf->Pt[i][k];
-  dim3 g((ncoef_of(c.Tc) + 255) / 256, cnt, 3);
+  dim3 g((ncoef_of(c.Tc) + 255) / 256, cnt, 9);
   const double *xc[3] = {pf->th_c, pf->fe_c, pf->fi_c};
   const double *xs[3] = {pf->th_cs, pf->fe_cs, pf->fi_cs};
   double *xf[3] = {pf->th_f, pf->fe_f, pf->fi_f};
+  InterpArrays arr;
   for (int q = 0; q < 3; ++q) {
-    {
-      PFSH_LAUNCH("k_interp_inc", s);
-      auto kern = (Mf + 1 == 5 && Mc + 1 == 3) ? k_interp_inc<5, 3> : k_interp_inc<9, 9>;
-      kern<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, 1, P, (const double2 *)(xc[q] + g0 * sc),
-                                     (const double2 *)(xs[q] + g0 * sc), (double2 *)(xf[q] + g0 * sf));
-    }
-    PFSH_CHECK_LAUNCH("k_interp_inc");
+    arr.xc[q] = (const double2 *)(xc[q] + g0 * sc);
+    arr.xcs[q] = (const double2 *)(xs[q] + g0 * sc);
+    arr.xf[q] = (double2 *)(xf[q] + g0 * sf);
   }
+  {
+    PFSH_LAUNCH("k_interp_inc", s);
+    auto kern = (Mf + 1 == 5 && Mc + 1 == 3) ? k_interp_inc<5, 3> : k_interp_inc<9, 9>;
+    kern<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, 1, P, arr);
+  }
+  PFSH_CHECK_LAUNCH("k_interp_inc");
   const int first = g0 == 0 ? 1 : 0;
   if (cnt - first > 0) {
     dim3 g0d((ncoef_of(c.Tf) + 255) / 256, cnt - first, 3);
