@@ -44,12 +44,15 @@ __device__ __forceinline__ int tri_m2(int idx, int T) {
 // (FAS correction of Eq. tau_term_level_l+1 with tau_f = 0; the Theta terms
 // of A_c(R Theta_f) - R A_f(Theta_f) cancel.)  MF, MC bound the node counts
 // at compile time (nf <= MF, ncn <= MC) so that the per-node values stay in
-// registers.
+// registers.  The same pass saves theta_c, F_E,c and F_I,c of every coarse
+// node (th_cs, fe_cs, fi_cs: the values Step D takes the coarse increment
+// against), since it reads the two right-hand sides anyway.
 template <int MF, int MC>
 __global__ void k_fas(int Tf, int Tc, int nts, int nf, int ncn, double dt, Mat16 RQf, Mat16 Qc,
                       const double2 *__restrict__ fe_f, const double2 *__restrict__ fi_f,
                       const double2 *__restrict__ fe_c, const double2 *__restrict__ fi_c,
-                      double2 *__restrict__ tau) {
+                      double2 *__restrict__ tau, const double2 *__restrict__ th_c, double2 *__restrict__ th_cs,
+                      double2 *__restrict__ fe_cs, double2 *__restrict__ fi_cs) {
   int idx = blockIdx.x * blockDim.x + threadIdx.x;
   int b = blockIdx.y;
   const int ncc = ncoef_of(Tc), ncf = ncoef_of(Tf);
@@ -67,7 +70,13 @@ __global__ void k_fas(int Tf, int Tc, int nts, int nf, int ncn, double dt, Mat16
       if (k < nf) Ff[k] = fe_f[k * fs + fo] + fi_f[k * fs + fo];
 #pragma unroll
     for (int k = 0; k < MC; ++k)
-      if (k < ncn) Fc[k] = fe_c[k * cs + co] + fi_c[k * cs + co];
+      if (k < ncn) {
+        const double2 e = fe_c[k * cs + co], g = fi_c[k * cs + co];
+        Fc[k] = e + g;
+        fe_cs[k * cs + co] = e;
+        fi_cs[k * cs + co] = g;
+        th_cs[k * cs + co] = th_c[k * cs + co];
+      }
 #pragma unroll
     for (int i = 0; i < MC; ++i) {
       if (i >= ncn) break;
@@ -489,13 +498,7 @@ static int steps_AB(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
   if ((rc = rhs_eval_nodes(pf->ctx_c, pf->th_c + g0 * sc, pf->fe_c + g0 * sc, pf->fi_c + g0 * sc, Mc + 1, cnt, cnode,
                            s)))
     return rc;
-  const double *src[3] = {pf->th_c, pf->fe_c, pf->fi_c};
-  double *dst[3] = {pf->th_cs, pf->fe_cs, pf->fi_cs};
-  {
-    const double *s3[3] = {src[0] + g0 * sc, src[1] + g0 * sc, src[2] + g0 * sc};
-    double *const d3[3] = {dst[0] + g0 * sc, dst[1] + g0 * sc, dst[2] + g0 * sc};
-    if ((rc = copy3(s3, d3, cnt * sc / 2, Mc + 1, cnode / 2, cnode / 2, s))) return rc;
-  }
+  // (the saved coarse copies for Step D are written by k_fas below)
   Mat16 RQf, Qc;
   for (int i = 0; i < 16; ++i)
     for (int k = 0; k < 16; ++k) {
@@ -516,7 +519,9 @@ static int steps_AB(pfasst *pf, int g0, int cnt, int par, cudaStream_t s) {
     auto kern = (Mf + 1 == 5 && Mc + 1 == 3) ? k_fas<5, 3> : k_fas<9, 9>;
     kern<<<g, 256, 0, s>>>(c.Tf, c.Tc, nts, Mf + 1, Mc + 1, c.dt, RQf, Qc, (const double2 *)(pf->fe_f + g0 * sf),
                             (const double2 *)(pf->fi_f + g0 * sf), (const double2 *)(pf->fe_c + g0 * sc),
-                            (const double2 *)(pf->fi_c + g0 * sc), (double2 *)(pf->tau + g0 * sc));
+                            (const double2 *)(pf->fi_c + g0 * sc), (double2 *)(pf->tau + g0 * sc),
+                            (const double2 *)(pf->th_c + g0 * sc), (double2 *)(pf->th_cs + g0 * sc),
+                            (double2 *)(pf->fe_cs + g0 * sc), (double2 *)(pf->fi_cs + g0 * sc));
   }
   PFSH_CHECK_LAUNCH("k_fas");
   return PFSH_OK;
