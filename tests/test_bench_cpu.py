@@ -65,3 +65,30 @@ def test_proc_cpu_seconds_counts_this_process():
     while time.process_time() < end:
         x += 1
     assert bench.proc_cpu_seconds([os.getpid()]) - t0 > 0.1
+
+
+def test_grid_work_is_split_between_the_long_and_short_row_kernels():
+    """A row of nlon points takes the long-row kernel when its 10 padded
+    transforms (nlon + nlon/16 + 1 complex entries) exceed 227 KB; the work
+    model gives each kernel the rows it serves, so the two together carry the
+    whole grid stage of the T1279/T639 workload."""
+    assert bench.grid_long_rows(3840, 4) and bench.grid_long_rows(1536, 8)
+    assert not bench.grid_long_rows(1920, 4) and not bench.grid_long_rows(768, 4)
+    W = bench.Workload(1279, 639, 16, 5, 3)
+    long_w = bench.kernel_work_per_iteration("k_grid_rhs_long", "bf16x3", W)[0]
+    short_w = bench.kernel_work_per_iteration("k_grid_rhs", "bf16x3", W)[0]
+    nfs, ncb, ncs = bench.rhs_states_per_iteration(W)
+    (nlat_f, _), (nlat_c, _) = W.GRID_F, W.GRID_C
+    assert long_w == nfs * bench.grid_rhs_bytes(1279, nlat_f, 1, 4)
+    assert short_w == (ncb + ncs) * bench.grid_rhs_bytes(639, nlat_c, 1, 4)
+    # at T255/T127 both levels take the short-row kernel
+    assert bench.kernel_work_per_iteration("k_grid_rhs_long", "bf16x3")[0] == 0
+
+
+def test_legendre_entry_count_of_one_direction():
+    """(T+2)(T+3)/2 rows (m <= n <= T+1) times nlat/2 latitudes: 788,276,160
+    entries at T1279 on 1920 latitudes, 3.15 GB as 3xBF16 images (4 bytes)."""
+    W = bench.Workload(1279, 639, 16, 5, 3)
+    entries = (W.TF + 2) * (W.TF + 3) // 2 * (W.GRID_F[0] // 2)
+    assert entries == 788_276_160
+    assert abs(entries * 4 / 1e9 - 3.153) < 1e-3
